@@ -1,0 +1,190 @@
+/*
+ * kifmm.h -- C ABI of the GB300 Laplace kernel-independent FMM.
+ *
+ * The library evaluates the 3D Laplace N-body sum, Eq. (1) of "The Fast
+ * Multipole Method" section:
+ *
+ *     phi_j = sum_{i != j} q_i / (4 pi |x_i - x_j|),   j = 1..n,
+ *
+ * with the kernel-independent FMM the paper implements: a linear octree split
+ * while a box holds more than ncrit points, the U/V/W/X interaction lists
+ * ("Computational structure of FMM operators": near field, M2L, M2P, P2L),
+ * check and equivalent surfaces of 6(p-1)^2 + 2 points, and the operators
+ * P2M, M2M, M2L, L2L, P2L, L2P, M2P and the near field (P2P).
+ *
+ * All types are plain C; no PyTorch or CUDA runtime type appears in a
+ * signature.  A cudaStream_t is passed as void*.
+ *
+ * Errors: every entry point returns an fmm_status and never aborts the
+ * process.  fmm_last_error() returns a thread-local message for the last
+ * failure on the calling thread.
+ */
+#ifndef KIFMM_H
+#define KIFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmm_plan_s *fmm_plan_t; /* opaque, owned by the library */
+
+typedef enum {
+    FMM_OK = 0,
+    FMM_ERR_INVALID_ARG = 1, /* bad pointer, size, option or state */
+    FMM_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    FMM_ERR_OOM = 3,         /* host or device allocation failed */
+    FMM_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    FMM_ERR_UNSUPPORTED = 5  /* valid request this build does not handle */
+} fmm_status;
+
+/* Arithmetic used for the V-list M2L translations. */
+typedef enum {
+    FMM_M2L_FP32 = 0,   /* FP32 FMA on the CUDA cores */
+    FMM_M2L_BF16X3 = 1, /* tcgen05 kind::f16, hi/lo BF16 split, 3 products */
+    FMM_M2L_TF32X3 = 2  /* tcgen05 kind::tf32, hi/lo TF32 split, 3 products */
+} fmm_m2l_mode;
+
+/* Plan options.  fmm_options_init() fills the defaults given here. */
+typedef struct {
+    double alpha_inner; /* radius of upward-equivalent / downward-check
+                           surfaces in box half-widths (1.05) */
+    double alpha_outer; /* radius of upward-check / downward-equivalent
+                           surfaces (2.95); must be < 3 */
+    double rcond;       /* pseudo-inverse cutoff: singular values below
+                           rcond * sigma_max are dropped (1e-7) */
+    double eps_svd;     /* M2L compression: rank k = number of singular
+                           values of the stacked M2L operators above
+                           eps_svd * sigma_max; 0 keeps them dense (1e-7) */
+    int32_t max_level;  /* deepest octree level, <= 16 (16) */
+    int32_t balance;    /* 1: refine to the 2:1 balance condition (1) */
+    int32_t m2l_mode;   /* fmm_m2l_mode (FMM_M2L_FP32) */
+    int32_t host_only;  /* 1: build tree, lists and operators on the host
+                           only; fmm_evaluate then returns
+                           FMM_ERR_INVALID_ARG.  For inspection. (0) */
+    int32_t device;     /* CUDA device ordinal; -1 = current device (-1) */
+    int32_t reserved[7];
+} fmm_options;
+
+void fmm_options_init(fmm_options *opts);
+
+/*
+ * Build a plan: octree, interaction lists, FP64 operator precomputation and
+ * the device copies the evaluation needs.
+ *
+ * sources  n x 3 row-major FP64 positions, host or device pointer (detected).
+ * targets  NULL or equal to sources: the targets are the sources, as in
+ *          Eq. (1).  Any other value returns FMM_ERR_UNSUPPORTED.
+ * n        number of points, >= 1.
+ * p        expansion order, 2 <= p <= 10 (surface points 6(p-1)^2 + 2).
+ * ncrit    largest number of points in a leaf before it is split, >= 1.
+ * out      receives the plan; untouched on failure.
+ *
+ * The plan copies what it needs; the caller keeps ownership of every
+ * pointer.  Synchronous with respect to the host.
+ */
+fmm_status fmm_plan_create(const double *sources, const double *targets,
+                           int64_t n, int p, int ncrit, fmm_plan_t *out);
+
+/* As fmm_plan_create, with options (NULL = defaults). */
+fmm_status fmm_plan_create_ex(const double *sources, const double *targets,
+                              int64_t n, int p, int ncrit,
+                              const fmm_options *opts, fmm_plan_t *out);
+
+/* Evaluation-time options that may change after creation. */
+enum {
+    FMM_OPT_M2L_MODE = 1 /* value: an fmm_m2l_mode */
+};
+fmm_status fmm_plan_set_option(fmm_plan_t plan, int key, double value);
+
+/*
+ * Evaluate potentials, Eq. (1), for nrhs charge vectors at once.
+ *
+ * charges     n x nrhs row-major FP32, in the caller's point order.
+ * nrhs        >= 1.
+ * potentials  n x nrhs row-major FP64, overwritten, caller's point order.
+ * stream      cudaStream_t (NULL = legacy default stream).
+ *
+ * If charges and potentials are both device pointers the call only enqueues
+ * work on `stream` and returns.  If either is a host pointer the library
+ * stages it through device memory on `stream` and returns after the stream
+ * has finished the evaluation.  A plan is not reentrant: do not overlap two
+ * evaluations of one plan.  Device-side failures are reported by the next
+ * call that synchronises.
+ */
+fmm_status fmm_evaluate(fmm_plan_t plan, const float *charges, int nrhs,
+                        double *potentials, void *stream);
+
+/* Destroy a plan and free its host and device memory.  NULL is a no-op. */
+void fmm_destroy(fmm_plan_t plan);
+
+/* Thread-local message describing the last failure on this thread. */
+const char *fmm_last_error(void);
+
+/* ---------------------------------------------------------------------
+ * Inspection (host data of a plan; used by tests and tools)
+ * ------------------------------------------------------------------- */
+
+/* Integer facts about a plan. */
+enum {
+    FMM_INFO_N = 0,           /* points */
+    FMM_INFO_NODES = 1,       /* boxes that hold points */
+    FMM_INFO_LEAVES = 2,      /* leaves that hold points */
+    FMM_INFO_DEPTH = 3,       /* deepest level */
+    FMM_INFO_NSURF = 4,       /* surface points per box, 6(p-1)^2 + 2 */
+    FMM_INFO_RANK_M2L = 5,    /* compressed M2L rank k */
+    FMM_INFO_RANK_UP = 6,     /* kept singular values of the upward
+                                 check-to-equivalent matrix */
+    FMM_INFO_RANK_DOWN = 7,   /* same, downward */
+    FMM_INFO_U_PAIRS = 8,     /* sum over leaves of |U| */
+    FMM_INFO_V_PAIRS = 9,     /* sum over boxes of |V| */
+    FMM_INFO_W_PAIRS = 10,    /* sum over leaves of |W| */
+    FMM_INFO_X_PAIRS = 11,    /* sum over boxes of |X| */
+    FMM_INFO_P2P_PAIRS = 12,  /* near-field (target, source) pairs */
+    FMM_INFO_M2L_TILES = 13,  /* M2L target tiles */
+    FMM_INFO_M2L_ENTRIES = 14,/* M2L (tile, offset) entries */
+    FMM_INFO_LAST_LAUNCHES = 15 /* kernels the last evaluation launched */
+};
+fmm_status fmm_plan_info(fmm_plan_t plan, int key, int64_t *value);
+
+/* Arrays a plan can export.  Sizes are in elements of the stated type. */
+enum {
+    FMM_ARRAY_NODE_KEYS = 0, /* int32 [nodes][4]: level, ix, iy, iz, in
+                                plan order (level, then Morton order) */
+    FMM_ARRAY_NODE_RANGE = 1,/* int64 [nodes][2]: first, end point index in
+                                the sorted order */
+    FMM_ARRAY_LEAF_FLAG = 2, /* int32 [nodes] */
+    FMM_ARRAY_PERM = 3,      /* int64 [n]: sorted position -> caller index */
+    FMM_ARRAY_U_PTR = 4,     /* int64 [nodes+1]: CSR offsets of U lists */
+    FMM_ARRAY_U_IDX = 5,     /* int32 [U pairs]: node indices */
+    FMM_ARRAY_V_PTR = 6,
+    FMM_ARRAY_V_IDX = 7,
+    FMM_ARRAY_W_PTR = 8,
+    FMM_ARRAY_W_IDX = 9,
+    FMM_ARRAY_X_PTR = 10,
+    FMM_ARRAY_X_IDX = 11,
+    FMM_ARRAY_SURFACE = 12,  /* double [nsurf][3] unit surface points */
+    FMM_ARRAY_M2L_U = 13,    /* double [nsurf][k]: left factor U_k */
+    FMM_ARRAY_M2L_V = 14,    /* double [nsurf][k]: right factor V_k */
+    FMM_ARRAY_M2L_S = 15,    /* double [316][k][k]: S_t = U_k^T K_t V_k,
+                                offsets t in lexicographic (tx,ty,tz) order
+                                over {-3..3}^3 minus {-1..1}^3 */
+    FMM_ARRAY_ROOT = 16      /* double [4]: root centre x, y, z, half-width */
+};
+/* Copy array `which` into dst (capacity `bytes`).  *needed receives the
+ * size in bytes (may be NULL).  dst == NULL only queries the size. */
+fmm_status fmm_plan_get_array(fmm_plan_t plan, int which, void *dst,
+                              int64_t bytes, int64_t *needed);
+
+/* Milliseconds each phase of the last evaluation took, measured with CUDA
+ * events on the evaluation stream when timing is on (FMM_TIMING=1 in the
+ * environment at plan creation).  phase: 0 upward, 1 M2L, 2 downward,
+ * 3 leaf evaluation.  Synchronises the plan's last stream. */
+fmm_status fmm_plan_phase_ms(fmm_plan_t plan, int phase, double *ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KIFMM_H */

@@ -1,0 +1,87 @@
+// Device-side views of a plan and the kernel launchers.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace kifmm {
+
+// Tree and lists on the device (all indices are node ids in plan order).
+struct DevTree {
+    int64_t n;
+    int nnodes, depth;
+    const float4 *pts;      // n: position relative to the leaf centre (root units)
+    const int64_t *perm;    // n: sorted position -> caller index
+    const float4 *geom;     // nodes: centre x, y, z (root units), half-width
+    const int2 *range;      // nodes: sorted point range [x, y)
+    const int *level;       // nodes
+    const int *parent;      // nodes
+    const int *child;       // nodes x 8
+    const int *leaves;      // nleaves
+    int nleaves;
+    const int *u_ptr, *u_idx, *w_ptr, *w_idx, *x_ptr, *x_idx, *v_ptr;
+    const int *x_slot;      // nodes: row block in the P2L buffer or -1
+};
+
+// FP32 operators.  Every matrix is stored as the transpose AT (n x m) of
+// the m x n operator A it applies, so that consecutive threads, which own
+// consecutive output rows i, read AT[j*m + i] coalesced.
+struct DevOps {
+    int ns, rP, rQ, k, kpad;
+    float ai, ao;
+    const float4 *surf;     // ns unit surface points
+    const float *Pu;        // AT of Pu^T:  ns x rP
+    const float *Ps_inv;    // rP
+    const float *PvT;       // AT of Pv:    rP x ns
+    const float *M2M;       // 8 x AT of M2M_sigma: ns x rP each
+    const float *Vk;        // AT of Vk^T:  ns x kpad (zero padded)
+    const float *QUkT;      // AT of Qu^T Uk: kpad x rQ (zero padded)
+    const float *Qu;        // AT of Qu^T:  ns x rQ
+    const float *L2L;       // 8 x AT of L2L_sigma: ns x rQ each
+    const float *Qs_inv;    // rQ
+    const float *QvT;       // AT of Qv:    rQ x ns
+    const float *St;        // 316 x kpad x kpad: St[t][j][i] = S_t[i][j]
+};
+
+// M2L tiles (see plan.h).
+struct DevM2L {
+    int ntiles;
+    const int *tile_target;     // ntiles x 128
+    const int *tile_entry_ptr;  // ntiles + 1
+    const int *entry_offset;    // entries
+    const int *entry_src;       // entries x 128
+};
+
+// Buffers of one evaluation.  Densities: [node][rhs][ns]; compressed M2L
+// vectors: [node][rhs][kpad]; P2L check potentials: [x slot][rhs][ns].
+struct DevWork {
+    int nrhs;
+    const float *charges_user;  // n x nrhs, caller order
+    float *qs;                  // n x nrhs, sorted order
+    float *up, *down;           // nodes x nrhs x ns
+    float *qhat, *chat;         // nodes x nrhs x kpad
+    float *xchk;                // x nodes x nrhs x ns
+    double *pot_user;           // n x nrhs, caller order
+    double scale;               // 1 / (4 pi root half-width)
+};
+
+cudaError_t launch_gather_charges(const DevTree &t, const DevWork &w, cudaStream_t s);
+cudaError_t launch_p2m(const DevTree &t, const DevOps &o, const DevWork &w,
+                       const int *nodes, int count, cudaStream_t s);
+cudaError_t launch_m2m(const DevTree &t, const DevOps &o, const DevWork &w,
+                       const int *nodes, int count, cudaStream_t s);
+cudaError_t launch_p2l(const DevTree &t, const DevOps &o, const DevWork &w,
+                       const int *nodes, int count, cudaStream_t s);
+cudaError_t launch_down(const DevTree &t, const DevOps &o, const DevWork &w,
+                        const int *chunks, const int *nodes, int nchunks,
+                        cudaStream_t s);
+cudaError_t launch_m2l_simt(const DevM2L &m, const DevOps &o, const DevWork &w,
+                            cudaStream_t s);
+cudaError_t launch_eval(const DevTree &t, const DevOps &o, const DevWork &w,
+                        cudaStream_t s);
+
+// Vectors (node x rhs pairs) handled per block by the matrix-vector kernels.
+constexpr int kMaxVec = 16;
+// Nodes per down-pass chunk (chunks never mix child positions).
+constexpr int kDownChunk = 16;
+
+} // namespace kifmm

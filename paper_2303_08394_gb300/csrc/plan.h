@@ -1,0 +1,129 @@
+// Internal host-side structures of a KIFMM plan.
+#pragma once
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "kifmm.h"
+
+namespace kifmm {
+
+// Number of M2L offsets: {-3..3}^3 minus {-1..1}^3.
+constexpr int kNumOffsets = 316;
+// Rows (targets) of one M2L tile.
+constexpr int kTileRows = 128;
+// Finest level representable by the 16-bit integer coordinates.
+constexpr int kKeyBits = 16;
+
+// Offset t = (tx, ty, tz) -> index 0..315 (lexicographic, tz fastest),
+// or -1 for |t|_inf <= 1 or out of range.
+int offset_index(int tx, int ty, int tz);
+
+// FP64 operators for the unit box (half-width 1, centre 0) and the kernel
+// 1/r.  All of them are level independent: the Laplace kernel is homogeneous
+// of degree -1, so a box of half-width h has K_h = K / h and its
+// pseudo-inverse h K^+, which cancel in every composite below.
+struct Operators {
+    int p = 0, ns = 0;                 // order, surface points 6(p-1)^2+2
+    double ai = 0, ao = 0, rcond = 0, eps_svd = 0;
+    std::vector<double> surf;          // ns x 3 unit surface
+    // Upward check-to-equivalent matrix K(ao s, ai s) = Pu diag(Ps) Pv^T,
+    // truncated to the rP singular values above rcond * sigma_max.
+    int rP = 0;
+    std::vector<double> Pu, Ps, Pv;    // ns x rP, rP, ns x rP
+    // Downward check-to-equivalent matrix K(ai s, ao s) = Qu diag(Qs) Qv^T.
+    int rQ = 0;
+    std::vector<double> Qu, Qs, Qv;    // ns x rQ, rQ, ns x rQ
+    // M2M: parent upward check potential of child sigma's density, already
+    // projected on Pu: 8 x (rP x ns) = Pu^T K(ao s, c_sigma + ai/2 s).
+    std::vector<double> M2M;
+    // L2L: child downward check potential from the parent's downward
+    // density, in child-normalised units and projected on Qu:
+    // 8 x (rQ x ns) = Qu^T (1/2) K(c_sigma + ai/2 s, ao s).
+    std::vector<double> L2L;
+    // M2L: K_t = K(ai s, 2t + ai s), t in the 316 offsets, compressed as
+    // K_t ~ Uk S_t Vk^T with Uk, Vk from the SVDs of [K_1 ... K_316] and
+    // [K_1; ...; K_316].  eps_svd == 0 keeps K_t dense (Uk = Vk = I).
+    int k = 0;
+    std::vector<double> Uk, Vk;        // ns x k
+    std::vector<double> S;             // 316 x k x k
+    std::vector<double> QUk;           // rQ x k = Qu^T Uk
+    std::vector<double> sigmaH, sigmaW;// singular values of the stacks
+};
+
+std::shared_ptr<const Operators> get_operators(int p, double ai, double ao,
+                                               double rcond, double eps_svd);
+
+// Octree over the (sorted) points plus interaction lists and schedules.
+struct Tree {
+    int64_t n = 0;
+    double centre[3] = {0, 0, 0}, hw = 0;   // root cube
+    int depth = 0;
+    std::vector<int64_t> perm;              // sorted position -> caller index
+    std::vector<float> rel;                 // n x 4: position relative to its
+                                            // leaf centre, root units, w = 0
+    // nodes that hold points, ordered by level then Morton key
+    std::vector<int32_t> key;               // nodes x 4 (level, ix, iy, iz)
+    std::vector<int64_t> begin, end;        // sorted point range
+    std::vector<int32_t> parent;            // -1 for the root
+    std::vector<int32_t> child;             // nodes x 8, -1 if absent
+    std::vector<uint8_t> leaf;
+    std::vector<int32_t> level_ptr;         // depth + 2 entries
+    std::vector<int32_t> leaves;            // node indices of leaves
+    // interaction lists, CSR over all nodes (sorted by node index)
+    std::vector<int64_t> u_ptr, v_ptr, w_ptr, x_ptr;
+    std::vector<int32_t> u_idx, v_idx, w_idx, x_idx;
+    std::vector<int16_t> v_off;             // offset index of each V entry
+    int64_t p2p_pairs = 0;
+
+    int64_t nodes() const { return (int64_t)parent.size(); }
+    double node_centre(int64_t node, int d) const;   // root units
+    double node_half_width(int64_t node) const;      // root units
+};
+
+struct TreeOptions {
+    int ncrit = 64;
+    int max_level = kKeyBits;
+    bool balance = true;
+};
+
+// Build the tree (throws std::runtime_error on bad input).
+void build_tree(const double *xyz, int64_t n, const TreeOptions &opt,
+                Tree &tree);
+// Fill U, V, W, X lists.
+void build_lists(Tree &tree);
+
+// M2L work decomposition: per level, targets grouped by parity class and
+// chunked into tiles of kTileRows; each tile lists the offsets any of its
+// targets uses and, per offset, the source node of every row (-1: none).
+struct M2LTable {
+    std::vector<int32_t> tile_level;      // tiles
+    std::vector<int32_t> tile_target;     // tiles x kTileRows (-1 pad)
+    std::vector<int32_t> tile_entry_ptr;  // tiles + 1
+    std::vector<int32_t> entry_offset;    // entries
+    std::vector<int32_t> entry_src;       // entries x kTileRows (-1 none)
+};
+void build_m2l_table(const Tree &tree, M2LTable &table);
+
+// Node schedules for the up and down passes.
+struct Schedules {
+    std::vector<int32_t> p2m_nodes;       // leaves at level >= 2
+    std::vector<int32_t> m2m_nodes;       // internal nodes, by level
+    std::vector<int32_t> m2m_level_ptr;   // depth + 2
+    std::vector<int32_t> down_nodes;      // nodes at level >= 2, by level,
+                                          // then child position, then order
+    std::vector<int32_t> down_level_ptr;  // depth + 2
+    std::vector<int32_t> down_chunk;      // chunks x 4: start, count, sigma,
+                                          // level (chunks never mix sigma)
+    std::vector<int32_t> down_chunk_level_ptr; // depth + 2
+    std::vector<int32_t> x_nodes;         // nodes with a non-empty X list
+    std::vector<int32_t> x_slot;          // nodes: slot in x_nodes or -1
+};
+void build_schedules(const Tree &tree, int chunk, Schedules &s);
+
+} // namespace kifmm
+
+// Host-side plan (the opaque fmm_plan_t).
+struct fmm_plan_s;

@@ -1,0 +1,461 @@
+// Linear octree, 2:1 balance and interaction lists ("The Fast Multipole
+// Method": root cube split into 8 equal children until a box holds at most
+// ncrit points; "Computational structure of FMM operators": U, V, W, X lists
+// and the balance condition; "Data-oriented design": nodes are ids in flat
+// arrays, points sorted so every box owns a contiguous range).
+//
+// Readings of what the paper leaves open:
+//  * root: smallest cube around all points, centred on the bounding box,
+//    half-width inflated by a relative 1e-6 (0.5 when all points coincide);
+//  * integer coordinate of a point: floor((x - corner) / (2 hw) * 2^16)
+//    clamped to [0, 2^16 - 1]; the box of level l holding it has index
+//    coordinate >> (16 - l), so a point on a split plane goes upward;
+//  * a split creates all 8 children, empty ones included, and the balance
+//    condition is enforced over all leaves; boxes without points are then
+//    dropped from every list and operator (their expansions are zero);
+//  * lists, for boxes holding points ("adjacent" = closed boxes touch):
+//    U(B) leaf: adjacent leaves, B included; V(B), level >= 2: children of
+//    the boxes adjacent to B's parent at the parent's level (the parent
+//    included) that are not adjacent to B; W(B) leaf: descendants of B's
+//    adjacent same-level boxes that are not adjacent to B but whose parent
+//    is; X(B) = {A : B in W(A)}.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <numeric>
+#include <stdexcept>
+
+#include "plan.h"
+
+namespace kifmm {
+
+namespace {
+
+inline uint64_t spread3(uint64_t v) {  // 16 bits -> every third bit
+    v &= 0xFFFF;
+    v = (v | (v << 16)) & 0x0000FF0000FFULL;
+    v = (v | (v << 8)) & 0x00F00F00F00FULL;
+    v = (v | (v << 4)) & 0x0C30C30C30C3ULL;
+    v = (v | (v << 2)) & 0x249249249249ULL;
+    return v;
+}
+inline uint64_t morton(uint32_t x, uint32_t y, uint32_t z) {
+    return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+}
+inline uint64_t pack(int l, int x, int y, int z) {
+    return ((uint64_t)l << 60) | ((uint64_t)(uint32_t)x << 40) |
+           ((uint64_t)(uint32_t)y << 20) | (uint64_t)(uint32_t)z;
+}
+
+struct BNode {        // construction node (empty boxes included)
+    int l, x, y, z;
+    int64_t b, e;     // sorted point range
+    int32_t first_child = -1;
+};
+
+// closed boxes touch or overlap
+inline bool adjacent(int la, int xa, int ya, int za, int lb, int xb, int yb,
+                     int zb) {
+    int L = std::max(la, lb);
+    int sa = L - la, sb = L - lb;
+    int64_t a[3] = {xa, ya, za}, b[3] = {xb, yb, zb};
+    for (int d = 0; d < 3; ++d) {
+        int64_t loa = a[d] << sa, hia = (a[d] + 1) << sa;
+        int64_t lob = b[d] << sb, hib = (b[d] + 1) << sb;
+        if (loa > hib || lob > hia) return false;
+    }
+    return true;
+}
+
+} // namespace
+
+double Tree::node_half_width(int64_t node) const {
+    return std::ldexp(1.0, -key[4 * node]);
+}
+double Tree::node_centre(int64_t node, int d) const {
+    int l = key[4 * node];
+    return -1.0 + (2.0 * key[4 * node + 1 + d] + 1.0) * std::ldexp(1.0, -l);
+}
+
+void build_tree(const double *xyz, int64_t n, const TreeOptions &opt,
+                Tree &t) {
+    if (n < 1) throw std::runtime_error("n must be >= 1");
+    if (opt.ncrit < 1) throw std::runtime_error("ncrit must be >= 1");
+    if (opt.max_level < 0 || opt.max_level > kKeyBits)
+        throw std::runtime_error("max_level must be in [0, 16]");
+    t = Tree();
+    t.n = n;
+    double lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) lo[d] = hi[d] = xyz[d];
+    for (int64_t i = 0; i < n; ++i)
+        for (int d = 0; d < 3; ++d) {
+            double v = xyz[3 * i + d];
+            if (!std::isfinite(v)) throw std::runtime_error("non-finite coordinate");
+            lo[d] = std::min(lo[d], v);
+            hi[d] = std::max(hi[d], v);
+        }
+    double ext = 0;
+    for (int d = 0; d < 3; ++d) {
+        t.centre[d] = 0.5 * (lo[d] + hi[d]);
+        ext = std::max(ext, hi[d] - lo[d]);
+    }
+    double hw = 0.5 * ext * (1.0 + 1e-6);
+    t.hw = hw > 0 ? hw : 0.5;
+    double corner[3];
+    for (int d = 0; d < 3; ++d) corner[d] = t.centre[d] - t.hw;
+
+    // integer coordinates and Morton order
+    std::vector<uint32_t> ic((size_t)3 * n);
+    std::vector<uint64_t> mk(n);
+    const double scale = (double)(1 << kKeyBits);
+    for (int64_t i = 0; i < n; ++i) {
+        for (int d = 0; d < 3; ++d) {
+            double u = (xyz[3 * i + d] - corner[d]) / (2.0 * t.hw);
+            double f = std::floor(u * scale);
+            int64_t k = (int64_t)f;
+            k = std::min<int64_t>(std::max<int64_t>(k, 0), (1 << kKeyBits) - 1);
+            ic[3 * i + d] = (uint32_t)k;
+        }
+        mk[i] = morton(ic[3 * i], ic[3 * i + 1], ic[3 * i + 2]);
+    }
+    t.perm.resize(n);
+    std::iota(t.perm.begin(), t.perm.end(), 0);
+    std::stable_sort(t.perm.begin(), t.perm.end(),
+                     [&](int64_t a, int64_t b) { return mk[a] < mk[b]; });
+    std::vector<uint64_t> smk(n);
+    for (int64_t i = 0; i < n; ++i) smk[i] = mk[t.perm[i]];
+
+    // construction tree (all 8 children of every split box)
+    std::vector<BNode> bn;
+    std::unordered_map<uint64_t, int32_t> where;
+    auto split = [&](int32_t id) {
+        BNode nd = bn[id];
+        int l = nd.l;
+        int shift = 3 * (kKeyBits - l - 1);
+        int32_t first = (int32_t)bn.size();
+        int64_t b = nd.b;
+        for (int c = 0; c < 8; ++c) {
+            // points of child c: digit at this level == c
+            int64_t e = b;
+            if (nd.e > nd.b) {
+                e = std::partition_point(smk.begin() + b, smk.begin() + nd.e,
+                                         [&](uint64_t k) { return (int)((k >> shift) & 7) <= c; }) -
+                    smk.begin();
+            }
+            BNode ch;
+            ch.l = l + 1;
+            ch.x = 2 * nd.x + (c & 1);
+            ch.y = 2 * nd.y + ((c >> 1) & 1);
+            ch.z = 2 * nd.z + ((c >> 2) & 1);
+            ch.b = b;
+            ch.e = e;
+            b = e;
+            where[pack(ch.l, ch.x, ch.y, ch.z)] = (int32_t)bn.size();
+            bn.push_back(ch);
+        }
+        bn[id].first_child = first;
+    };
+    BNode root;
+    root.l = root.x = root.y = root.z = 0;
+    root.b = 0;
+    root.e = n;
+    bn.push_back(root);
+    where[pack(0, 0, 0, 0)] = 0;
+    for (size_t i = 0; i < bn.size(); ++i) {
+        if (bn[i].e - bn[i].b > opt.ncrit && bn[i].l < opt.max_level) split((int32_t)i);
+    }
+    if (opt.balance) {
+        // A leaf at level l must split when an internal box at level l+1
+        // touches it.  After a split, the new children and the leaves one
+        // level up that touch the split box are examined again.
+        std::deque<int32_t> work;
+        for (size_t i = 0; i < bn.size(); ++i)
+            if (bn[i].first_child < 0) work.push_back((int32_t)i);
+        while (!work.empty()) {
+            int32_t id = work.front();
+            work.pop_front();
+            const BNode nd = bn[id];
+            if (nd.first_child >= 0 || nd.l >= opt.max_level) continue;
+            bool must = false;
+            for (int a = 2 * nd.x - 1; a <= 2 * nd.x + 2 && !must; ++a)
+                for (int b = 2 * nd.y - 1; b <= 2 * nd.y + 2 && !must; ++b)
+                    for (int c = 2 * nd.z - 1; c <= 2 * nd.z + 2 && !must; ++c) {
+                        if (a >> 1 == nd.x && b >> 1 == nd.y && c >> 1 == nd.z &&
+                            a >= 0 && b >= 0 && c >= 0)
+                            continue;
+                        if (a < 0 || b < 0 || c < 0) continue;
+                        auto it = where.find(pack(nd.l + 1, a, b, c));
+                        if (it != where.end() && bn[it->second].first_child >= 0) must = true;
+                    }
+            if (!must) continue;
+            split(id);
+            int32_t first = bn[id].first_child;
+            for (int c = 0; c < 8; ++c) work.push_back(first + c);
+            if (nd.l >= 1) {
+                int px = nd.x >> 1, py = nd.y >> 1, pz = nd.z >> 1;
+                for (int a = px - 1; a <= px + 1; ++a)
+                    for (int b = py - 1; b <= py + 1; ++b)
+                        for (int c = pz - 1; c <= pz + 1; ++c) {
+                            if (a < 0 || b < 0 || c < 0) continue;
+                            auto it = where.find(pack(nd.l - 1, a, b, c));
+                            if (it == where.end()) continue;
+                            const BNode &m = bn[it->second];
+                            if (m.first_child < 0 &&
+                                adjacent(m.l, m.x, m.y, m.z, nd.l, nd.x, nd.y, nd.z))
+                                work.push_back(it->second);
+                        }
+            }
+        }
+    }
+
+    // keep boxes holding points, ordered by level then Morton key
+    std::vector<int32_t> keep;
+    for (size_t i = 0; i < bn.size(); ++i)
+        if (bn[i].e > bn[i].b) keep.push_back((int32_t)i);
+    std::sort(keep.begin(), keep.end(), [&](int32_t a, int32_t b) {
+        if (bn[a].l != bn[b].l) return bn[a].l < bn[b].l;
+        return morton(bn[a].x, bn[a].y, bn[a].z) < morton(bn[b].x, bn[b].y, bn[b].z);
+    });
+    std::vector<int32_t> newid(bn.size(), -1);
+    for (size_t i = 0; i < keep.size(); ++i) newid[keep[i]] = (int32_t)i;
+    const int64_t nn = (int64_t)keep.size();
+    t.key.resize(4 * nn);
+    t.begin.resize(nn);
+    t.end.resize(nn);
+    t.parent.assign(nn, -1);
+    t.child.assign(8 * nn, -1);
+    t.leaf.assign(nn, 0);
+    t.depth = 0;
+    for (int64_t i = 0; i < nn; ++i) {
+        const BNode &nd = bn[keep[i]];
+        t.key[4 * i] = nd.l;
+        t.key[4 * i + 1] = nd.x;
+        t.key[4 * i + 2] = nd.y;
+        t.key[4 * i + 3] = nd.z;
+        t.begin[i] = nd.b;
+        t.end[i] = nd.e;
+        t.depth = std::max(t.depth, nd.l);
+        if (nd.first_child < 0) {
+            t.leaf[i] = 1;
+        } else {
+            bool any = false;
+            for (int c = 0; c < 8; ++c) {
+                int32_t ch = newid[nd.first_child + c];
+                t.child[8 * i + c] = ch;
+                if (ch >= 0) {
+                    t.parent[ch] = (int32_t)i;
+                    any = true;
+                }
+            }
+            if (!any) t.leaf[i] = 1;  // cannot happen for a box with points
+        }
+        if (t.leaf[i]) t.leaves.push_back((int32_t)i);
+    }
+    t.level_ptr.assign(t.depth + 2, 0);
+    for (int64_t i = 0; i < nn; ++i) t.level_ptr[t.key[4 * i] + 1]++;
+    for (int l = 0; l <= t.depth; ++l) t.level_ptr[l + 1] += t.level_ptr[l];
+
+    // point positions relative to their leaf centre, in root units
+    t.rel.assign((size_t)4 * n, 0.0f);
+    for (int32_t lf : t.leaves) {
+        double c[3];
+        for (int d = 0; d < 3; ++d) c[d] = t.node_centre(lf, d);
+        for (int64_t s = t.begin[lf]; s < t.end[lf]; ++s) {
+            int64_t i = t.perm[s];
+            for (int d = 0; d < 3; ++d)
+                t.rel[4 * s + d] = (float)((xyz[3 * i + d] - t.centre[d]) / t.hw - c[d]);
+        }
+    }
+}
+
+void build_lists(Tree &t) {
+    const int64_t nn = t.nodes();
+    std::unordered_map<uint64_t, int32_t> where;
+    where.reserve(nn * 2);
+    for (int64_t i = 0; i < nn; ++i)
+        where[pack(t.key[4 * i], t.key[4 * i + 1], t.key[4 * i + 2], t.key[4 * i + 3])] =
+            (int32_t)i;
+    auto K = [&](int32_t i, int d) { return t.key[4 * i + d]; };
+    auto adj = [&](int32_t a, int32_t b) {
+        return adjacent(K(a, 0), K(a, 1), K(a, 2), K(a, 3), K(b, 0), K(b, 1), K(b, 2), K(b, 3));
+    };
+    auto lookup = [&](int l, int x, int y, int z) -> int32_t {
+        if (x < 0 || y < 0 || z < 0) return -1;
+        auto it = where.find(pack(l, x, y, z));
+        return it == where.end() ? -1 : it->second;
+    };
+
+    std::vector<std::vector<int32_t>> U(nn), V(nn), W(nn), X(nn);
+    // U: descend from the root into every box touching the leaf
+    for (int32_t b : t.leaves) {
+        std::vector<int32_t> stack = {0};
+        while (!stack.empty()) {
+            int32_t nd = stack.back();
+            stack.pop_back();
+            if (!adj(nd, b)) continue;
+            if (t.leaf[nd]) {
+                U[b].push_back(nd);
+            } else {
+                for (int c = 0; c < 8; ++c)
+                    if (t.child[8 * nd + c] >= 0) stack.push_back(t.child[8 * nd + c]);
+            }
+        }
+        std::sort(U[b].begin(), U[b].end());
+    }
+    // V: children of the parent's colleagues, not adjacent
+    for (int64_t b = 0; b < nn; ++b) {
+        if (K(b, 0) < 2) continue;
+        int32_t par = t.parent[b];
+        int pl = K(par, 0), px = K(par, 1), py = K(par, 2), pz = K(par, 3);
+        for (int a = -1; a <= 1; ++a)
+            for (int c = -1; c <= 1; ++c)
+                for (int e = -1; e <= 1; ++e) {
+                    int32_t col = lookup(pl, px + a, py + c, pz + e);
+                    if (col < 0 || t.leaf[col]) continue;
+                    for (int s = 0; s < 8; ++s) {
+                        int32_t ch = t.child[8 * col + s];
+                        if (ch >= 0 && !adj(ch, (int32_t)b)) V[b].push_back(ch);
+                    }
+                }
+        std::sort(V[b].begin(), V[b].end());
+    }
+    // W (and X): descendants of the colleagues
+    for (int32_t b : t.leaves) {
+        int l = K(b, 0), x = K(b, 1), y = K(b, 2), z = K(b, 3);
+        for (int a = -1; a <= 1; ++a)
+            for (int c = -1; c <= 1; ++c)
+                for (int e = -1; e <= 1; ++e) {
+                    if (a == 0 && c == 0 && e == 0) continue;
+                    int32_t col = lookup(l, x + a, y + c, z + e);
+                    if (col < 0 || t.leaf[col]) continue;
+                    std::vector<int32_t> stack;
+                    for (int s = 0; s < 8; ++s)
+                        if (t.child[8 * col + s] >= 0) stack.push_back(t.child[8 * col + s]);
+                    while (!stack.empty()) {
+                        int32_t d = stack.back();
+                        stack.pop_back();
+                        if (!adj(d, b)) {
+                            W[b].push_back(d);
+                        } else if (!t.leaf[d]) {
+                            for (int s = 0; s < 8; ++s)
+                                if (t.child[8 * d + s] >= 0) stack.push_back(t.child[8 * d + s]);
+                        }
+                    }
+                }
+        std::sort(W[b].begin(), W[b].end());
+        for (int32_t a : W[b]) X[a].push_back(b);
+    }
+    for (auto &xs : X) std::sort(xs.begin(), xs.end());
+
+    auto to_csr = [&](std::vector<std::vector<int32_t>> &L, std::vector<int64_t> &ptr,
+                      std::vector<int32_t> &idx) {
+        ptr.assign(nn + 1, 0);
+        for (int64_t i = 0; i < nn; ++i) ptr[i + 1] = ptr[i] + (int64_t)L[i].size();
+        idx.resize(ptr[nn]);
+        for (int64_t i = 0; i < nn; ++i)
+            std::copy(L[i].begin(), L[i].end(), idx.begin() + ptr[i]);
+    };
+    to_csr(U, t.u_ptr, t.u_idx);
+    to_csr(V, t.v_ptr, t.v_idx);
+    to_csr(W, t.w_ptr, t.w_idx);
+    to_csr(X, t.x_ptr, t.x_idx);
+    t.v_off.resize(t.v_idx.size());
+    for (int64_t b = 0; b < nn; ++b)
+        for (int64_t e = t.v_ptr[b]; e < t.v_ptr[b + 1]; ++e) {
+            int32_t a = t.v_idx[e];
+            int o = offset_index(K(a, 1) - K(b, 1), K(a, 2) - K(b, 2), K(a, 3) - K(b, 3));
+            if (o < 0) throw std::runtime_error("internal: V entry outside the offset set");
+            t.v_off[e] = (int16_t)o;
+        }
+    t.p2p_pairs = 0;
+    for (int32_t b : t.leaves)
+        for (int64_t e = t.u_ptr[b]; e < t.u_ptr[b + 1]; ++e) {
+            int32_t a = t.u_idx[e];
+            t.p2p_pairs += (t.end[b] - t.begin[b]) * (t.end[a] - t.begin[a]);
+        }
+}
+
+void build_m2l_table(const Tree &t, M2LTable &m) {
+    m = M2LTable();
+    m.tile_entry_ptr.push_back(0);
+    for (int l = 2; l <= t.depth; ++l) {
+        for (int cls = 0; cls < 8; ++cls) {
+            std::vector<int32_t> targets;
+            for (int32_t b = t.level_ptr[l]; b < t.level_ptr[l + 1]; ++b) {
+                int c = (t.key[4 * b + 1] & 1) | ((t.key[4 * b + 2] & 1) << 1) |
+                        ((t.key[4 * b + 3] & 1) << 2);
+                if (c == cls && t.v_ptr[b + 1] > t.v_ptr[b]) targets.push_back(b);
+            }
+            for (size_t s = 0; s < targets.size(); s += kTileRows) {
+                size_t cnt = std::min<size_t>(kTileRows, targets.size() - s);
+                m.tile_level.push_back(l);
+                size_t tbase = m.tile_target.size();
+                m.tile_target.resize(tbase + kTileRows, -1);
+                std::vector<int32_t> src((size_t)kNumOffsets * kTileRows, -1);
+                std::vector<char> used(kNumOffsets, 0);
+                for (size_t r = 0; r < cnt; ++r) {
+                    int32_t b = targets[s + r];
+                    m.tile_target[tbase + r] = b;
+                    for (int64_t e = t.v_ptr[b]; e < t.v_ptr[b + 1]; ++e) {
+                        int o = t.v_off[e];
+                        src[(size_t)o * kTileRows + r] = t.v_idx[e];
+                        used[o] = 1;
+                    }
+                }
+                for (int o = 0; o < kNumOffsets; ++o) {
+                    if (!used[o]) continue;
+                    m.entry_offset.push_back(o);
+                    m.entry_src.insert(m.entry_src.end(), src.begin() + (size_t)o * kTileRows,
+                                       src.begin() + (size_t)(o + 1) * kTileRows);
+                }
+                m.tile_entry_ptr.push_back((int32_t)m.entry_offset.size());
+            }
+        }
+    }
+}
+
+void build_schedules(const Tree &t, int chunk, Schedules &s) {
+    s = Schedules();
+    for (int32_t lf : t.leaves)
+        if (t.key[4 * lf] >= 2) s.p2m_nodes.push_back(lf);
+    s.m2m_level_ptr.assign(t.depth + 2, 0);
+    s.down_level_ptr.assign(t.depth + 2, 0);
+    s.down_chunk_level_ptr.assign(t.depth + 2, 0);
+    for (int l = 0; l <= t.depth; ++l) {
+        s.m2m_level_ptr[l] = (int32_t)s.m2m_nodes.size();
+        if (l >= 2)
+            for (int32_t b = t.level_ptr[l]; b < t.level_ptr[l + 1]; ++b)
+                if (!t.leaf[b]) s.m2m_nodes.push_back(b);
+        s.down_level_ptr[l] = (int32_t)s.down_nodes.size();
+        s.down_chunk_level_ptr[l] = (int32_t)(s.down_chunk.size() / 4);
+        if (l >= 2) {
+            for (int sg = 0; sg < 8; ++sg) {
+                size_t start = s.down_nodes.size();
+                for (int32_t b = t.level_ptr[l]; b < t.level_ptr[l + 1]; ++b) {
+                    int c = (t.key[4 * b + 1] & 1) | ((t.key[4 * b + 2] & 1) << 1) |
+                            ((t.key[4 * b + 3] & 1) << 2);
+                    if (c == sg) s.down_nodes.push_back(b);
+                }
+                for (size_t p = start; p < s.down_nodes.size(); p += chunk) {
+                    int cnt = (int)std::min<size_t>(chunk, s.down_nodes.size() - p);
+                    s.down_chunk.push_back((int32_t)p);
+                    s.down_chunk.push_back(cnt);
+                    s.down_chunk.push_back(sg);
+                    s.down_chunk.push_back(l);
+                }
+            }
+        }
+    }
+    s.m2m_level_ptr[t.depth + 1] = (int32_t)s.m2m_nodes.size();
+    s.down_level_ptr[t.depth + 1] = (int32_t)s.down_nodes.size();
+    s.down_chunk_level_ptr[t.depth + 1] = (int32_t)(s.down_chunk.size() / 4);
+    s.x_slot.assign(t.nodes(), -1);
+    for (int64_t b = 0; b < t.nodes(); ++b)
+        if (t.x_ptr[b + 1] > t.x_ptr[b]) {
+            s.x_slot[b] = (int32_t)s.x_nodes.size();
+            s.x_nodes.push_back((int32_t)b);
+        }
+}
+
+} // namespace kifmm

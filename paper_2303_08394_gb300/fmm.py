@@ -1,0 +1,134 @@
+"""Python face of the C ABI: one plan per point cloud, evaluations on it.
+
+Only argument marshalling happens here; every step of an evaluation runs in
+libkifmm.so's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native as N
+
+
+def _ptr(a):
+    """Raw address of a numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+class FMMPlan:
+    """A KIFMM plan over n points (sources are also the targets, Eq. (1)).
+
+    points: (n, 3) float64, numpy (host) or torch tensor (host or CUDA).
+    p: expansion order; ncrit: largest leaf before a split.
+    Options (see include/kifmm.h): alpha_inner, alpha_outer, rcond, eps_svd,
+    max_level, balance, m2l_mode, host_only, device.
+    """
+
+    def __init__(self, points, p: int, ncrit: int, **options):
+        L = N.lib()
+        opts = N.Options()
+        L.fmm_options_init(ctypes.byref(opts))
+        for k, v in options.items():
+            if not hasattr(opts, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(opts, k, v)
+        if isinstance(points, np.ndarray):
+            pts = np.ascontiguousarray(points, dtype=np.float64)
+            if pts.ndim != 2 or pts.shape[1] != 3:
+                raise ValueError("points must be (n, 3)")
+        else:
+            pts = points.contiguous()
+            if str(pts.dtype) != "torch.float64" or pts.dim() != 2 or pts.shape[1] != 3:
+                raise ValueError("points must be a (n, 3) float64 tensor")
+        self._keep = pts
+        self.n = int(pts.shape[0])
+        self.p, self.ncrit = p, ncrit
+        self.host_only = bool(options.get("host_only", 0))
+        h = ctypes.c_void_p()
+        N.check(L.fmm_plan_create_ex(_ptr(pts), None, self.n, p, ncrit, ctypes.byref(opts),
+                                     ctypes.byref(h)))
+        self._h = h
+
+    # ---------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            N.lib().fmm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---------------------------------------------------------------
+    def set_m2l_mode(self, mode: int):
+        N.check(N.lib().fmm_plan_set_option(self._h, N.OPT_M2L_MODE, float(mode)))
+
+    def evaluate(self, charges, out=None, stream=None):
+        """Potentials (n, nrhs) float64 for charges (n,) or (n, nrhs) float32.
+
+        Torch CUDA tensors: the work is enqueued on ``stream`` (default: the
+        current torch stream) and the call returns at once.  Numpy arrays:
+        the library stages them through device memory and returns when done.
+        """
+        if isinstance(charges, np.ndarray):
+            q = np.ascontiguousarray(charges, dtype=np.float32)
+            vec = q.ndim == 1
+            q = q.reshape(self.n, -1)
+            nrhs = q.shape[1]
+            if out is None:
+                out = np.empty((self.n, nrhs), dtype=np.float64)
+            st = 0 if stream is None else int(stream)
+            N.check(N.lib().fmm_evaluate(self._h, q.ctypes.data, nrhs, out.ctypes.data,
+                                         ctypes.c_void_p(st)))
+            return out[:, 0] if vec else out
+        import torch
+        q = charges
+        if q.dtype != torch.float32:
+            raise TypeError("charges must be float32")
+        vec = q.dim() == 1
+        q = q.reshape(self.n, -1).contiguous()
+        nrhs = q.shape[1]
+        if out is None:
+            out = torch.empty((self.n, nrhs), dtype=torch.float64, device=q.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(q.device) if q.is_cuda else None
+        st = 0 if stream is None else stream.cuda_stream
+        N.check(N.lib().fmm_evaluate(self._h, q.data_ptr(), nrhs, out.data_ptr(),
+                                     ctypes.c_void_p(st)))
+        return out[:, 0] if vec else out
+
+    # ---------------------------------------------------------------
+    def info(self, key: str) -> int:
+        v = ctypes.c_int64()
+        N.check(N.lib().fmm_plan_info(self._h, N.INFO[key], ctypes.byref(v)))
+        return v.value
+
+    def array(self, name: str) -> np.ndarray:
+        which, dt = N.ARRAYS[name]
+        need = ctypes.c_int64()
+        N.check(N.lib().fmm_plan_get_array(self._h, which, None, 0, ctypes.byref(need)))
+        out = np.empty(need.value // np.dtype(dt).itemsize, dtype=dt)
+        N.check(N.lib().fmm_plan_get_array(self._h, which, out.ctypes.data, need.value,
+                                           ctypes.byref(need)))
+        return out
+
+    def phase_ms(self):
+        """Per-phase milliseconds of the last evaluation (needs FMM_TIMING=1)."""
+        out = []
+        for ph in range(4):
+            v = ctypes.c_double()
+            N.check(N.lib().fmm_plan_phase_ms(self._h, ph, ctypes.byref(v)))
+            out.append(v.value)
+        return dict(zip(("upward", "m2l", "downward", "leaf"), out))

@@ -1,0 +1,157 @@
+"""C-ABI host logic, no GPU needed: the library loads and exports every
+declared symbol; host-only plans build the same octree, point partition and
+U/V/W/X lists as the oracle (bit-exact: this is index work); the FP64
+operators are consistent with the oracle's kernel matrices; invalid
+arguments come back as status codes."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import kifmm as ok
+from paper_2303_08394_gb300 import FMMPlan, _native as N
+from paper_2303_08394_gb300 import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2303_08394_gb300 import build
+    build.build()
+
+
+def test_exports_every_declared_symbol():
+    header = open(os.path.join(ROOT, "include", "kifmm.h")).read()
+    declared = set(re.findall(r"\b(fmm_[a-z_]+)\s*\(", header))
+    assert declared == set(N.EXPORTS)
+    lib = ctypes.CDLL(N.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def _plan_keys(P):
+    keys = P.array("node_keys").reshape(-1, 4)
+    return [tuple(int(v) for v in k) for k in keys]
+
+
+def _csr(P, name, keys):
+    ptr = P.array(name + "_ptr")
+    idx = P.array(name + "_idx")
+    out = {}
+    for b in range(len(keys)):
+        if ptr[b + 1] > ptr[b]:
+            out[keys[b]] = sorted(keys[i] for i in idx[ptr[b]:ptr[b + 1]])
+    return out
+
+
+CASES = [("cube", 4000, 24, True), ("sphere", 3000, 8, True), ("gauss", 3000, 8, True),
+         ("sphere", 3000, 8, False), ("gauss", 2500, 5, False)]
+
+
+@pytest.mark.parametrize("kind,n,ncrit,balance", CASES)
+def test_tree_and_lists_match_oracle(kind, n, ncrit, balance):
+    gen = {"cube": wl.uniform_cube, "sphere": wl.sphere_surface,
+           "gauss": wl.gaussian_mixture}[kind]
+    x, _ = gen(n, 31)
+    P = FMMPlan(x, 4, ncrit, host_only=1, balance=int(balance))
+    tree = ok.Octree(x, ncrit, balance=balance)
+    U, V, W, X = ok.build_lists(tree)
+    keys = _plan_keys(P)
+    assert set(keys) == tree.nonempty
+    assert len(keys) == len(set(keys))
+    leaf = P.array("leaf_flag")
+    assert {k for k, f in zip(keys, leaf) if f} == set(tree.leaves)
+    # point partition: the sorted range of every box holds the oracle's points
+    rng = P.array("node_range").reshape(-1, 2)
+    perm = P.array("perm")
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    for k, (a, b) in zip(keys, rng):
+        assert np.array_equal(np.sort(perm[a:b]), np.sort(tree.points[k]))
+    for name, ref in (("u", U), ("v", V), ("w", W), ("x", X)):
+        got = _csr(P, name, keys)
+        assert got == {k: sorted(v) for k, v in ref.items()}, name
+    root = P.array("root")
+    np.testing.assert_array_equal(root[:3], tree.centre)
+    assert root[3] == tree.half_width
+
+
+def test_counts_of_the_uniform_workload():
+    x, _ = wl.uniform_cube(10_000, 0)
+    P = FMMPlan(x, 4, 64, host_only=1)
+    assert P.info("depth") == 3 and P.info("leaves") == 512 and P.info("nodes") == 585
+    assert P.info("v_pairs") == 56_448
+    assert P.info("w_pairs") == 0 and P.info("x_pairs") == 0
+    assert P.info("nsurf") == 56
+
+
+@pytest.mark.parametrize("p", [4, 6])
+def test_operators_against_oracle_kernel(p):
+    x, _ = wl.uniform_cube(500, 1)
+    P = FMMPlan(x, p, 64, host_only=1)
+    surf = P.array("surface").reshape(-1, 3)
+    np.testing.assert_array_equal(surf, ok.surface_grid(p))
+    k = P.info("rank_m2l")
+    ns = len(surf)
+    Uk = P.array("m2l_u").reshape(ns, k)
+    Vk = P.array("m2l_v").reshape(ns, k)
+    S = P.array("m2l_s").reshape(316, k, k)
+    np.testing.assert_allclose(Uk.T @ Uk, np.eye(k), atol=1e-10)
+    np.testing.assert_allclose(Vk.T @ Vk, np.eye(k), atol=1e-10)
+    offs = [(a, b, c) for a in range(-3, 4) for b in range(-3, 4) for c in range(-3, 4)
+            if max(abs(a), abs(b), abs(c)) > 1]
+    assert len(offs) == 316
+    worst = 0.0
+    for i, t in enumerate(offs):
+        kt = 4 * np.pi * ok.laplace_kernel(1.05 * surf, 2.0 * np.array(t) + 1.05 * surf)
+        err = np.linalg.norm(Uk @ S[i] @ Vk.T - kt) / np.linalg.norm(kt)
+        worst = max(worst, err)
+    assert worst < 50 * 1e-7, worst
+
+
+def test_dense_m2l_option_keeps_full_rank():
+    x, _ = wl.uniform_cube(300, 2)
+    P = FMMPlan(x, 4, 32, host_only=1, eps_svd=0.0)
+    assert P.info("rank_m2l") == 56
+    S = P.array("m2l_s").reshape(316, 56, 56)
+    surf = ok.surface_grid(4)
+    kt = 4 * np.pi * ok.laplace_kernel(1.05 * surf, np.array([-3.0, -3.0, -3.0]) * 2 + 1.05 * surf)
+    np.testing.assert_allclose(S[0], kt, rtol=1e-13)
+
+
+def test_invalid_arguments():
+    x, _ = wl.uniform_cube(10, 3)
+    with pytest.raises(N.FMMError) as e:
+        FMMPlan(x[:0], 4, 8, host_only=1)
+    assert e.value.status == N.FMM_ERR_INVALID_ARG
+    with pytest.raises(N.FMMError):
+        FMMPlan(x, 1, 8, host_only=1)
+    with pytest.raises(N.FMMError):
+        FMMPlan(x, 4, 0, host_only=1)
+    with pytest.raises(N.FMMError):
+        FMMPlan(x, 4, 8, host_only=1, alpha_outer=3.0)
+    bad = x.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(N.FMMError):
+        FMMPlan(bad, 4, 8, host_only=1)
+    L = N.lib()
+    h = ctypes.c_void_p()
+    pts = np.ascontiguousarray(x)
+    other = pts.copy()
+    st = L.fmm_plan_create(pts.ctypes.data, other.ctypes.data, 10, 4, 8, ctypes.byref(h))
+    assert st == N.FMM_ERR_UNSUPPORTED
+    assert b"targets" in L.fmm_last_error()
+    P = FMMPlan(x, 4, 8, host_only=1)
+    with pytest.raises(N.FMMError):
+        P.evaluate(np.ones(10, dtype=np.float32))
+    L.fmm_destroy(None)
+
+
+def test_single_point_and_duplicates():
+    P = FMMPlan(np.array([[0.3, 0.2, 0.1]]), 4, 1, host_only=1)
+    assert P.info("nodes") == 1 and P.info("leaves") == 1 and P.info("depth") == 0
+    x = np.zeros((40, 3))
+    P = FMMPlan(x, 4, 8, host_only=1, max_level=5)
+    assert P.info("depth") == 5

@@ -1,0 +1,152 @@
+"""GPU parity: the CUDA path against the FP64 oracle, through the C ABI.
+
+Bars (FP32 path):
+* against the oracle KIFMM run with the same p, radii and pseudo-inverse
+  cutoff: relative L2 error <= 1e-6;
+* against the FP64 direct sum: error <= 1.5x the oracle KIFMM's own error
+  at the same p;
+* column r of an nrhs evaluation equals the single-vector evaluation of
+  charges[:, r] bit for bit (same FP32 operations in the same order).
+"""
+import numpy as np
+import pytest
+
+from oracle.direct import direct_sum
+from oracle.kifmm import KIFMM
+from paper_2303_08394_gb300 import FMMPlan
+from paper_2303_08394_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2303_08394_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def gpu_eval(plan, q):
+    qd = torch.as_tensor(np.asarray(q, dtype=np.float32), device="cuda")
+    out = plan.evaluate(qd)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+CASES = [
+    # name, generator, n, p, ncrit
+    ("cube10k_p4", wl.uniform_cube, 10_000, 4, 64),
+    ("cube12k_p6", wl.uniform_cube, 12_000, 6, 48),
+    ("sphere8k_p5", wl.sphere_surface, 8_000, 5, 16),
+    ("gauss8k_p6", wl.gaussian_mixture, 8_000, 6, 24),
+    ("sphere6k_p7", wl.sphere_surface, 6_000, 7, 32),
+]
+
+
+@pytest.mark.parametrize("name,gen,n,p,ncrit", CASES, ids=[c[0] for c in CASES])
+def test_fmm_matches_oracle(name, gen, n, p, ncrit):
+    x, q = gen(n, 41)
+    q = q[:, 0]
+    plan = FMMPlan(x, p, ncrit)
+    phi = gpu_eval(plan, q)[:, 0]
+    ora = KIFMM(x, p, ncrit)
+    phi_o = ora.evaluate(q)
+    ref = direct_sum(x, q)
+    e_gpu_ora = rel(phi, phi_o)
+    e_gpu, e_ora = rel(phi, ref), rel(phi_o, ref)
+    assert e_gpu_ora <= 1e-6, (e_gpu_ora, e_gpu, e_ora)
+    assert e_gpu <= 1.5 * e_ora, (e_gpu, e_ora)
+    # the lists the GPU ran on are the oracle's lists
+    assert plan.info("v_pairs") == sum(len(v) for v in ora.V.values())
+    assert plan.info("u_pairs") == sum(len(v) for v in ora.U.values())
+
+
+@pytest.mark.parametrize("nrhs", [3, 8, 21])
+def test_nrhs_columns_equal_single_vector(nrhs):
+    x, q = wl.gaussian_mixture(5000, 42, nrhs=nrhs)
+    plan = FMMPlan(x, 5, 20)
+    multi = gpu_eval(plan, q)
+    for r in (0, nrhs // 2, nrhs - 1):
+        single = gpu_eval(plan, q[:, r])[:, 0]
+        np.testing.assert_array_equal(multi[:, r], single)
+
+
+def test_single_leaf_equals_direct_sum():
+    x, q = wl.uniform_cube(120, 43)
+    plan = FMMPlan(x, 4, 200)
+    assert plan.info("depth") == 0
+    phi = gpu_eval(plan, q[:, 0])[:, 0]
+    ref = direct_sum(x, q[:, 0])
+    assert rel(phi, ref) < 1e-6
+
+
+def test_one_point_and_coincident_points():
+    plan = FMMPlan(np.array([[0.5, 0.5, 0.5]]), 4, 8)
+    assert gpu_eval(plan, [2.0])[0, 0] == 0.0
+    x, q = wl.uniform_cube(3000, 44)
+    x[10] = x[11]
+    x[200:205] = x[300]
+    plan = FMMPlan(x, 5, 16)
+    phi = gpu_eval(plan, q[:, 0])[:, 0]
+    ref = direct_sum(x, q[:, 0])
+    ora = KIFMM(x, 5, 16).evaluate(q[:, 0])
+    assert rel(phi, ora) < 1e-6
+    assert np.all(np.isfinite(phi))
+
+
+def test_ragged_tiles_and_deep_tree():
+    """Adaptive tree with many levels, partly filled M2L tiles and W/X lists."""
+    x, q = wl.gaussian_mixture(7000, 45)
+    x = np.concatenate([x, 0.5 + 1e-4 * np.random.default_rng(0).standard_normal((300, 3))])
+    q = np.concatenate([q[:, 0], np.ones(300)])
+    plan = FMMPlan(x, 4, 6)
+    assert plan.info("depth") >= 9
+    assert plan.info("w_pairs") > 0 and plan.info("x_pairs") > 0
+    phi = gpu_eval(plan, q)[:, 0]
+    ora = KIFMM(x, 4, 6).evaluate(q)
+    assert rel(phi, ora) < 1e-6
+
+
+def test_host_buffers_match_device_buffers():
+    x, q = wl.uniform_cube(6000, 46, nrhs=2)
+    plan = FMMPlan(x, 4, 32)
+    dev = gpu_eval(plan, q)
+    host = plan.evaluate(np.asarray(q, dtype=np.float32))
+    np.testing.assert_array_equal(host, dev)
+    pinned_q = torch.tensor(np.asarray(q, dtype=np.float32)).pin_memory()
+    pinned_out = torch.empty((len(x), 2), dtype=torch.float64).pin_memory()
+    plan.evaluate(pinned_q, out=pinned_out)
+    np.testing.assert_array_equal(pinned_out.numpy(), dev)
+
+
+def test_evaluate_on_a_side_stream_and_repeat():
+    x, q = wl.uniform_cube(8000, 47)
+    plan = FMMPlan(x, 4, 40)
+    qd = torch.as_tensor(q[:, 0].astype(np.float32), device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        a = plan.evaluate(qd)
+        b = plan.evaluate(qd)
+    s.synchronize()
+    np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+    assert plan.info("last_launches") >= 5
+
+
+@pytest.mark.slow
+def test_million_point_workload_sampled_against_direct_sum():
+    """The 10^6-point uniform workload at p=6, ncrit=150 (the benchmark's
+    workload and launch configuration): relative L2 error on 1,000 sampled
+    targets against the FP64 direct sum stays within 1e-5."""
+    w = wl.CUBE_1M_P6
+    x, q = w.generate(0)
+    plan = FMMPlan(x, w.p, w.ncrit)
+    phi = gpu_eval(plan, q[:, 0])[:, 0]
+    idx = wl.sample_targets(w.n, w.error_samples, 0)
+    # the zero-distance self pair is skipped, so these are Eq. (1) potentials
+    ref = direct_sum(x, q[:, 0], targets=x[idx])
+    assert rel(phi[idx], ref) <= 1e-5
