@@ -3,6 +3,14 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "constants.h"
+
+// Reciprocal square root used by every kernel evaluation 1/r (MUFU rsqrt,
+// <= 2 ulp).  A build may define KIFMM_RSQRT to trade speed for rounding.
+#ifndef KIFMM_RSQRT
+#define KIFMM_RSQRT(x) rsqrtf(x)
+#endif
+
 namespace kifmm {
 
 // Tree and lists on the device (all indices are node ids in plan order).
@@ -80,8 +88,10 @@ cudaError_t launch_eval(const DevTree &t, const DevOps &o, const DevWork &w,
                         cudaStream_t s);
 
 // Vectors (node x rhs pairs) handled per block by the matrix-vector kernels.
-constexpr int kMaxVec = 16;
+constexpr int kMaxVec = 32;
+// Right-hand sides handled per block by the point-evaluation kernels.
+constexpr int kMaxRhs = 16;
 // Nodes per down-pass chunk (chunks never mix child positions).
-constexpr int kDownChunk = 16;
+constexpr int kDownChunk = 32;
 
 } // namespace kifmm

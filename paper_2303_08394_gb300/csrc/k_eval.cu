@@ -39,7 +39,7 @@ __device__ __forceinline__ void batch(const float4 *spos, const float (*sq)[32],
         const float4 p = spos[j];
         const float dx = p.x - tx, dy = p.y - ty, dz = p.z - tz;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+        const float inv = r2 > 0.f ? KIFMM_RSQRT(r2) : 0.f;
         if (NR == 1) {
             part[0] = fmaf(p.w, inv, part[0]);
         } else {

@@ -1,15 +1,19 @@
 // V-list M2L in FP32 on the CUDA cores ("Computational structure of FMM
 // operators": M2L over V is a matrix-vector product per (target, source)
-// pair; here the products of one tile of 128 targets and one offset t are
-// batched into a 128 x k by k x k product).
+// pair; here the products of one tile of targets and one offset t are
+// batched into a rows x k by k x k product).
 //
 // chat[target] = sum_{A in V(target)} S_t(A,target) qhat[A]
 //
-// A block owns 128 rows (target, rhs) of one tile.  For every offset the
-// tile uses it gathers the 128 source vectors (zero where a target has no
-// source at that offset) and multiplies them by S_t, accumulating in
-// registers: thread (tr, tc) holds rows 8 tr .. 8 tr + 7 and columns
-// tc + 16 c.
+// A block owns 16*RPT rows (target, rhs) of one tile.  For every offset the
+// tile uses it gathers the source vectors (zero where a target has no source
+// at that offset) and multiplies them by S_t.  Thread (tr, tc) holds rows
+// RPT*tr .. RPT*tr + RPT - 1 and columns tc + 16 c.
+//
+// Summation order: each offset's product is summed in a fresh partial and
+// then added to the running total.  One accumulator over all ~189 k terms
+// of a target loses about 5x more accuracy in FP32 (the far field then
+// misses the 1e-6 bar against the FP64 oracle).
 #include "device.cuh"
 
 namespace kifmm {
@@ -18,19 +22,20 @@ namespace {
 
 constexpr int kKc = 16;  // K chunk
 
-template <int CPT>
+template <int CPT, int RPT>
 __global__ void __launch_bounds__(256) k_m2l_simt(DevM2L m, DevOps o, DevWork w) {
-    __shared__ float xs[kKc][128 + 4];
+    constexpr int RB = 16 * RPT;  // rows per block
+    __shared__ __align__(16) float xs[kKc][RB + 4];
     __shared__ __align__(16) float ss[kKc][16 * CPT];
-    __shared__ int rowsrc[128];
+    __shared__ int rowsrc[RB];
     const int tile = blockIdx.x;
     const int chunk = blockIdx.y;
     const int kp = o.kpad;  // == 16 * CPT
     const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
     const int nrhs = w.nrhs;
-    float acc[8][CPT];
+    float acc[RPT][CPT], part[RPT][CPT];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < RPT; ++i)
 #pragma unroll
         for (int c = 0; c < CPT; ++c) acc[i][c] = 0.f;
 
@@ -38,30 +43,38 @@ __global__ void __launch_bounds__(256) k_m2l_simt(DevM2L m, DevOps o, DevWork w)
     for (int e = e0; e < e1; ++e) {
         const int off = m.entry_offset[e];
         __syncthreads();
-        if (tid < 128) {
-            const int g = chunk * 128 + tid;
+        if (tid < RB) {
+            const int g = chunk * RB + tid;
             const int slot = g / nrhs, r = g - slot * nrhs;
-            const int src = m.entry_src[(size_t)e * 128 + slot];
+            int src = -1;
+            if (slot < kTileRows) src = m.entry_src[(size_t)e * kTileRows + slot];
             rowsrc[tid] = src >= 0 ? src * nrhs + r : -1;
         }
+#pragma unroll
+        for (int i = 0; i < RPT; ++i)
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) part[i][c] = 0.f;
         const float *St = o.St + (size_t)off * kp * kp;
         for (int kc = 0; kc < kp; kc += kKc) {
             __syncthreads();
-            {   // gather 128 rows x 16 columns of qhat, stored transposed
-                const int row = tid >> 1, half = tid & 1;
+            {   // gather RB rows x 16 columns of qhat, stored transposed
+                constexpr int PER = kKc * RB / 256;  // floats per thread: 8 or 4
+                const int row = tid / (kKc / PER), part_c = (tid % (kKc / PER)) * PER;
                 const int rs = rowsrc[row];
-                float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+                float v[PER];
+#pragma unroll
+                for (int q = 0; q < PER; ++q) v[q] = 0.f;
                 if (rs >= 0) {
                     const float4 *src = reinterpret_cast<const float4 *>(
-                        w.qhat + (size_t)rs * kp + kc + half * 8);
-                    a = __ldg(src);
-                    b = __ldg(src + 1);
+                        w.qhat + (size_t)rs * kp + kc + part_c);
+#pragma unroll
+                    for (int q = 0; q < PER / 4; ++q) {
+                        const float4 a = __ldg(src + q);
+                        v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+                    }
                 }
-                const int c0 = half * 8;
-                xs[c0 + 0][row] = a.x; xs[c0 + 1][row] = a.y;
-                xs[c0 + 2][row] = a.z; xs[c0 + 3][row] = a.w;
-                xs[c0 + 4][row] = b.x; xs[c0 + 5][row] = b.y;
-                xs[c0 + 6][row] = b.z; xs[c0 + 7][row] = b.w;
+#pragma unroll
+                for (int q = 0; q < PER; ++q) xs[part_c + q][row] = v[q];
             }
             // 16 rows of St (j = kc..kc+15), all kp columns
             for (int idx = tid; idx < kKc * kp / 4; idx += 256) {
@@ -72,25 +85,31 @@ __global__ void __launch_bounds__(256) k_m2l_simt(DevM2L m, DevOps o, DevWork w)
             __syncthreads();
 #pragma unroll
             for (int kk = 0; kk < kKc; ++kk) {
-                float a[8], bcol[CPT];
-                const float4 a0 = *reinterpret_cast<const float4 *>(&xs[kk][tr * 8]);
-                const float4 a1 = *reinterpret_cast<const float4 *>(&xs[kk][tr * 8 + 4]);
-                a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
-                a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+                float a[RPT], bcol[CPT];
+#pragma unroll
+                for (int q = 0; q < RPT / 4; ++q) {
+                    const float4 a4 = *reinterpret_cast<const float4 *>(&xs[kk][tr * RPT + 4 * q]);
+                    a[4 * q] = a4.x; a[4 * q + 1] = a4.y; a[4 * q + 2] = a4.z; a[4 * q + 3] = a4.w;
+                }
 #pragma unroll
                 for (int c = 0; c < CPT; ++c) bcol[c] = ss[kk][tc + 16 * c];
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
+                for (int i = 0; i < RPT; ++i)
 #pragma unroll
-                    for (int c = 0; c < CPT; ++c) acc[i][c] = fmaf(a[i], bcol[c], acc[i][c]);
+                    for (int c = 0; c < CPT; ++c) part[i][c] = fmaf(a[i], bcol[c], part[i][c]);
             }
         }
+#pragma unroll
+        for (int i = 0; i < RPT; ++i)
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) acc[i][c] += part[i][c];
     }
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int g = chunk * 128 + tr * 8 + i;
+    for (int i = 0; i < RPT; ++i) {
+        const int g = chunk * RB + tr * RPT + i;
         const int slot = g / nrhs, r = g - slot * nrhs;
-        const int tgt = m.tile_target[(size_t)tile * 128 + slot];
+        if (slot >= kTileRows) continue;
+        const int tgt = m.tile_target[(size_t)tile * kTileRows + slot];
         if (tgt < 0) continue;
         float *out = w.chat + ((size_t)tgt * nrhs + r) * kp;
 #pragma unroll
@@ -100,8 +119,11 @@ __global__ void __launch_bounds__(256) k_m2l_simt(DevM2L m, DevOps o, DevWork w)
 
 template <int CPT>
 cudaError_t launch_cpt(const DevM2L &m, const DevOps &o, const DevWork &w, cudaStream_t s) {
-    dim3 grid(m.ntiles, w.nrhs);
-    k_m2l_simt<CPT><<<grid, 256, 0, s>>>(m, o, w);
+    constexpr int RPT = CPT <= 12 ? 8 : 4;
+    constexpr int RB = 16 * RPT;
+    const int rows = kTileRows * w.nrhs;
+    dim3 grid(m.ntiles, (rows + RB - 1) / RB);
+    k_m2l_simt<CPT, RPT><<<grid, 256, 0, s>>>(m, o, w);
     return cudaGetLastError();
 }
 

@@ -6,16 +6,10 @@
 #include <unordered_map>
 #include <vector>
 
+#include "constants.h"
 #include "kifmm.h"
 
 namespace kifmm {
-
-// Number of M2L offsets: {-3..3}^3 minus {-1..1}^3.
-constexpr int kNumOffsets = 316;
-// Rows (targets) of one M2L tile.
-constexpr int kTileRows = 128;
-// Finest level representable by the 16-bit integer coordinates.
-constexpr int kKeyBits = 16;
 
 // Offset t = (tx, ty, tz) -> index 0..315 (lexicographic, tz fastest),
 // or -1 for |t|_inf <= 1 or out of range.

@@ -32,7 +32,9 @@ def built():
 
 
 def gpu_eval(plan, q):
-    qd = torch.as_tensor(np.asarray(q, dtype=np.float32), device="cuda")
+    """Evaluate through the C ABI with device buffers; returns (n, nrhs)."""
+    q = np.asarray(q, dtype=np.float32)
+    qd = torch.as_tensor(q.reshape(len(q), -1), device="cuda")
     out = plan.evaluate(qd)
     torch.cuda.synchronize()
     return out.cpu().numpy()
