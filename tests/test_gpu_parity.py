@@ -4,7 +4,9 @@ Bars (FP32 path):
 * against the oracle KIFMM run with the same p, radii and pseudo-inverse
   cutoff: relative L2 error <= 1e-6;
 * against the FP64 direct sum: error <= 1.5x the oracle KIFMM's own error
-  at the same p;
+  at the same p, plus an FP32 resolution floor of 3e-7 (where the FP64
+  method is already more accurate than FP32 can resolve, e.g. p = 7, the
+  FP32 path is held to that floor instead);
 * column r of an nrhs evaluation equals the single-vector evaluation of
   charges[:, r] bit for bit (same FP32 operations in the same order).
 """
@@ -18,6 +20,9 @@ from paper_2303_08394_gb300 import workloads as wl
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+# relative L2 resolution of an FP32 evaluation of the whole method
+FP32_FLOOR = 3e-7
 
 
 def rel(a, b):
@@ -62,7 +67,7 @@ def test_fmm_matches_oracle(name, gen, n, p, ncrit):
     e_gpu_ora = rel(phi, phi_o)
     e_gpu, e_ora = rel(phi, ref), rel(phi_o, ref)
     assert e_gpu_ora <= 1e-6, (e_gpu_ora, e_gpu, e_ora)
-    assert e_gpu <= 1.5 * e_ora, (e_gpu, e_ora)
+    assert e_gpu <= 1.5 * e_ora + FP32_FLOOR, (e_gpu, e_ora)
     # the lists the GPU ran on are the oracle's lists
     assert plan.info("v_pairs") == sum(len(v) for v in ora.V.values())
     assert plan.info("u_pairs") == sum(len(v) for v in ora.U.values())
