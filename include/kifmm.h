@@ -116,6 +116,31 @@ fmm_status fmm_plan_set_option(fmm_plan_t plan, int key, double value);
 fmm_status fmm_evaluate(fmm_plan_t plan, const float *charges, int nrhs,
                         double *potentials, void *stream);
 
+/*
+ * The evaluation of fmm_evaluate without any device allocation.  The paper
+ * has no counterpart: this serves callers that may not allocate device
+ * memory while they evaluate -- an application whose device memory is owned
+ * by another allocator, a latency-critical loop in which cudaMalloc/cudaFree
+ * would add their implicit device-wide synchronisation, or a service that
+ * must not grow its device footprint after start-up.  (fmm_evaluate
+ * allocates its workspace on its first call and whenever nrhs grows.)
+ *
+ * The workspace comes from one fixed 64 MiB array in device memory that the
+ * library holds on every GPU that loads it, until the process exits.  The
+ * first call on a device looks the array up (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.
+ *
+ * charges, potentials: device pointers only, layouts as in fmm_evaluate;
+ * host pointers return FMM_ERR_INVALID_ARG.  A plan and nrhs whose workspace
+ * exceeds 64 MiB return FMM_ERR_INVALID_ARG with the sizes in the message.
+ * Every call on a device shares the array and overwrites it; nothing in it
+ * has to start at zero.  Calls whose work overlaps on the GPU (different
+ * streams, or different plans, on one device) race on the array: order them
+ * on one stream or synchronise between them.
+ */
+fmm_status fmm_evaluate_noalloc(fmm_plan_t plan, const float *charges, int nrhs,
+                                double *potentials, void *stream);
+
 /* Destroy a plan and free its host and device memory.  NULL is a no-op. */
 void fmm_destroy(fmm_plan_t plan);
 

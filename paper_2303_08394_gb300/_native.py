@@ -30,8 +30,8 @@ ARRAYS = {"node_keys": (0, "i4"), "node_range": (1, "i8"), "leaf_flag": (2, "i4"
 
 # every symbol include/kifmm.h declares
 EXPORTS = ("fmm_options_init", "fmm_plan_create", "fmm_plan_create_ex",
-           "fmm_plan_set_option", "fmm_evaluate", "fmm_destroy", "fmm_last_error",
-           "fmm_plan_info", "fmm_plan_get_array", "fmm_plan_phase_ms")
+           "fmm_plan_set_option", "fmm_evaluate", "fmm_evaluate_noalloc", "fmm_destroy",
+           "fmm_last_error", "fmm_plan_info", "fmm_plan_get_array", "fmm_plan_phase_ms")
 
 
 class Options(ctypes.Structure):
@@ -68,6 +68,7 @@ def lib():
                                      ctypes.POINTER(Options), ctypes.POINTER(vp)]
     L.fmm_plan_set_option.argtypes = [vp, ctypes.c_int, ctypes.c_double]
     L.fmm_evaluate.argtypes = [vp, fp, ctypes.c_int, dp, vp]
+    L.fmm_evaluate_noalloc.argtypes = [vp, fp, ctypes.c_int, dp, vp]
     L.fmm_destroy.argtypes = [vp]
     L.fmm_destroy.restype = None
     L.fmm_last_error.argtypes = []
@@ -76,7 +77,7 @@ def lib():
     L.fmm_plan_get_array.argtypes = [vp, ctypes.c_int, vp, i64, ctypes.POINTER(i64)]
     L.fmm_plan_phase_ms.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     for name in ("fmm_plan_create", "fmm_plan_create_ex", "fmm_plan_set_option",
-                 "fmm_evaluate", "fmm_plan_info", "fmm_plan_get_array", "fmm_plan_phase_ms"):
+                 "fmm_evaluate", "fmm_evaluate_noalloc", "fmm_plan_info", "fmm_plan_get_array", "fmm_plan_phase_ms"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L

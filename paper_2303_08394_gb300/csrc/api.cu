@@ -17,6 +17,7 @@
 #include "kifmm.h"
 #include "linalg.h"
 #include "plan.h"
+#include "plan_impl.h"
 
 using namespace kifmm;
 
@@ -284,17 +285,33 @@ fmm_status ensure_workspace(fmm_plan_s *P, int nrhs) {
 
 fmm_status enqueue(fmm_plan_s *P, const float *charges, int nrhs, double *pot,
                    cudaStream_t st) {
+    WorkBuffers b;
+    b.qs = P->qs;
+    b.up = P->up;
+    b.down = P->down;
+    b.qhat = P->qhat;
+    b.chat = P->chat;
+    b.xchk = P->xchk;
+    return kifmm::plan_enqueue(P, charges, nrhs, pot, b, st);
+}
+
+} // namespace
+
+// Enqueue every kernel of one evaluation on `st`, using the given
+// per-evaluation buffers (sized for nrhs, see plan_workspace_bytes).
+fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, double *pot,
+                               const WorkBuffers &b, cudaStream_t st) {
     const Tree &t = P->tree;
     const Schedules &sc = P->sched;
     DevWork w{};
     w.nrhs = nrhs;
     w.charges_user = charges;
-    w.qs = P->qs;
-    w.up = P->up;
-    w.down = P->down;
-    w.qhat = P->qhat;
-    w.chat = P->chat;
-    w.xchk = P->xchk;
+    w.qs = b.qs;
+    w.up = b.up;
+    w.down = b.down;
+    w.qhat = b.qhat;
+    w.chat = b.chat;
+    w.xchk = b.xchk;
     w.pot_user = pot;
     w.scale = 1.0 / (4.0 * M_PI * t.hw);
     int64_t launches = 0;
@@ -332,6 +349,23 @@ fmm_status enqueue(fmm_plan_s *P, const float *charges, int nrhs, double *pot,
     P->last_launches = launches;
     return FMM_OK;
 }
+
+// Bytes of each per-evaluation buffer of plan P for nrhs right-hand sides.
+void kifmm::plan_workspace_bytes(const fmm_plan_s *P, int nrhs, WorkspaceBytes *out) {
+    const Tree &t = P->tree;
+    const size_t nn = (size_t)t.nodes(), ns = P->ops->ns, kp = P->kpad;
+    const size_t nx = P->sched.x_nodes.size();
+    out->qs = (size_t)t.n * nrhs * sizeof(float);
+    out->up = out->down = nn * nrhs * ns * sizeof(float);
+    out->qhat = out->chat = nn * nrhs * kp * sizeof(float);
+    out->xchk = nx * nrhs * ns * sizeof(float);
+}
+
+int kifmm::plan_device(const fmm_plan_s *P) { return P->device; }
+fmm_status kifmm::plan_set_error(fmm_status s, const std::string &msg) { return fail(s, msg); }
+bool kifmm::plan_host_only(const fmm_plan_s *P) { return P->opts.host_only != 0; }
+
+namespace {
 
 } // namespace
 

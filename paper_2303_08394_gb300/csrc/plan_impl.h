@@ -1,0 +1,30 @@
+// Internal entry points shared by the C-ABI translation units.
+#pragma once
+#include <cstddef>
+#include <string>
+#include <cuda_runtime.h>
+
+#include "kifmm.h"
+
+namespace kifmm {
+
+// Per-evaluation device buffers (see DevWork for their layouts).
+struct WorkBuffers {
+    float *qs = nullptr, *up = nullptr, *down = nullptr, *qhat = nullptr, *chat = nullptr,
+          *xchk = nullptr;
+};
+
+// Byte sizes of those buffers for one plan and nrhs.
+struct WorkspaceBytes {
+    size_t qs = 0, up = 0, down = 0, qhat = 0, chat = 0, xchk = 0;
+};
+
+void plan_workspace_bytes(const fmm_plan_s *P, int nrhs, WorkspaceBytes *out);
+fmm_status plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, double *pot,
+                        const WorkBuffers &b, cudaStream_t st);
+int plan_device(const fmm_plan_s *P);
+// Record the message fmm_last_error() returns on this thread; returns s.
+fmm_status plan_set_error(fmm_status s, const std::string &msg);
+bool plan_host_only(const fmm_plan_s *P);
+
+} // namespace kifmm
