@@ -69,14 +69,30 @@ struct fmm_plan_s {
     DevM2L dm{};
     int *d_p2m = nullptr, *d_m2m = nullptr, *d_down = nullptr, *d_chunks = nullptr,
         *d_xnodes = nullptr;
+    // index lists of the level products: children of every internal box
+    // (sigma-major over m2m_nodes), M2L source of each box (itself or -1),
+    // parent's position within its level's internal boxes, child offset
+    // (sigma * rQ) into the parent's stacked L2L output
+    int *d_m2m_child = nullptr, *d_chat_src = nullptr, *d_ppos = nullptr, *d_poff = nullptr;
+    int max_level_nodes = 0, max_level_internal = 0;
     // workspace, sized for nrhs_cap right-hand sides
     int nrhs_cap = 0;
     float *qs = nullptr, *up = nullptr, *down = nullptr, *qhat = nullptr, *chat = nullptr,
-          *xchk = nullptr, *charges_stage = nullptr;
+          *xchk = nullptr, *charges_stage = nullptr, *chk = nullptr, *ybuf = nullptr,
+          *yp = nullptr;
     double *pot_stage = nullptr;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaStream_t last_stream = nullptr;
     int64_t last_launches = 0;
+    int num_sms = 0;
+    // tensor-core M2L: split S_t arrays and their TMA maps, per mode
+    // (index 0: BF16x3, 1: TF32x3)
+    void *s_split[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    CUtensorMap tmap[2][2];
+    bool tc_ready[2] = {false, false};
+    float *qh_hi = nullptr, *qh_lo = nullptr;   // split qhat (4-byte slots)
+    int qh_cap = 0;                             // nrhs the split buffers hold
+    int *err_host = nullptr, *err_dev = nullptr;  // mapped pinned error word
 
     ~fmm_plan_s() {
         if (opts.host_only) return;
@@ -85,15 +101,21 @@ struct fmm_plan_s {
         cudaSetDevice(device);
         for (void *a : allocs) cudaFree(a);
         free_workspace();
+        for (auto &m : s_split)
+            for (void *a : m)
+                if (a) cudaFree(a);
+        if (qh_hi) cudaFree(qh_hi);
+        if (qh_lo) cudaFree(qh_lo);
+        if (err_host) cudaFreeHost(err_host);
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
         cudaSetDevice(prev);
     }
     void free_workspace() {
-        void *w[] = {qs, up, down, qhat, chat, xchk, charges_stage, pot_stage};
+        void *w[] = {qs, up, down, qhat, chat, xchk, charges_stage, pot_stage, chk, ybuf, yp};
         for (void *a : w)
             if (a) cudaFree(a);
-        qs = up = down = qhat = chat = xchk = charges_stage = nullptr;
+        qs = up = down = qhat = chat = xchk = charges_stage = chk = ybuf = yp = nullptr;
         pot_stage = nullptr;
         nrhs_cap = 0;
     }
@@ -111,6 +133,111 @@ struct fmm_plan_s {
 };
 
 namespace {
+
+uint16_t bf16_rn(float f) {  // round to nearest even, finite inputs
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+float bf16_val(uint16_t h) {
+    uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+float tf32_rn(float f) {  // 10-bit mantissa, round to nearest even
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0xFFFu + ((u >> 13) & 1u);
+    u &= 0xFFFFE000u;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (looked up
+// once; no link against the driver library).
+fmm_status encode_fn(EncodeTiledFn *out) {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                            &q));
+        if (!f || q != cudaDriverEntryPointSuccess)
+            return fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+        fn = reinterpret_cast<EncodeTiledFn>(f);
+    }
+    *out = fn;
+    return FMM_OK;
+}
+
+// Split S_t (FP64) into hi/lo operand arrays [316][kpad][kpad] (row n holds
+// S_t[n][0..kpad)) and encode their TMA maps (boxes of 128 bytes x kpad rows,
+// 128-byte swizzle).
+fmm_status prepare_tc(fmm_plan_s *P, int mode) {
+    const int idx = mode == FMM_M2L_TF32X3 ? 1 : 0;
+    if (P->tc_ready[idx]) return FMM_OK;
+    const int kp = P->kpad, k = P->ops->k;
+    if (kp > 256)
+        return fail(FMM_ERR_UNSUPPORTED, "tensor-core M2L needs rank k <= 256 (raise eps_svd)");
+    const bool tf = idx == 1;
+    const size_t esize = tf ? 4 : 2;
+    const size_t count = (size_t)kNumOffsets * kp * kp;
+    std::vector<uint16_t> bh, bl;
+    std::vector<float> th, tl;
+    if (tf) {
+        th.assign(count, 0.f);
+        tl.assign(count, 0.f);
+    } else {
+        bh.assign(count, 0);
+        bl.assign(count, 0);
+    }
+    const std::vector<double> &S = P->ops->S;
+    for (int t = 0; t < kNumOffsets; ++t)
+        for (int n = 0; n < k; ++n)
+            for (int j = 0; j < k; ++j) {
+                const double x = S[(size_t)t * k * k + (size_t)n * k + j];
+                const size_t o = (size_t)t * kp * kp + (size_t)n * kp + j;
+                if (tf) {
+                    const float h = tf32_rn((float)x);
+                    th[o] = h;
+                    tl[o] = tf32_rn((float)(x - (double)h));
+                } else {
+                    const uint16_t h = bf16_rn((float)x);
+                    bh[o] = h;
+                    bl[o] = bf16_rn((float)(x - (double)bf16_val(h)));
+                }
+            }
+    for (int sp = 0; sp < 2; ++sp) {
+        CK(cudaMalloc(&P->s_split[idx][sp], count * esize));
+        const void *src = tf ? (const void *)(sp ? tl.data() : th.data())
+                             : (const void *)(sp ? bl.data() : bh.data());
+        CK(cudaMemcpy(P->s_split[idx][sp], src, count * esize, cudaMemcpyHostToDevice));
+    }
+    EncodeTiledFn fn = nullptr;
+    if (fmm_status st = encode_fn(&fn)) return st;
+    const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)kNumOffsets * kp};
+    const cuuint64_t strides[1] = {(cuuint64_t)kp * esize};
+    const cuuint32_t box[2] = {(cuuint32_t)(128 / esize), (cuuint32_t)kp};
+    const cuuint32_t estr[2] = {1, 1};
+    for (int sp = 0; sp < 2; ++sp) {
+        CUresult r = fn(
+            &P->tmap[idx][sp], tf ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+            2, P->s_split[idx][sp], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    }
+    P->tc_ready[idx] = true;
+    return FMM_OK;
+}
 
 fmm_status upload_plan(fmm_plan_s *P) {
     const Tree &t = P->tree;
@@ -170,6 +297,36 @@ fmm_status upload_plan(fmm_plan_s *P) {
     if ((s = P->upload(P->sched.down_nodes, &P->d_down))) return s;
     if ((s = P->upload(P->sched.down_chunk, &P->d_chunks))) return s;
     if ((s = P->upload(P->sched.x_nodes, &P->d_xnodes))) return s;
+    {
+        const Schedules &sc = P->sched;
+        const int total = (int)sc.m2m_nodes.size();
+        std::vector<int> child((size_t)8 * total), chat_src(nn, -1), ppos(nn, -1), poff(nn, 0);
+        std::vector<int> pos_in_level(nn, -1);
+        for (int l = 0; l <= t.depth; ++l)
+            for (int q = sc.m2m_level_ptr[l]; q < sc.m2m_level_ptr[l + 1]; ++q) {
+                const int b = sc.m2m_nodes[q];
+                pos_in_level[b] = q - sc.m2m_level_ptr[l];
+                for (int sg = 0; sg < 8; ++sg) child[(size_t)sg * total + q] = t.child[8 * b + sg];
+            }
+        for (int64_t b = 0; b < nn; ++b) {
+            if (t.v_ptr[b + 1] > t.v_ptr[b]) chat_src[b] = (int)b;
+            const int l = t.key[4 * b];
+            if (l >= 3) ppos[b] = pos_in_level[t.parent[b]];
+            const int sg = (t.key[4 * b + 1] & 1) | ((t.key[4 * b + 2] & 1) << 1) |
+                           ((t.key[4 * b + 3] & 1) << 2);
+            poff[b] = sg * o.rQ;
+        }
+        if ((s = P->upload(child, &P->d_m2m_child))) return s;
+        if ((s = P->upload(chat_src, &P->d_chat_src))) return s;
+        if ((s = P->upload(ppos, &P->d_ppos))) return s;
+        if ((s = P->upload(poff, &P->d_poff))) return s;
+        for (int l = 0; l <= t.depth; ++l) {
+            P->max_level_nodes = std::max(P->max_level_nodes, t.level_ptr[l + 1] - t.level_ptr[l]);
+            P->max_level_internal =
+                std::max(P->max_level_internal, sc.m2m_level_ptr[l + 1] - sc.m2m_level_ptr[l]);
+        }
+        P->max_level_nodes = std::max(P->max_level_nodes, (int)sc.p2m_nodes.size());
+    }
 
     // M2L tables
     DevM2L &m = P->dm;
@@ -205,50 +362,64 @@ fmm_status upload_plan(fmm_plan_s *P) {
 #define UPF(vec, field)                                   \
     if ((s = P->upload(vec, &f))) return s;               \
     op.field = f;
-    UPF(to_f32(o.Pu), Pu);
+    // AT (n x m row-major, FP64) -> FP32 with rows padded to round4(m)
+    auto padded = [](const std::vector<double> &at, int n, int m) {
+        const int mp = (m + 3) & ~3;
+        std::vector<float> out((size_t)n * mp, 0.f);
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < m; ++i) out[(size_t)j * mp + i] = (float)at[(size_t)j * m + i];
+        return out;
+    };
+    auto append = [](std::vector<float> &dst, const std::vector<float> &src) {
+        dst.insert(dst.end(), src.begin(), src.end());
+    };
+    UPF(padded(o.Pu, ns, rP), Pu);                       // AT of Pu^T
     {
         std::vector<float> inv(rP);
         for (int i = 0; i < rP; ++i) inv[i] = (float)(1.0 / o.Ps[i]);
         UPF(inv, Ps_inv);
     }
-    UPF(to_f32(transpose(o.Pv, ns, rP)), PvT);
+    UPF(padded(transpose(o.Pv, ns, rP), rP, ns), PvT);   // AT of Pv
     {
-        std::vector<float> mm((size_t)8 * ns * rP);
-        for (int sg = 0; sg < 8; ++sg)
-            for (int i = 0; i < rP; ++i)
-                for (int j = 0; j < ns; ++j)
-                    mm[(size_t)sg * ns * rP + (size_t)j * rP + i] =
-                        (float)o.M2M[(size_t)sg * rP * ns + (size_t)i * ns + j];
+        std::vector<float> mm;
+        for (int sg = 0; sg < 8; ++sg) {
+            std::vector<double> m1(o.M2M.begin() + (size_t)sg * rP * ns,
+                                   o.M2M.begin() + (size_t)(sg + 1) * rP * ns);
+            append(mm, padded(transpose(m1, rP, ns), ns, rP));
+        }
         UPF(mm, M2M);
     }
     {
-        std::vector<float> vk((size_t)ns * kp, 0.f);
+        std::vector<double> vk((size_t)ns * kp, 0.0);        // AT of Vk^T, zero padded
         for (int j = 0; j < ns; ++j)
-            for (int i = 0; i < k; ++i) vk[(size_t)j * kp + i] = (float)o.Vk[(size_t)j * k + i];
-        UPF(vk, Vk);
+            for (int i = 0; i < k; ++i) vk[(size_t)j * kp + i] = o.Vk[(size_t)j * k + i];
+        UPF(padded(vk, ns, kp), Vk);
     }
     {
-        std::vector<float> q((size_t)kp * rQ, 0.f);
+        std::vector<double> q((size_t)kp * rQ, 0.0);         // AT of Qu^T Uk
         for (int i = 0; i < rQ; ++i)
-            for (int j = 0; j < k; ++j) q[(size_t)j * rQ + i] = (float)o.QUk[(size_t)i * k + j];
-        UPF(q, QUkT);
+            for (int j = 0; j < k; ++j) q[(size_t)j * rQ + i] = o.QUk[(size_t)i * k + j];
+        UPF(padded(q, kp, rQ), QUkT);
     }
-    UPF(to_f32(o.Qu), Qu);
+    UPF(padded(o.Qu, ns, rQ), Qu);                       // AT of Qu^T
     {
-        std::vector<float> ll((size_t)8 * ns * rQ);
+        // AT of [L2L_0; ...; L2L_7] with row (sigma, i) divided by Qs[i]:
+        // ns x 8 rQ, so one product gives all eight children's contributions
+        // already scaled for the downward pseudo-inverse
+        std::vector<double> at((size_t)ns * 8 * rQ);
         for (int sg = 0; sg < 8; ++sg)
             for (int i = 0; i < rQ; ++i)
                 for (int j = 0; j < ns; ++j)
-                    ll[(size_t)sg * ns * rQ + (size_t)j * rQ + i] =
-                        (float)o.L2L[(size_t)sg * rQ * ns + (size_t)i * ns + j];
-        UPF(ll, L2L);
+                    at[(size_t)j * 8 * rQ + (size_t)sg * rQ + i] =
+                        o.L2L[(size_t)sg * rQ * ns + (size_t)i * ns + j] / o.Qs[i];
+        UPF(padded(at, ns, 8 * rQ), L2L);
     }
     {
         std::vector<float> inv(rQ);
         for (int i = 0; i < rQ; ++i) inv[i] = (float)(1.0 / o.Qs[i]);
         UPF(inv, Qs_inv);
     }
-    UPF(to_f32(transpose(o.Qv, ns, rQ)), QvT);
+    UPF(padded(transpose(o.Qv, ns, rQ), rQ, ns), QvT);   // AT of Qv
     {
         std::vector<float> st((size_t)kNumOffsets * kp * kp, 0.f);
         for (int tt = 0; tt < kNumOffsets; ++tt)
@@ -261,25 +432,50 @@ fmm_status upload_plan(fmm_plan_s *P) {
 #undef UPF
     if (P->timing)
         for (auto &e : P->ev) CK(cudaEventCreate(&e));
+    CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
+    CK(cudaHostAlloc((void **)&P->err_host, sizeof(int), cudaHostAllocMapped));
+    *P->err_host = 0;
+    CK(cudaHostGetDevicePointer((void **)&P->err_dev, P->err_host, 0));
+    if (P->opts.m2l_mode != FMM_M2L_FP32) {
+        fmm_status s2 = prepare_tc(P, P->opts.m2l_mode);
+        if (s2 != FMM_OK) return s2;
+    }
     return FMM_OK;
 }
 
 fmm_status ensure_workspace(fmm_plan_s *P, int nrhs) {
     if (nrhs <= P->nrhs_cap) return FMM_OK;
     P->free_workspace();
-    const Tree &t = P->tree;
-    const size_t nn = (size_t)t.nodes(), ns = P->ops->ns, kp = P->kpad;
-    const size_t nx = P->sched.x_nodes.size();
-    auto alloc = [&](void **p, size_t bytes) -> cudaError_t {
-        return cudaMalloc(p, bytes ? bytes : 16);
+    WorkspaceBytes wb;
+    kifmm::plan_workspace_bytes(P, nrhs, &wb);
+    auto alloc = [&](float **p, size_t bytes) -> cudaError_t {
+        return cudaMalloc((void **)p, bytes ? bytes : 16);
     };
-    CK(alloc((void **)&P->qs, (size_t)t.n * nrhs * sizeof(float)));
-    CK(alloc((void **)&P->up, nn * nrhs * ns * sizeof(float)));
-    CK(alloc((void **)&P->down, nn * nrhs * ns * sizeof(float)));
-    CK(alloc((void **)&P->qhat, nn * nrhs * kp * sizeof(float)));
-    CK(alloc((void **)&P->chat, nn * nrhs * kp * sizeof(float)));
-    CK(alloc((void **)&P->xchk, nx * nrhs * ns * sizeof(float)));
+    CK(alloc(&P->qs, wb.qs));
+    CK(alloc(&P->up, wb.up));
+    CK(alloc(&P->down, wb.down));
+    CK(alloc(&P->qhat, wb.qhat));
+    CK(alloc(&P->chat, wb.chat));
+    CK(alloc(&P->xchk, wb.xchk));
+    CK(alloc(&P->chk, wb.chk));
+    CK(alloc(&P->ybuf, wb.ybuf));
+    CK(alloc(&P->yp, wb.yp));
     P->nrhs_cap = nrhs;
+    return FMM_OK;
+}
+
+// Split-operand copies of qhat for the tensor-core M2L (4-byte slots, so the
+// same buffers serve BF16 and TF32).
+fmm_status ensure_split(fmm_plan_s *P, int nrhs) {
+    if (P->opts.m2l_mode == FMM_M2L_FP32 || nrhs <= P->qh_cap) return FMM_OK;
+    if (P->qh_hi) cudaFree(P->qh_hi);
+    if (P->qh_lo) cudaFree(P->qh_lo);
+    P->qh_hi = P->qh_lo = nullptr;
+    P->qh_cap = 0;
+    const size_t bytes = ((size_t)P->tree.nodes() * nrhs + 1) * P->kpad * 4;
+    CK(cudaMalloc((void **)&P->qh_hi, bytes));
+    CK(cudaMalloc((void **)&P->qh_lo, bytes));
+    P->qh_cap = nrhs;
     return FMM_OK;
 }
 
@@ -292,6 +488,11 @@ fmm_status enqueue(fmm_plan_s *P, const float *charges, int nrhs, double *pot,
     b.qhat = P->qhat;
     b.chat = P->chat;
     b.xchk = P->xchk;
+    b.chk = P->chk;
+    b.ybuf = P->ybuf;
+    b.yp = P->yp;
+    b.qh_hi = P->qh_hi;
+    b.qh_lo = P->qh_lo;
     return kifmm::plan_enqueue(P, charges, nrhs, pot, b, st);
 }
 
@@ -313,33 +514,157 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
     w.chat = b.chat;
     w.xchk = b.xchk;
     w.pot_user = pot;
+    if (!b.chk || !b.ybuf || !b.yp) return fail(FMM_ERR_INVALID_ARG, "workspace is incomplete");
     w.scale = 1.0 / (4.0 * M_PI * t.hw);
     int64_t launches = 0;
     if (P->timing) CK(cudaEventRecord(P->ev[0], st));
     CK(launch_gather_charges(P->dt, w, st));
     ++launches;
+    const DevOps &o = P->dops;
+    const int ns = o.ns, rP = o.rP, rQ = o.rQ, kp = o.kpad;
+    const int rPp = (rP + 3) & ~3, rQp = (rQ + 3) & ~3;  // y rows, 16-byte aligned
+    auto gemm = [&](VGemm &g) -> fmm_status {
+        g.nrhs = nrhs;
+        if (g.count > 0) ++launches;
+        CK(launch_vgemm(g, st));
+        return FMM_OK;
+    };
+    auto seg = [](const float *AT, int n, const float *src, int src_ld, const int *idx, int base) {
+        VSeg s{};
+        s.AT = AT;
+        s.n = n;
+        s.src = src;
+        s.src_ld = src_ld;
+        s.src_idx = idx;
+        s.src_base = base;
+        return s;
+    };
+    // rho = Pv y (y already divided by Ps), written to up[node]; then the
+    // M2L projection qhat[node] = Vk^T rho
+    auto finish_up = [&](const int *nodes, int count) -> fmm_status {
+        VGemm g{};
+        g.m = ns;
+        g.count = count;
+        g.nseg = 1;
+        g.seg[0] = seg(o.PvT, rP, b.ybuf, rPp, nullptr, 0);
+        g.dst = b.up;
+        g.dst_ld = ns;
+        g.dst_idx = nodes;
+        if (fmm_status e = gemm(g)) return e;
+        VGemm h{};
+        h.m = kp;
+        h.count = count;
+        h.nseg = 1;
+        h.seg[0] = seg(o.Vk, ns, b.up, ns, nodes, 0);
+        h.dst = b.qhat;
+        h.dst_ld = kp;
+        h.dst_idx = nodes;
+        return gemm(h);
+    };
     if (t.depth >= 2) {
-        if (!sc.p2m_nodes.empty()) ++launches;
-        CK(launch_p2m(P->dt, P->dops, w, P->d_p2m, (int)sc.p2m_nodes.size(), st));
+        // P2M: check potentials, y = Pu^T chk / Ps, rho, qhat
+        const int np = (int)sc.p2m_nodes.size();
+        if (np > 0) {
+            ++launches;
+            CK(launch_p2m_check(P->dt, o, w, P->d_p2m, np, b.chk, ns, st));
+            VGemm g{};
+            g.m = rP;
+            g.count = np;
+            g.nseg = 1;
+            g.seg[0] = seg(o.Pu, ns, b.chk, ns, nullptr, 0);
+            g.scale = o.Ps_inv;
+            g.dst = b.ybuf;
+            g.dst_ld = rPp;
+            if (fmm_status e = gemm(g)) return e;
+            if (fmm_status e = finish_up(P->d_p2m, np)) return e;
+        }
+        // M2M, bottom-up: y = sum_sigma M2M_sigma up[child_sigma] / Ps
+        const int total = (int)sc.m2m_nodes.size();
+        const int mp = (rP + 3) & ~3;
         for (int l = t.depth - 1; l >= 2; --l) {
-            int a = sc.m2m_level_ptr[l], b = sc.m2m_level_ptr[l + 1];
-            if (b > a) ++launches;
-            CK(launch_m2m(P->dt, P->dops, w, P->d_m2m + a, b - a, st));
+            const int a0 = sc.m2m_level_ptr[l], cnt = sc.m2m_level_ptr[l + 1] - a0;
+            if (cnt == 0) continue;
+            VGemm g{};
+            g.m = rP;
+            g.count = cnt;
+            g.nseg = 8;
+            for (int sg = 0; sg < 8; ++sg)
+                g.seg[sg] = seg(o.M2M + (size_t)sg * ns * mp, ns, b.up, ns,
+                                P->d_m2m_child + (size_t)sg * total + a0, 0);
+            g.scale = o.Ps_inv;
+            g.dst = b.ybuf;
+            g.dst_ld = rPp;
+            if (fmm_status e = gemm(g)) return e;
+            if (fmm_status e = finish_up(P->d_m2m + a0, cnt)) return e;
         }
     }
     if (P->timing) CK(cudaEventRecord(P->ev[1], st));
     if (t.depth >= 2 && P->dm.ntiles > 0) {
-        CK(launch_m2l_simt(P->dm, P->dops, w, st));
-        ++launches;
+        const int mode = P->opts.m2l_mode;
+        if (mode == FMM_M2L_FP32) {
+            CK(launch_m2l_simt(P->dm, P->dops, w, st));
+            ++launches;
+        } else {
+            const int idx = mode == FMM_M2L_TF32X3 ? 1 : 0;
+            if (!P->tc_ready[idx] || !b.qh_hi || !b.qh_lo)
+                return fail(FMM_ERR_INVALID_ARG, "tensor-core M2L buffers are not prepared");
+            CK(launch_m2l_tc(P->dm, P->dops, w, (int)t.nodes(), idx == 1, P->tmap[idx][0],
+                             P->tmap[idx][1], b.qh_hi, b.qh_lo, P->err_dev, P->num_sms, st));
+            launches += 2;
+        }
     }
     if (P->timing) CK(cudaEventRecord(P->ev[2], st));
     if (t.depth >= 2) {
         if (!sc.x_nodes.empty()) ++launches;
-        CK(launch_p2l(P->dt, P->dops, w, P->d_xnodes, (int)sc.x_nodes.size(), st));
+        CK(launch_p2l(P->dt, o, w, P->d_xnodes, (int)sc.x_nodes.size(), st));
+        const int total = (int)sc.m2m_nodes.size();
+        (void)total;
         for (int l = 2; l <= t.depth; ++l) {
-            int a = sc.down_chunk_level_ptr[l], b = sc.down_chunk_level_ptr[l + 1];
-            if (b > a) ++launches;
-            CK(launch_down(P->dt, P->dops, w, P->d_chunks + 4 * a, P->d_down, b - a, st));
+            const int b0 = t.level_ptr[l], cnt = t.level_ptr[l + 1] - b0;
+            if (cnt == 0) continue;
+            // L2L: all eight children's (scaled) check potentials from the
+            // parents' downward densities, one product over the parent level
+            if (l >= 3) {
+                const int a0 = sc.m2m_level_ptr[l - 1], pc = sc.m2m_level_ptr[l] - a0;
+                VGemm g{};
+                g.m = 8 * rQ;
+                g.count = pc;
+                g.nseg = 1;
+                g.seg[0] = seg(o.L2L, ns, b.down, ns, P->d_m2m + a0, 0);
+                g.dst = b.yp;
+                g.dst_ld = 8 * rQ;
+                if (fmm_status e = gemm(g)) return e;
+            }
+            // y = ((Qu^T Uk) chat + Qu^T xchk) / Qs + L2L part
+            VGemm g{};
+            g.m = rQ;
+            g.count = cnt;
+            g.nseg = 1;
+            g.seg[0] = seg(o.QUkT, kp, b.chat, kp, P->d_chat_src + b0, 0);
+            if (!sc.x_nodes.empty()) {
+                g.seg[1] = seg(o.Qu, ns, b.xchk, ns, P->dt.x_slot + b0, 0);
+                g.nseg = 2;
+            }
+            g.scale = o.Qs_inv;
+            if (l >= 3) {
+                g.add = b.yp;
+                g.add_ld = 8 * rQ;
+                g.add_idx = P->d_ppos + b0;
+                g.add_off = P->d_poff + b0;
+            }
+            g.dst = b.ybuf;
+            g.dst_ld = rQp;
+            if (fmm_status e = gemm(g)) return e;
+            // rho = Qv y -> down[node]
+            VGemm h{};
+            h.m = ns;
+            h.count = cnt;
+            h.nseg = 1;
+            h.seg[0] = seg(o.QvT, rQ, b.ybuf, rQp, nullptr, 0);
+            h.dst = b.down;
+            h.dst_ld = ns;
+            h.dst_base = b0;
+            if (fmm_status e = gemm(h)) return e;
         }
     }
     if (P->timing) CK(cudaEventRecord(P->ev[3], st));
@@ -359,9 +684,26 @@ void kifmm::plan_workspace_bytes(const fmm_plan_s *P, int nrhs, WorkspaceBytes *
     out->up = out->down = nn * nrhs * ns * sizeof(float);
     out->qhat = out->chat = nn * nrhs * kp * sizeof(float);
     out->xchk = nx * nrhs * ns * sizeof(float);
+    out->qh = P->opts.m2l_mode == FMM_M2L_FP32 ? 0 : (nn * nrhs + 1) * kp * 4;
+    const size_t rmax = (size_t)((std::max(P->ops->rP, P->ops->rQ) + 3) & ~3);
+    out->chk = P->sched.p2m_nodes.size() * nrhs * ns * sizeof(float);
+    out->ybuf = (size_t)P->max_level_nodes * nrhs * rmax * sizeof(float);
+    out->yp = (size_t)P->max_level_internal * nrhs * 8 * P->ops->rQ * sizeof(float);
 }
 
 int kifmm::plan_device(const fmm_plan_s *P) { return P->device; }
+int kifmm::plan_m2l_mode(const fmm_plan_s *P) { return P->opts.m2l_mode; }
+
+// A bounded device-side wait that expired sets the plan's mapped error word;
+// it is reported once, by the next call that looks, and then cleared.
+fmm_status kifmm::plan_check_device_error(fmm_plan_s *P) {
+    if (!P->err_host) return FMM_OK;
+    const int e = *(volatile int *)P->err_host;
+    if (e == 0) return FMM_OK;
+    *(volatile int *)P->err_host = 0;
+    return fail(FMM_ERR_TIMEOUT, "a bounded wait in the tensor-core M2L expired (roles mask " +
+                                     std::to_string(e) + "); results of that evaluation are invalid");
+}
 fmm_status kifmm::plan_set_error(fmm_status s, const std::string &msg) { return fail(s, msg); }
 bool kifmm::plan_host_only(const fmm_plan_s *P) { return P->opts.host_only != 0; }
 
@@ -410,8 +752,9 @@ fmm_status fmm_plan_create_ex(const double *sources, const double *targets, int6
         return fail(FMM_ERR_INVALID_ARG, "eps_svd in [0,1)");
     if (o.max_level < 0 || o.max_level > kKeyBits)
         return fail(FMM_ERR_INVALID_ARG, "max_level in [0,16]");
-    if (o.m2l_mode != FMM_M2L_FP32)
-        return fail(FMM_ERR_UNSUPPORTED, "only the FP32 M2L is built in this library version");
+    if (o.m2l_mode != FMM_M2L_FP32 && o.m2l_mode != FMM_M2L_BF16X3 &&
+        o.m2l_mode != FMM_M2L_TF32X3)
+        return fail(FMM_ERR_INVALID_ARG, "unknown M2L mode");
     fmm_plan_s *P = nullptr;
     try {
         P = new fmm_plan_s();
@@ -479,14 +822,16 @@ fmm_status fmm_plan_create_ex(const double *sources, const double *targets, int6
 fmm_status fmm_plan_set_option(fmm_plan_t plan, int key, double value) {
     if (!plan) return fail(FMM_ERR_INVALID_ARG, "plan is NULL");
     if (key == FMM_OPT_M2L_MODE) {
-        int mode = (int)value;
-        if (mode == FMM_M2L_FP32) {
-            plan->opts.m2l_mode = mode;
-            return FMM_OK;
+        const int mode = (int)value;
+        if (mode != FMM_M2L_FP32 && mode != FMM_M2L_BF16X3 && mode != FMM_M2L_TF32X3)
+            return fail(FMM_ERR_INVALID_ARG, "unknown M2L mode");
+        if (mode != FMM_M2L_FP32 && !plan->opts.host_only) {
+            CK(cudaSetDevice(plan->device));
+            fmm_status s = prepare_tc(plan, mode);
+            if (s != FMM_OK) return s;
         }
-        if (mode == FMM_M2L_BF16X3 || mode == FMM_M2L_TF32X3)
-            return fail(FMM_ERR_UNSUPPORTED, "tensor-core M2L is not built in this version");
-        return fail(FMM_ERR_INVALID_ARG, "unknown M2L mode");
+        plan->opts.m2l_mode = mode;
+        return FMM_OK;
     }
     return fail(FMM_ERR_INVALID_ARG, "unknown option key");
 }
@@ -499,8 +844,11 @@ fmm_status fmm_evaluate(fmm_plan_t P, const float *charges, int nrhs, double *po
     if (nrhs < 1) return fail(FMM_ERR_INVALID_ARG, "nrhs must be >= 1");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CK(cudaSetDevice(P->device));
+    if (fmm_status e = kifmm::plan_check_device_error(P)) return e;
     const bool dq = is_device_pointer(charges), dp = is_device_pointer(potentials);
     fmm_status s = ensure_workspace(P, nrhs);
+    if (s != FMM_OK) return s;
+    s = ensure_split(P, nrhs);
     if (s != FMM_OK) return s;
     const size_t nq = (size_t)P->tree.n * nrhs;
     const float *dq_ptr = charges;
@@ -518,7 +866,10 @@ fmm_status fmm_evaluate(fmm_plan_t P, const float *charges, int nrhs, double *po
     if (s != FMM_OK) return s;
     P->last_stream = st;
     if (!dp) CK(cudaMemcpyAsync(potentials, dp_ptr, nq * sizeof(double), cudaMemcpyDeviceToHost, st));
-    if (!dq || !dp) CK(cudaStreamSynchronize(st));
+    if (!dq || !dp) {
+        CK(cudaStreamSynchronize(st));
+        return kifmm::plan_check_device_error(P);
+    }
     return FMM_OK;
 }
 

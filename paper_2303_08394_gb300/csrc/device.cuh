@@ -1,6 +1,7 @@
 // Device-side views of a plan and the kernel launchers.
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "constants.h"
@@ -31,8 +32,9 @@ struct DevTree {
 };
 
 // FP32 operators.  Every matrix is stored as the transpose AT (n x m) of
-// the m x n operator A it applies, so that consecutive threads, which own
-// consecutive output rows i, read AT[j*m + i] coalesced.
+// the m x n operator A it applies, rows padded to round4(m) floats so each
+// row is 16-byte aligned; consecutive threads own consecutive output rows i
+// and read AT[j*round4(m) + i].
 struct DevOps {
     int ns, rP, rQ, k, kpad;
     float ai, ao;
@@ -44,7 +46,7 @@ struct DevOps {
     const float *Vk;        // AT of Vk^T:  ns x kpad (zero padded)
     const float *QUkT;      // AT of Qu^T Uk: kpad x rQ (zero padded)
     const float *Qu;        // AT of Qu^T:  ns x rQ
-    const float *L2L;       // 8 x AT of L2L_sigma: ns x rQ each
+    const float *L2L;       // AT of [L2L_0; ..; L2L_7] / Qs: ns x 8 rQ
     const float *Qs_inv;    // rQ
     const float *QvT;       // AT of Qv:    rQ x ns
     const float *St;        // 316 x kpad x kpad: St[t][j][i] = S_t[i][j]
@@ -72,23 +74,61 @@ struct DevWork {
     double scale;               // 1 / (4 pi root half-width)
 };
 
+// Batched operator x gathered-vector products (k_vgemm.cu):
+//   Y[dst(v)][i] = scale[i] * sum_s sum_j A_s[i][j] X_s[src_s(v)][j] + add(v)[i]
+// for v = pos * nrhs + r, pos < count, i < m.  A_s is stored as its transpose
+// AT (n x round4(m)).  Source row of segment s for v: (src_idx[pos] or
+// src_base + pos) * nrhs + r in rows of src_ld floats (index < 0 reads
+// zeros).  Destination row: (dst_idx[pos] or dst_base + pos) * nrhs + r.
+// Optional add row: (add_idx[pos]) * nrhs + r in rows of add_ld floats,
+// offset by add_off[pos] floats.
+constexpr int kMaxSeg = 8;
+struct VSeg {
+    const float *AT;
+    int n;
+    const float *src;
+    int src_ld;
+    const int *src_idx;
+    int src_base;
+};
+struct VGemm {
+    int m, count, nrhs, nseg;
+    VSeg seg[kMaxSeg];
+    const float *scale;
+    float *dst;
+    int dst_ld;
+    const int *dst_idx;
+    int dst_base;
+    const float *add;
+    int add_ld;
+    const int *add_idx;
+    const int *add_off;
+};
+cudaError_t launch_vgemm(const VGemm &g, cudaStream_t s);
+
+// Upward check potentials of leaves (k_updown.cu): chk[pos*nrhs + r][j] for
+// pos < count, rows of `ld` floats.
+cudaError_t launch_p2m_check(const DevTree &t, const DevOps &o, const DevWork &w,
+                             const int *nodes, int count, float *chk, int ld, cudaStream_t s);
+
 cudaError_t launch_gather_charges(const DevTree &t, const DevWork &w, cudaStream_t s);
-cudaError_t launch_p2m(const DevTree &t, const DevOps &o, const DevWork &w,
-                       const int *nodes, int count, cudaStream_t s);
-cudaError_t launch_m2m(const DevTree &t, const DevOps &o, const DevWork &w,
-                       const int *nodes, int count, cudaStream_t s);
 cudaError_t launch_p2l(const DevTree &t, const DevOps &o, const DevWork &w,
                        const int *nodes, int count, cudaStream_t s);
-cudaError_t launch_down(const DevTree &t, const DevOps &o, const DevWork &w,
-                        const int *chunks, const int *nodes, int nchunks,
-                        cudaStream_t s);
 cudaError_t launch_m2l_simt(const DevM2L &m, const DevOps &o, const DevWork &w,
                             cudaStream_t s);
 cudaError_t launch_eval(const DevTree &t, const DevOps &o, const DevWork &w,
                         cudaStream_t s);
 
-// Vectors (node x rhs pairs) handled per block by the matrix-vector kernels.
-constexpr int kMaxVec = 32;
+// Tensor-core M2L (k_m2l_tc.cu).  qh_hi/qh_lo hold (nnodes*nrhs + 1) rows of
+// kpad operand elements (BF16, or TF32 in 32-bit words), the last row zero;
+// s_hi/s_lo map the split S_t arrays [316*kpad rows][kpad] with 128-byte
+// swizzled boxes of 128 bytes x kpad rows.  *err is set nonzero if a bounded
+// wait expired.
+size_t m2l_tc_smem(int kpad, int *stages);
+cudaError_t launch_m2l_tc(const DevM2L &m, const DevOps &o, const DevWork &w, int nnodes,
+                          bool tf32, const CUtensorMap &s_hi, const CUtensorMap &s_lo,
+                          void *qh_hi, void *qh_lo, int *err, int num_sms, cudaStream_t st);
+
 // Right-hand sides handled per block by the point-evaluation kernels.
 constexpr int kMaxRhs = 16;
 // Nodes per down-pass chunk (chunks never mix child positions).

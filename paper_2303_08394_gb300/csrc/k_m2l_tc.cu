@@ -1,0 +1,402 @@
+// V-list M2L on the 5th-generation tensor cores (tcgen05), split precision.
+//
+// Per M2L tile (128 target rows) and per offset t the tile uses:
+//     D[128 x kpad] += X_t[128 x kpad] * S_t^T,   X_t row r = qhat of the
+// source at offset t from target r (zero row if none).  Operands are split
+// x = x_hi + x_lo in BF16 (kind::f16) or TF32 (kind::tf32) and every K step
+// issues x_hi*S_hi + x_hi*S_lo + x_lo*S_hi with FP32 accumulation in TMEM.
+//
+// Warp roles (448 threads):
+//   0-3, 10-13  gather the 128 rows of X_t for one 128-byte K chunk into
+//        shared memory in the 128-byte swizzled K-major layout (thread =
+//        row); the two sets take alternate chunks and issue a chunk's loads
+//        before waiting for its stage, so loads overlap the MMAs;
+//   4-7  epilogue: every kGroup offsets, add the TMEM accumulator into a
+//        TMEM running total; after the tile's last offset write the total
+//        (FP32) to chat.  The two-level sum keeps the FP32 rounding of the
+//        ~189 k products per target at the level the FP32 path reaches;
+//   8    TMA loads of the S_t chunks (hi and lo) for the same K chunk;
+//   9    allocates TMEM, issues the MMAs (one thread), frees TMEM.
+// Stages of shared memory are recycled through mbarriers: producers wait
+// for `empty`, the MMA thread waits for `full_a` / `full_b` and releases the
+// stage with tcgen05.commit.  Every wait is bounded; on expiry the block
+// records the failing role in *err, sets a block-wide abort flag, drains
+// what it issued and frees its TMEM before returning.
+#include <algorithm>
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "device.cuh"
+#include "tc_ptx.cuh"
+
+namespace kifmm {
+
+namespace {
+
+constexpr int kThreads = 448;
+#ifndef KIFMM_TC_GROUP
+#define KIFMM_TC_GROUP 1
+#endif
+// Offsets summed in one TMEM accumulator before it is added to the total.
+constexpr int kGroup = KIFMM_TC_GROUP;
+constexpr uint64_t kWaitLimit = 2000000000ull;  // 2 s per wait
+
+struct TcArgs {
+    DevM2L m;
+    int nrhs, kpad, nch, stages, row_chunks, nitems, nbuf;
+    uint32_t tmem_cols;
+    const uint4 *qh_hi, *qh_lo;   // rows of kpad elements (16-byte pieces)
+    int zero_row;                 // index of an all-zero qhat row
+    float *chat;
+    int *err;                     // device-visible error word (0 = ok)
+};
+
+template <bool kTF32> struct Fmt {
+    static constexpr int esize = kTF32 ? 4 : 2;
+    static constexpr int kc = 128 / esize;        // elements per 128-byte K chunk
+    static constexpr int kstep = kTF32 ? 8 : 16;  // K per MMA instruction (32 bytes)
+    static constexpr uint32_t ab = kTF32 ? 2u : 1u;
+};
+
+template <bool kTF32>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_m2l_tc(const __grid_constant__ CUtensorMap s_hi, const __grid_constant__ CUtensorMap s_lo,
+             TcArgs a) {
+    using F = Fmt<kTF32>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned base for the swizzled tiles
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int kp = a.kpad, S = a.stages;
+    const uint32_t a_bytes = 128 * 128;                // one split of X_t chunk
+    const uint32_t b_bytes = (uint32_t)kp * 128;       // one split of S_t chunk
+    const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)S * stage_bytes);
+    uint64_t *full_a = bars, *full_b = bars + S, *empty = bars + 2 * S;
+    uint64_t *acc_full = bars + 3 * S, *acc_empty = acc_full + 2, *done = acc_full + 4;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    volatile int *never = abort_flag + 1;  // stays 0: drains ignore the abort flag
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(&full_a[s], 128);
+            tc::mbar_init(&full_b[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&acc_full[b], 1);
+            tc::mbar_init(&acc_empty[b], 128);
+        }
+        tc::mbar_init(done, 1);
+        *abort_flag = 0;
+        *never = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 9) tc::tmem_alloc(tmem_slot, a.tmem_cols);
+    if (warp == 8 && lane == 0) {
+        tc::prefetch_tmap(&s_hi);
+        tc::prefetch_tmap(&s_lo);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    // TMEM columns: nbuf accumulators of kp columns, then the running total.
+    // With two accumulators the epilogue drains one while the MMAs fill the
+    // other.
+    const int nbuf = a.nbuf;
+    const uint32_t tot_col = (uint32_t)(nbuf * kp);
+
+    auto a_tile = [&](int s, int split) { return smem + (size_t)s * stage_bytes + split * a_bytes; };
+    auto b_tile = [&](int s, int split) {
+        return smem + (size_t)s * stage_bytes + 2 * a_bytes + split * b_bytes;
+    };
+    auto fail = [&](int role) {
+        *abort_flag = 1;
+        atomicOr(a.err, 1 << role);
+    };
+
+    if (warp < 4 || warp >= 10) {
+        // ------------------------------------------------ X_t row gatherers
+        // Two sets of 128 threads take alternate K chunks, so two chunks'
+        // loads are in flight while the MMAs consume a third.
+        const int set = warp < 4 ? 0 : 1;
+        const int r = set == 0 ? tid : tid - 320;  // row 0..127 of the tile
+        uint32_t j = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x) {
+            const int tile = item / a.row_chunks, rc = item - tile * a.row_chunks;
+            const int g = rc * 128 + r;
+            const int slot = g / a.nrhs, rhs = g - slot * a.nrhs;
+            const int e0 = a.m.tile_entry_ptr[tile], e1 = a.m.tile_entry_ptr[tile + 1];
+            for (int e = e0; e < e1 && ok; ++e) {
+                const int src = a.m.entry_src[(size_t)e * kTileRows + slot];
+                const int qrow = src >= 0 ? src * a.nrhs + rhs : a.zero_row;
+                const uint4 *hi = a.qh_hi + (size_t)qrow * (kp * F::esize / 16);
+                const uint4 *lo = a.qh_lo + (size_t)qrow * (kp * F::esize / 16);
+                for (int c = 0; c < a.nch && ok; ++c, ++j) {
+                    if ((int)(j & 1) != set) continue;
+                    const int s = j % S;
+                    const int valid = min(F::kc, kp - c * F::kc);   // elements in this chunk
+                    const int pieces = valid * F::esize / 16;        // 16-byte pieces (<= 8)
+                    uint4 vh[8], vl[8];
+#pragma unroll
+                    for (int p = 0; p < 8; ++p)
+                        if (p < pieces) {
+                            vh[p] = __ldg(hi + c * 8 + p);
+                            vl[p] = __ldg(lo + c * 8 + p);
+                        }
+                    ok = tc::mbar_wait(&empty[s], ((j / S) & 1) ^ 1, abort_flag, kWaitLimit);
+                    if (!ok) {
+                        if (!*abort_flag) fail(0);
+                        break;
+                    }
+                    unsigned char *th = a_tile(s, 0), *tl = a_tile(s, 1);
+                    const uint32_t row_off = (r >> 3) * 1024 + (r & 7) * 128;
+#pragma unroll
+                    for (int p = 0; p < 8; ++p)
+                        if (p < pieces) {
+                            const uint32_t off = row_off + ((p ^ (r & 7)) << 4);
+                            *reinterpret_cast<uint4 *>(th + off) = vh[p];
+                            *reinterpret_cast<uint4 *>(tl + off) = vl[p];
+                        }
+                    tc::fence_proxy_async_smem();
+                    tc::mbar_arrive(&full_a[s]);
+                }
+            }
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // ------------------------------------------------ epilogue
+        const int q = warp - 4;               // TMEM lane quarter
+        const int row = q * 32 + lane;
+        const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+        uint32_t gi = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x) {
+            const int tile = item / a.row_chunks, rc = item - tile * a.row_chunks;
+            const int g = rc * 128 + row;
+            const int slot = g / a.nrhs, rhs = g - slot * a.nrhs;
+            const int tgt = a.m.tile_target[(size_t)tile * kTileRows + slot];
+            const int ne = a.m.tile_entry_ptr[tile + 1] - a.m.tile_entry_ptr[tile];
+            const int ngroups = (ne + kGroup - 1) / kGroup;
+            for (int grp = 0; grp < ngroups; ++grp, ++gi) {
+                const int buf = gi % nbuf;
+                const uint32_t acc_col = (uint32_t)(buf * kp);
+                ok = tc::mbar_wait(&acc_full[buf], (gi / nbuf) & 1, abort_flag, kWaitLimit);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) {
+                    if (lane == 0 && !*abort_flag) fail(1);
+                    break;
+                }
+                tc::tc_fence_after();
+                const bool first = grp == 0, last = grp == ngroups - 1;
+                for (int cc = 0; cc < kp; cc += 16) {
+                    float v[16], t[16];
+                    tc::tmem_ld16(lane_addr + acc_col + cc, v);
+                    if (!first) tc::tmem_ld16(lane_addr + tot_col + cc, t);
+                    tc::tmem_wait_ld();
+                    if (first) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) t[i] = v[i];
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) t[i] += v[i];
+                    }
+                    if (last) {
+                        if (slot < kTileRows && tgt >= 0) {
+                            float4 *out = reinterpret_cast<float4 *>(
+                                a.chat + ((size_t)tgt * a.nrhs + rhs) * kp + cc);
+                            out[0] = make_float4(t[0], t[1], t[2], t[3]);
+                            out[1] = make_float4(t[4], t[5], t[6], t[7]);
+                            out[2] = make_float4(t[8], t[9], t[10], t[11]);
+                            out[3] = make_float4(t[12], t[13], t[14], t[15]);
+                        }
+                    } else {
+                        tc::tmem_st16(lane_addr + tot_col + cc, t);
+                    }
+                }
+                tc::tmem_wait_st();
+                tc::tc_fence_before();
+                tc::mbar_arrive(&acc_empty[buf]);
+            }
+        }
+    } else if (warp == 8) {
+        // ------------------------------------------------ TMA for S_t chunks
+        if (lane == 0) {
+            uint32_t j = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x) {
+                const int tile = item / a.row_chunks;
+                const int e0 = a.m.tile_entry_ptr[tile], e1 = a.m.tile_entry_ptr[tile + 1];
+                for (int e = e0; e < e1 && ok; ++e) {
+                    const int row0 = a.m.entry_offset[e] * kp;
+                    for (int c = 0; c < a.nch; ++c, ++j) {
+                        const int s = j % S;
+                        ok = tc::mbar_wait(&empty[s], ((j / S) & 1) ^ 1, abort_flag, kWaitLimit);
+                        if (!ok) {
+                            if (!*abort_flag) fail(2);
+                            break;
+                        }
+                        tc::mbar_arrive_expect_tx(&full_b[s], 2 * b_bytes);
+                        tc::tma_load_2d(b_tile(s, 0), &s_hi, &full_b[s], c * F::kc, row0);
+                        tc::tma_load_2d(b_tile(s, 1), &s_lo, &full_b[s], c * F::kc, row0);
+                    }
+                }
+            }
+            // on abort, let the copies already issued land before the block exits
+            if (!ok && j > 0) {
+                const uint32_t last = j - 1;
+                tc::mbar_wait(&full_b[last % S], (last / S) & 1, never, kWaitLimit);
+            }
+        }
+    } else {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t id = tc::idesc(F::ab, 128, (uint32_t)kp);
+            uint32_t j = 0, gi = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x) {
+                const int tile = item / a.row_chunks;
+                const int e0 = a.m.tile_entry_ptr[tile], e1 = a.m.tile_entry_ptr[tile + 1];
+                for (int eg = e0; eg < e1 && ok; eg += kGroup, ++gi) {
+                    const int buf = gi % nbuf;
+                    const uint32_t acc_col = (uint32_t)(buf * kp);
+                    ok = tc::mbar_wait(&acc_empty[buf], ((gi / nbuf) & 1) ^ 1, abort_flag,
+                                       kWaitLimit);
+                    if (!ok) {
+                        if (!*abort_flag) fail(3);
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    uint32_t accumulate = 0;
+                    const int eend = min(e1, eg + kGroup);
+                    for (int e = eg; e < eend && ok; ++e) {
+                        for (int c = 0; c < a.nch; ++c, ++j) {
+                            const int s = j % S;
+                            const uint32_t ph = (j / S) & 1;
+                            ok = tc::mbar_wait(&full_a[s], ph, abort_flag, kWaitLimit) &&
+                                 tc::mbar_wait(&full_b[s], ph, abort_flag, kWaitLimit);
+                            if (!ok) {
+                                if (!*abort_flag) fail(4);
+                                break;
+                            }
+                            tc::tc_fence_after();
+                            const int ksteps = min(F::kc, kp - c * F::kc) / F::kstep;
+                            const uint32_t ah = tc::smem_u32(a_tile(s, 0)), al = tc::smem_u32(a_tile(s, 1));
+                            const uint32_t bh = tc::smem_u32(b_tile(s, 0)), bl = tc::smem_u32(b_tile(s, 1));
+                            for (int k = 0; k < ksteps; ++k) {
+                                const uint32_t koff = (uint32_t)k * 32;
+                                const uint64_t dah = tc::sdesc_k128(ah + koff, 1024);
+                                const uint64_t dal = tc::sdesc_k128(al + koff, 1024);
+                                const uint64_t dbh = tc::sdesc_k128(bh + koff, 1024);
+                                const uint64_t dbl = tc::sdesc_k128(bl + koff, 1024);
+                                tc::mma<kTF32>(tmem + acc_col, dah, dbh, id, accumulate);
+                                accumulate = 1;
+                                tc::mma<kTF32>(tmem + acc_col, dah, dbl, id, 1);
+                                tc::mma<kTF32>(tmem + acc_col, dal, dbh, id, 1);
+                            }
+                            tc::mma_commit(&empty[s]);
+                        }
+                    }
+                    if (ok) tc::mma_commit(&acc_full[buf]);
+                }
+            }
+            // every MMA this thread issued has completed before TMEM is freed
+            tc::mma_commit(done);
+            tc::mbar_wait(done, 0, never, kWaitLimit);
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (warp == 9) tc::tmem_dealloc(tmem, a.tmem_cols);
+}
+
+// Split qhat (FP32) into hi/lo rows in the operand format; the row after the
+// last is all zero (the source of rows that have none).
+template <bool kTF32>
+__global__ void k_split_qhat(const float *__restrict__ qhat, int64_t nrows, int kp, void *hi,
+                             void *lo) {
+    const int64_t total = (nrows + 1) * kp;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = i < nrows * kp ? qhat[i] : 0.f;
+        if (kTF32) {
+            uint32_t h, l;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+            const float r = x - __uint_as_float(h);
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
+            static_cast<uint32_t *>(hi)[i] = h;
+            static_cast<uint32_t *>(lo)[i] = l;
+        } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+            static_cast<__nv_bfloat16 *>(hi)[i] = h;
+            static_cast<__nv_bfloat16 *>(lo)[i] = l;
+        }
+    }
+}
+
+} // namespace
+
+size_t m2l_tc_smem(int kpad, int *stages) {
+    const size_t stage = 2 * 128 * 128 + 2 * (size_t)kpad * 128;
+    const size_t budget = 227 * 1024 - 1024 - 256;
+    int s = (int)(budget / stage);
+    if (s > 4) s = 4;
+    if (stages) *stages = s;
+    return 1024 + (size_t)s * stage + 256;
+}
+
+cudaError_t launch_m2l_tc(const DevM2L &m, const DevOps &o, const DevWork &w, int nnodes,
+                          bool tf32, const CUtensorMap &s_hi, const CUtensorMap &s_lo,
+                          void *qh_hi, void *qh_lo, int *err, int num_sms, cudaStream_t st) {
+    if (m.ntiles == 0) return cudaSuccess;
+    const int kp = o.kpad;
+    const int64_t nrows = (int64_t)nnodes * w.nrhs;
+    // 1. operand split of the compressed multipoles
+    {
+        int64_t total = (nrows + 1) * kp;
+        int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 16);
+        if (tf32)
+            k_split_qhat<true><<<blocks, 256, 0, st>>>(w.qhat, nrows, kp, qh_hi, qh_lo);
+        else
+            k_split_qhat<false><<<blocks, 256, 0, st>>>(w.qhat, nrows, kp, qh_hi, qh_lo);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    TcArgs a;
+    a.m = m;
+    a.nrhs = w.nrhs;
+    a.kpad = kp;
+    a.nch = (kp * (tf32 ? 4 : 2) + 127) / 128;
+    a.row_chunks = w.nrhs;
+    a.nitems = m.ntiles * a.row_chunks;
+    a.nbuf = 3 * kp <= 512 ? 2 : 1;
+    uint32_t cols = 32;
+    while (cols < (uint32_t)((a.nbuf + 1) * kp)) cols <<= 1;
+    a.tmem_cols = cols;
+    a.qh_hi = static_cast<const uint4 *>(qh_hi);
+    a.qh_lo = static_cast<const uint4 *>(qh_lo);
+    a.zero_row = (int)nrows;
+    a.chat = w.chat;
+    a.err = err;
+    const size_t sm = m2l_tc_smem(kp, &a.stages);
+    const int grid = std::min(a.nitems, num_sms);
+    cudaError_t e;
+    if (tf32) {
+        e = cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_m2l_tc<true><<<grid, kThreads, sm, st>>>(s_hi, s_lo, a);
+    } else {
+        e = cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_m2l_tc<false><<<grid, kThreads, sm, st>>>(s_hi, s_lo, a);
+    }
+    return cudaGetLastError();
+}
+
+} // namespace kifmm

@@ -58,13 +58,15 @@ extern "C" fmm_status fmm_evaluate_noalloc(fmm_plan_t plan, const float *charges
     if (dev < 0 || dev >= kMaxDevices) return fail(FMM_ERR_UNSUPPORTED, "device ordinal too large");
     cudaError_t e = cudaSetDevice(dev);
     if (e != cudaSuccess) return fail(FMM_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    if (fmm_status err = kifmm::plan_check_device_error(plan)) return err;
     if (!is_device_pointer(charges) || !is_device_pointer(potentials))
         return fail(FMM_ERR_INVALID_ARG,
                     "fmm_evaluate_noalloc needs device pointers (host buffers would need staging)");
 
     kifmm::WorkspaceBytes wb;
     kifmm::plan_workspace_bytes(plan, nrhs, &wb);
-    const size_t sizes[6] = {wb.qs, wb.up, wb.down, wb.qhat, wb.chat, wb.xchk};
+    const size_t sizes[11] = {wb.qs, wb.up,  wb.down, wb.qhat, wb.chat, wb.xchk,
+                              wb.qh, wb.qh,  wb.chk,  wb.ybuf, wb.yp};
     size_t total = 0;
     for (size_t s : sizes) total += align256(s);
     if (total > kNoAllocScratchBytes)
@@ -90,8 +92,8 @@ extern "C" fmm_status fmm_evaluate_noalloc(fmm_plan_t plan, const float *charges
     // later reads within the same call, so nothing has to start at zero and
     // the previous call's contents are harmless.
     unsigned char *p = static_cast<unsigned char *>(base);
-    float *parts[6];
-    for (int i = 0; i < 6; ++i) {
+    float *parts[11];
+    for (int i = 0; i < 11; ++i) {
         parts[i] = reinterpret_cast<float *>(p);
         p += align256(sizes[i]);
     }
@@ -102,6 +104,11 @@ extern "C" fmm_status fmm_evaluate_noalloc(fmm_plan_t plan, const float *charges
     b.qhat = parts[3];
     b.chat = parts[4];
     b.xchk = parts[5];
+    b.qh_hi = wb.qh ? parts[6] : nullptr;
+    b.qh_lo = wb.qh ? parts[7] : nullptr;
+    b.chk = parts[8];
+    b.ybuf = parts[9];
+    b.yp = parts[10];
     fmm_status s = kifmm::plan_enqueue(plan, charges, nrhs, potentials, b,
                                        static_cast<cudaStream_t>(stream));
     return s;  // on failure plan_enqueue has set the message fmm_last_error() returns

@@ -12,17 +12,24 @@ namespace kifmm {
 struct WorkBuffers {
     float *qs = nullptr, *up = nullptr, *down = nullptr, *qhat = nullptr, *chat = nullptr,
           *xchk = nullptr;
+    float *qh_hi = nullptr, *qh_lo = nullptr;  // tensor-core M2L operand splits
+    float *chk = nullptr, *ybuf = nullptr, *yp = nullptr;  // level-product temporaries
 };
 
 // Byte sizes of those buffers for one plan and nrhs.
 struct WorkspaceBytes {
     size_t qs = 0, up = 0, down = 0, qhat = 0, chat = 0, xchk = 0;
+    size_t qh = 0;  // each of the two operand splits (0 for the FP32 M2L)
+    size_t chk = 0, ybuf = 0, yp = 0;
 };
 
 void plan_workspace_bytes(const fmm_plan_s *P, int nrhs, WorkspaceBytes *out);
 fmm_status plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, double *pot,
                         const WorkBuffers &b, cudaStream_t st);
 int plan_device(const fmm_plan_s *P);
+int plan_m2l_mode(const fmm_plan_s *P);
+// FMM_ERR_TIMEOUT (once) if a device-side bounded wait expired, else FMM_OK.
+fmm_status plan_check_device_error(fmm_plan_s *P);
 // Record the message fmm_last_error() returns on this thread; returns s.
 fmm_status plan_set_error(fmm_status s, const std::string &msg);
 bool plan_host_only(const fmm_plan_s *P);
