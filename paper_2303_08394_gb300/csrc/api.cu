@@ -522,7 +522,8 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
     ++launches;
     const DevOps &o = P->dops;
     const int ns = o.ns, rP = o.rP, rQ = o.rQ, kp = o.kpad;
-    const int rPp = (rP + 3) & ~3, rQp = (rQ + 3) & ~3;  // y rows, 16-byte aligned
+    // row strides of the per-box arrays, all 16-byte aligned
+    const int nsp = (ns + 3) & ~3, rPp = (rP + 3) & ~3, rQp = (rQ + 3) & ~3;
     auto gemm = [&](VGemm &g) -> fmm_status {
         g.nrhs = nrhs;
         if (g.count > 0) ++launches;
@@ -548,14 +549,14 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
         g.nseg = 1;
         g.seg[0] = seg(o.PvT, rP, b.ybuf, rPp, nullptr, 0);
         g.dst = b.up;
-        g.dst_ld = ns;
+        g.dst_ld = nsp;
         g.dst_idx = nodes;
         if (fmm_status e = gemm(g)) return e;
         VGemm h{};
         h.m = kp;
         h.count = count;
         h.nseg = 1;
-        h.seg[0] = seg(o.Vk, ns, b.up, ns, nodes, 0);
+        h.seg[0] = seg(o.Vk, ns, b.up, nsp, nodes, 0);
         h.dst = b.qhat;
         h.dst_ld = kp;
         h.dst_idx = nodes;
@@ -566,12 +567,12 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
         const int np = (int)sc.p2m_nodes.size();
         if (np > 0) {
             ++launches;
-            CK(launch_p2m_check(P->dt, o, w, P->d_p2m, np, b.chk, ns, st));
+            CK(launch_p2m_check(P->dt, o, w, P->d_p2m, np, b.chk, nsp, st));
             VGemm g{};
             g.m = rP;
             g.count = np;
             g.nseg = 1;
-            g.seg[0] = seg(o.Pu, ns, b.chk, ns, nullptr, 0);
+            g.seg[0] = seg(o.Pu, ns, b.chk, nsp, nullptr, 0);
             g.scale = o.Ps_inv;
             g.dst = b.ybuf;
             g.dst_ld = rPp;
@@ -589,7 +590,7 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
             g.count = cnt;
             g.nseg = 8;
             for (int sg = 0; sg < 8; ++sg)
-                g.seg[sg] = seg(o.M2M + (size_t)sg * ns * mp, ns, b.up, ns,
+                g.seg[sg] = seg(o.M2M + (size_t)sg * ns * mp, ns, b.up, nsp,
                                 P->d_m2m_child + (size_t)sg * total + a0, 0);
             g.scale = o.Ps_inv;
             g.dst = b.ybuf;
@@ -630,7 +631,7 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
                 g.m = 8 * rQ;
                 g.count = pc;
                 g.nseg = 1;
-                g.seg[0] = seg(o.L2L, ns, b.down, ns, P->d_m2m + a0, 0);
+                g.seg[0] = seg(o.L2L, ns, b.down, nsp, P->d_m2m + a0, 0);
                 g.dst = b.yp;
                 g.dst_ld = 8 * rQ;
                 if (fmm_status e = gemm(g)) return e;
@@ -642,7 +643,7 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
             g.nseg = 1;
             g.seg[0] = seg(o.QUkT, kp, b.chat, kp, P->d_chat_src + b0, 0);
             if (!sc.x_nodes.empty()) {
-                g.seg[1] = seg(o.Qu, ns, b.xchk, ns, P->dt.x_slot + b0, 0);
+                g.seg[1] = seg(o.Qu, ns, b.xchk, nsp, P->dt.x_slot + b0, 0);
                 g.nseg = 2;
             }
             g.scale = o.Qs_inv;
@@ -662,7 +663,7 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
             h.nseg = 1;
             h.seg[0] = seg(o.QvT, rQ, b.ybuf, rQp, nullptr, 0);
             h.dst = b.down;
-            h.dst_ld = ns;
+            h.dst_ld = nsp;
             h.dst_base = b0;
             if (fmm_status e = gemm(h)) return e;
         }
@@ -678,7 +679,7 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
 // Bytes of each per-evaluation buffer of plan P for nrhs right-hand sides.
 void kifmm::plan_workspace_bytes(const fmm_plan_s *P, int nrhs, WorkspaceBytes *out) {
     const Tree &t = P->tree;
-    const size_t nn = (size_t)t.nodes(), ns = P->ops->ns, kp = P->kpad;
+    const size_t nn = (size_t)t.nodes(), ns = (P->ops->ns + 3) & ~3, kp = P->kpad;
     const size_t nx = P->sched.x_nodes.size();
     out->qs = (size_t)t.n * nrhs * sizeof(float);
     out->up = out->down = nn * nrhs * ns * sizeof(float);

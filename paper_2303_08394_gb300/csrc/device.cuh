@@ -61,8 +61,9 @@ struct DevM2L {
     const int *entry_src;       // entries x 128
 };
 
-// Buffers of one evaluation.  Densities: [node][rhs][ns]; compressed M2L
-// vectors: [node][rhs][kpad]; P2L check potentials: [x slot][rhs][ns].
+// Buffers of one evaluation.  Densities: [node][rhs][round4(ns)];
+// compressed M2L vectors: [node][rhs][kpad]; P2L check potentials:
+// [x slot][rhs][round4(ns)].
 struct DevWork {
     int nrhs;
     const float *charges_user;  // n x nrhs, caller order

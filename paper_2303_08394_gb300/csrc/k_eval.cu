@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
     float(*sq)[32] = s_q[wid];
     const int gwarp = blockIdx.x * kWarpsPerBlock + wid;
     const int nwarps = gridDim.x * kWarpsPerBlock;
-    const int ns = o.ns;
+    const int ns = o.ns, nsp = (o.ns + 3) & ~3;  // surface rows are padded to nsp
     for (int li = gwarp; li < t.nleaves; li += nwarps) {
         const int b = t.leaves[li];
         const float4 gb = t.geom[b];
@@ -103,12 +103,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
                     __syncwarp();
                     if (j < ns) {
                         float4 s = o.surf[j];
-                        const float *d = w.down + ((size_t)b * w.nrhs + r0) * ns + j;
+                        const float *d = w.down + ((size_t)b * w.nrhs + r0) * nsp + j;
                         spos[lane] = make_float4(rad * s.x, rad * s.y, rad * s.z,
                                                  NR == 1 ? d[0] : 0.f);
                         if (NR > 1) {
 #pragma unroll
-                            for (int r = 0; r < NR; ++r) sq[r][lane] = d[(size_t)r * ns];
+                            for (int r = 0; r < NR; ++r) sq[r][lane] = d[(size_t)r * nsp];
                         }
                     }
                     __syncwarp();
@@ -126,12 +126,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
                     __syncwarp();
                     if (j < ns) {
                         float4 s = o.surf[j];
-                        const float *d = w.up + ((size_t)a * w.nrhs + r0) * ns + j;
+                        const float *d = w.up + ((size_t)a * w.nrhs + r0) * nsp + j;
                         spos[lane] = make_float4(sx + rad * s.x, sy + rad * s.y,
                                                  sz + rad * s.z, NR == 1 ? d[0] : 0.f);
                         if (NR > 1) {
 #pragma unroll
-                            for (int r = 0; r < NR; ++r) sq[r][lane] = d[(size_t)r * ns];
+                            for (int r = 0; r < NR; ++r) sq[r][lane] = d[(size_t)r * nsp];
                         }
                     }
                     __syncwarp();

@@ -13,15 +13,14 @@ namespace kifmm {
 
 namespace {
 
-// Upward check potential of leaf `pos` at check point j, all rhs of the
-// chunk: thread per (leaf, j); the leaf's points are read as warp-wide
-// broadcasts.
+// Upward check potential of leaf `pos` at check point j for NR right-hand
+// sides from r0: thread per (leaf, j); the leaf's points are read as
+// warp-wide broadcasts.
+template <int NR>
 __global__ void __launch_bounds__(128) k_p2m_check(DevTree t, DevOps o, DevWork w,
                                                    const int *nodes, int count, float *chk,
-                                                   int ld, int nr) {
+                                                   int ld, int r0) {
     const int ns = o.ns;
-    const int r0 = blockIdx.y * nr;
-    const int nrr = min(nr, w.nrhs - r0);
     const int64_t total = (int64_t)count * ns;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -31,9 +30,9 @@ __global__ void __launch_bounds__(128) k_p2m_check(DevTree t, DevOps o, DevWork 
         const int2 rg = t.range[node];
         const float4 s = o.surf[j];
         const float cx = o.ao * s.x, cy = o.ao * s.y, cz = o.ao * s.z;
-        float acc[kMaxRhs];
+        float acc[NR];
 #pragma unroll
-        for (int r = 0; r < kMaxRhs; ++r) acc[r] = 0.f;
+        for (int r = 0; r < NR; ++r) acc[r] = 0.f;
 #pragma unroll 4
         for (int i = rg.x; i < rg.y; ++i) {
             const float4 p = __ldg(t.pts + i);
@@ -42,10 +41,10 @@ __global__ void __launch_bounds__(128) k_p2m_check(DevTree t, DevOps o, DevWork 
             const float inv = r2 > 0.f ? KIFMM_RSQRT(r2) : 0.f;
             const float *q = w.qs + (size_t)i * w.nrhs + r0;
 #pragma unroll
-            for (int r = 0; r < kMaxRhs; ++r)
-                if (r < nrr) acc[r] = fmaf(__ldg(q + r), inv, acc[r]);
+            for (int r = 0; r < NR; ++r) acc[r] = fmaf(__ldg(q + r), inv, acc[r]);
         }
-        for (int r = 0; r < nrr; ++r) chk[((size_t)pos * w.nrhs + r0 + r) * ld + j] = acc[r];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) chk[((size_t)pos * w.nrhs + r0 + r) * ld + j] = acc[r];
     }
 }
 
@@ -60,7 +59,7 @@ __global__ void __launch_bounds__(128) k_p2l(DevTree t, DevOps o, DevWork w, con
     const int nrr = min(nr, w.nrhs - r0);
     const float4 gb = t.geom[b];
     const float inv_h = 1.f / gb.w;
-    const int ns = o.ns;
+    const int ns = o.ns, nsp = (o.ns + 3) & ~3;
     const int slot = t.x_slot[b];
     for (int j0 = 0; j0 < ns; j0 += blockDim.x) {
         const int j = j0 + threadIdx.x;
@@ -99,7 +98,7 @@ __global__ void __launch_bounds__(128) k_p2l(DevTree t, DevOps o, DevWork w, con
         }
         if (j < ns)
             for (int r = 0; r < nrr; ++r)
-                w.xchk[((size_t)slot * w.nrhs + r0 + r) * ns + j] = acc[r];
+                w.xchk[((size_t)slot * w.nrhs + r0 + r) * nsp + j] = acc[r];
     }
 }
 
@@ -125,15 +124,27 @@ cudaError_t launch_gather_charges(const DevTree &t, const DevWork &w, cudaStream
     return cudaGetLastError();
 }
 
+template <int NR>
+cudaError_t p2m_check_nr(const DevTree &t, const DevOps &o, const DevWork &w, const int *nodes,
+                         int count, float *chk, int ld, int r0, cudaStream_t s) {
+    const int64_t total = (int64_t)count * o.ns;
+    const int blocks = (int)std::min<int64_t>((total + 127) / 128, 152 * 32);
+    k_p2m_check<NR><<<blocks, 128, 0, s>>>(t, o, w, nodes, count, chk, ld, r0);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_p2m_check(const DevTree &t, const DevOps &o, const DevWork &w,
                              const int *nodes, int count, float *chk, int ld, cudaStream_t s) {
     if (count == 0) return cudaSuccess;
-    const int nr = rhs_chunk(w.nrhs);
-    const int64_t total = (int64_t)count * o.ns;
-    int blocks = (int)std::min<int64_t>((total + 127) / 128, 152 * 32);
-    const dim3 grid(blocks, (w.nrhs + nr - 1) / nr);
-    k_p2m_check<<<grid, 128, 0, s>>>(t, o, w, nodes, count, chk, ld, nr);
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    for (int r0 = 0; r0 < w.nrhs && e == cudaSuccess;) {
+        const int left = w.nrhs - r0;
+        if (left >= 8) { e = p2m_check_nr<8>(t, o, w, nodes, count, chk, ld, r0, s); r0 += 8; }
+        else if (left >= 4) { e = p2m_check_nr<4>(t, o, w, nodes, count, chk, ld, r0, s); r0 += 4; }
+        else if (left >= 2) { e = p2m_check_nr<2>(t, o, w, nodes, count, chk, ld, r0, s); r0 += 2; }
+        else { e = p2m_check_nr<1>(t, o, w, nodes, count, chk, ld, r0, s); r0 += 1; }
+    }
+    return e;
 }
 
 cudaError_t launch_p2l(const DevTree &t, const DevOps &o, const DevWork &w, const int *nodes,

@@ -10,44 +10,87 @@
 // of 4 floats) with a source array whose row for vector v is chosen through
 // an index list (a child, the parent, the box itself, ...; -1 reads zeros).
 //
-// Tiling: a block computes 64 output rows x 32 vectors, 128 threads, each a
-// 4 x 4 register tile; K advances in chunks of 16 through shared memory
-// (operands read as float4).  The next chunk is loaded into registers while
-// the current one is multiplied.
+// Tiling: a block computes 64 output rows x 32 vectors with 128 threads,
+// each a 4 x 4 register tile (rows 4*tr.., vectors tv + 8 q).  K advances in
+// chunks of 16; chunks are copied global -> shared with cp.async, kStages
+// chunks in flight, so the per-chunk L2 round trip is paid once per
+// kStages chunks.  Missing sources and the ragged end of K are zero-filled
+// by the copies themselves (source size below 16 bytes).  Every source and
+// operator row stride is a multiple of 4 floats, so each 16-byte copy is
+// aligned.
 #include "device.cuh"
 
 namespace kifmm {
 
 namespace {
 
-constexpr int BM = 64, BV = 32, BK = 16;
+constexpr int BM = 64, BV = 32, BK = 16, kStages = 4;
+constexpr int XLD = BK + 4;  // padded row of the vector tile (floats)
 
-__device__ __forceinline__ float4 load_vec4(const float *row, int j, int n) {
-    // four consecutive elements of a source row, zero past its end
-    if (j + 4 <= n && ((reinterpret_cast<uintptr_t>(row + j) & 15) == 0))
-        return __ldg(reinterpret_cast<const float4 *>(row + j));
-    float4 r;
-    r.x = j + 0 < n ? __ldg(row + j + 0) : 0.f;
-    r.y = j + 1 < n ? __ldg(row + j + 1) : 0.f;
-    r.z = j + 2 < n ? __ldg(row + j + 2) : 0.f;
-    r.w = j + 3 < n ? __ldg(row + j + 3) : 0.f;
-    return r;
+__device__ __forceinline__ void cp16(void *dst, const void *src, int bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src), "r"(bytes)
+                 : "memory");
 }
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_stages() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(kStages - 1) : "memory");
+}
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
-    __shared__ __align__(16) float As[2][BK][BM];
-    __shared__ __align__(16) float Xs[2][BK][BV + 4];
+    __shared__ __align__(16) float As[kStages][BK][BM];     // As[.][j][i]
+    __shared__ __align__(16) float Xs[kStages][BV][XLD];    // Xs[.][v][j]
     const int tid = threadIdx.x;
-    const int tr = tid >> 3, tv = tid & 7;         // 16 row groups x 8 vector groups
+    const int tr = tid >> 3, tv = tid & 7;
     const int i0 = blockIdx.y * BM;
     const int v0 = blockIdx.x * BV;
     const int nvec = g.count * g.nrhs;
+    const int mp = (g.m + 3) & ~3;
 
-    // the vector this thread loads for the X tile, and its list position
-    const int lv = tid >> 2, lq = tid & 3;          // 32 vectors x 4 float4 pieces
+    // the vector this thread copies (32 vectors x 4 pieces of 4 floats)
+    const int lv = tid >> 2, lq = tid & 3;
     const int vload = v0 + lv;
     const int pos_l = vload < nvec ? vload / g.nrhs : -1;
     const int rhs_l = vload < nvec ? vload - pos_l * g.nrhs : 0;
+
+    int total_chunks = 0;
+    for (int s = 0; s < g.nseg; ++s) total_chunks += (g.seg[s].n + BK - 1) / BK;
+
+    // copy chunk `c` (flattened over the segments) into stage `st`
+    auto issue = [&](int c) {
+        if (c < total_chunks) {
+            int s = 0, cc = c;
+            while (cc >= (g.seg[s].n + BK - 1) / BK) {
+                cc -= (g.seg[s].n + BK - 1) / BK;
+                ++s;
+            }
+            const VSeg &sg = g.seg[s];
+            const int st = c % kStages;
+            const int j0 = cc * BK;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q = tid + h * 128;            // 16 rows x 16 pieces
+                const int jj = q >> 4, ii = (q & 15) * 4;
+                const int j = j0 + jj, i = i0 + ii;
+                const bool in = j < sg.n && i < mp;
+                cp16(&As[st][jj][ii], in ? sg.AT + (size_t)j * mp + i : sg.AT, in ? 16 : 0);
+            }
+            int bytes = 0;
+            const float *src = sg.src;
+            if (pos_l >= 0) {
+                const int node = sg.src_idx ? sg.src_idx[pos_l] : sg.src_base + pos_l;
+                const int j = j0 + lq * 4;
+                if (node >= 0 && j < sg.n) {
+                    src = sg.src + ((size_t)node * g.nrhs + rhs_l) * sg.src_ld + j;
+                    bytes = 4 * min(4, sg.n - j);
+                }
+            }
+            cp16(&Xs[st][lv][lq * 4], src, bytes);
+        }
+        cp_commit();
+    };
 
     float acc[4][4];
 #pragma unroll
@@ -55,81 +98,40 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
 
-    // flattened K chunks over all segments
-    int total_chunks = 0;
-    for (int s = 0; s < g.nseg; ++s) total_chunks += (g.seg[s].n + BK - 1) / BK;
-
-    float4 ra[2], rx;
-    auto fetch = [&](int chunk) {
-        int s = 0, c = chunk;
-        while (c >= (g.seg[s].n + BK - 1) / BK) {
-            c -= (g.seg[s].n + BK - 1) / BK;
-            ++s;
-        }
-        const VSeg &sg = g.seg[s];
-        const int j0 = c * BK;
-        const int mp = (g.m + 3) & ~3;
-        // A: 16 rows (j) x 64 columns (i) of AT, 2 float4 per thread
+    for (int c = 0; c < kStages - 1; ++c) issue(c);
+    for (int c = 0; c < total_chunks; ++c) {
+        issue(c + kStages - 1);
+        cp_wait_stages();
+        __syncthreads();
+        const int st = c % kStages;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int q = tid + h * 128;            // 0..255
-            const int jj = q >> 4, ii = (q & 15) * 4;
-            const int j = j0 + jj, i = i0 + ii;
-            if (j < sg.n && i < mp)
-                ra[h] = __ldg(reinterpret_cast<const float4 *>(sg.AT + (size_t)j * mp + i));
-            else
-                ra[h] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        // X: 32 vectors x 16 elements, 1 float4 per thread
-        rx = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (pos_l >= 0) {
-            const int node = sg.src_idx ? sg.src_idx[pos_l] : sg.src_base + pos_l;
-            if (node >= 0) {
-                const float *row = sg.src + ((size_t)node * g.nrhs + rhs_l) * sg.src_ld;
-                rx = load_vec4(row, j0 + lq * 4, sg.n);
+        for (int k4 = 0; k4 < BK; k4 += 4) {
+            float a[4][4], x[4][4];  // a[kk][row], x[vec][kk]
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float4 t = *reinterpret_cast<const float4 *>(&As[st][k4 + e][tr * 4]);
+                a[e][0] = t.x; a[e][1] = t.y; a[e][2] = t.z; a[e][3] = t.w;
             }
-        }
-    };
-    auto stash = [&](int buf) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int q = tid + h * 128;
-            *reinterpret_cast<float4 *>(&As[buf][q >> 4][(q & 15) * 4]) = ra[h];
+            for (int q = 0; q < 4; ++q) {
+                const float4 t = *reinterpret_cast<const float4 *>(&Xs[st][tv + 8 * q][k4]);
+                x[q][0] = t.x; x[q][1] = t.y; x[q][2] = t.z; x[q][3] = t.w;
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a[e][p], x[q][e], acc[p][q]);
         }
-        Xs[buf][lq * 4 + 0][lv] = rx.x;
-        Xs[buf][lq * 4 + 1][lv] = rx.y;
-        Xs[buf][lq * 4 + 2][lv] = rx.z;
-        Xs[buf][lq * 4 + 3][lv] = rx.w;
-    };
-
-    if (total_chunks > 0) {
-        fetch(0);
-        stash(0);
         __syncthreads();
     }
-    for (int c = 0; c < total_chunks; ++c) {
-        const int buf = c & 1;
-        if (c + 1 < total_chunks) fetch(c + 1);
-#pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            const float4 a = *reinterpret_cast<const float4 *>(&As[buf][kk][tr * 4]);
-            const float4 x = *reinterpret_cast<const float4 *>(&Xs[buf][kk][tv * 4]);
-            const float av[4] = {a.x, a.y, a.z, a.w}, xv[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], xv[q], acc[p][q]);
-        }
-        if (c + 1 < total_chunks) {
-            stash(buf ^ 1);
-            __syncthreads();
-        }
-    }
+    cp_wait_all();
 
     // epilogue
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const int v = v0 + tv * 4 + q;
+        const int v = v0 + tv + 8 * q;
         if (v >= nvec) continue;
         const int pos = v / g.nrhs, rhs = v - pos * g.nrhs;
         const int dnode = g.dst_idx ? g.dst_idx[pos] : g.dst_base + pos;
@@ -158,6 +160,8 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
 cudaError_t launch_vgemm(const VGemm &g, cudaStream_t s) {
     if (g.count == 0) return cudaSuccess;
     if (g.nseg < 1 || g.nseg > kMaxSeg) return cudaErrorInvalidValue;
+    for (int k = 0; k < g.nseg; ++k)
+        if ((g.seg[k].src_ld & 3) != 0) return cudaErrorInvalidValue;  // 16-byte rows
     const int nvec = g.count * g.nrhs;
     const dim3 grid((nvec + BV - 1) / BV, (g.m + BM - 1) / BM);
     if (grid.y > 65535u) return cudaErrorInvalidValue;
