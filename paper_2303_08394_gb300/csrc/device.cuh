@@ -6,13 +6,22 @@
 
 #include "constants.h"
 
-// Reciprocal square root used by every kernel evaluation 1/r (MUFU rsqrt,
-// <= 2 ulp).  A build may define KIFMM_RSQRT to trade speed for rounding.
+// Reciprocal square root used by every kernel evaluation 1/r: the PTX
+// rsqrt.approx.ftz.f32 instruction (relative error about 2^-23; squared
+// distances below the smallest normal float are flushed to zero, which only
+// the self pairs reach).  A build may define KIFMM_RSQRT to trade speed for
+// rounding.
 #ifndef KIFMM_RSQRT
-#define KIFMM_RSQRT(x) rsqrtf(x)
+#define KIFMM_RSQRT(x) ::kifmm::rsqrt_approx(x)
 #endif
 
 namespace kifmm {
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // Tree and lists on the device (all indices are node ids in plan order).
 struct DevTree {

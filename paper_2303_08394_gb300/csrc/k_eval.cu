@@ -1,21 +1,52 @@
 // Leaf evaluation: near field over U ("P2P"), L2P from the leaf's own
 // downward density, and M2P from the upward densities of its W list
 // ("Computational structure of FMM operators": all three are evaluations of
-// Eq. (1) between point sets).  One warp owns one target leaf and 32 of its
-// targets at a time (one per lane); sources are staged 32 at a time in the
-// warp's shared memory and read as broadcasts.
+// Eq. (1) between point sets, so they share one loop).
 //
-// Precision: FP32 rsqrt/FMA per pair; each 32-source batch is summed in
-// plain FP32 and added into a per-target Kahan (sum, compensation) pair;
-// the final potential is formed in FP64, scaled by 1/(4 pi hw) and written
-// in the caller's point order.
+// One block of 128 threads owns one target leaf B.  Its sources form a list
+// of segments: B's own points, the points of the other leaves in U(B), B's
+// downward equivalent surface (charges = downward density) and the upward
+// equivalent surface of every box in W(B) (charges = upward density).  The
+// segment table is built in shared memory with a block scan; then all 128
+// threads copy up to CAP sources at once into shared memory, positions
+// shifted into B's frame (leaf-relative coordinates plus the exact dyadic
+// difference of box centres, so no precision is lost at deep levels).
+//
+// Compute: a warp owns a chunk of 16 T targets, T = 1..4 chosen per leaf
+// from its size: lane l holds targets (l mod 16) + 16 i, i < T, and the two
+// half-warps take alternate staged sources, so one shared-memory access
+// (two adjacent 16-byte words) feeds 2 T pairs per lane.  Leaves with at
+// most 16 T targets use one chunk and the four warps split the sources.
+// The staged count is padded with zero charges far away so the inner loop
+// is unrolled; the r > 0 test that drops the self pair runs only over B's
+// own points.
+//
+// Precision: FP32 rsqrt/FMA per pair.  Each run of 32 sources per lane is
+// summed in plain FP32 and added into a per-target Kahan (sum,
+// compensation) pair; the pairs of the two half-warps and of the source
+// slices are merged with further Kahan additions in a fixed order, and the
+// potential is formed in FP64 (sum - compensation), scaled by 1/(4 pi hw)
+// and written in the caller's point order.  Runs are assigned from the
+// source order alone, so every right-hand side gets bit-identical
+// arithmetic whatever NR it is batched in.
 #include "device.cuh"
 
 namespace kifmm {
 
 namespace {
 
-constexpr int kWarpsPerBlock = 8;
+constexpr int kWarps = 4, kThreads = 32 * kWarps;
+constexpr int kSegCap = 256;       // segments per table window
+constexpr float kFar = 1.0e15f;    // position of padding sources (charge 0)
+
+// Staged sources per round; targets per lane go up to kTMax for every NR so
+// that the work split (and the rounding) is the same for every column.
+constexpr int kTMax = 4;
+// minb: resident blocks per SM the register allocation must allow.
+template <int NR> struct Cfg {
+    static constexpr int cap = NR == 1 ? 1024 : (NR == 2 ? 768 : 512);
+    static constexpr int minb = NR <= 2 ? 6 : 1;
+};
 
 struct Kahan {
     float s = 0.f, c = 0.f;
@@ -25,134 +56,317 @@ struct Kahan {
         c = __fsub_rn(__fsub_rn(t, s), y);
         s = t;
     }
-    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+    // merge another (sum, compensation) pair
+    __device__ __forceinline__ void merge(float s2, float c2) {
+        add(s2);
+        add(-c2);
+    }
 };
 
-// One batch of up to 32 staged sources against this lane's target.
-template <int NR>
-__device__ __forceinline__ void batch(const float4 *spos, const float (*sq)[32], int cnt,
-                                      float tx, float ty, float tz, Kahan *acc) {
-    float part[NR];
+template <int NR> struct Charges;
+template <> struct Charges<2> {
+    __device__ static void get(const float *sq, int j, float (&q)[2]) {
+        const float2 v = reinterpret_cast<const float2 *>(sq)[j];
+        q[0] = v.x; q[1] = v.y;
+    }
+};
+template <> struct Charges<4> {
+    __device__ static void get(const float *sq, int j, float (&q)[4]) {
+        const float4 v = reinterpret_cast<const float4 *>(sq)[j];
+        q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
+    }
+};
+template <> struct Charges<8> {
+    __device__ static void get(const float *sq, int j, float (&q)[8]) {
+        const float4 a = reinterpret_cast<const float4 *>(sq)[2 * j];
+        const float4 b = reinterpret_cast<const float4 *>(sq)[2 * j + 1];
+        q[0] = a.x; q[1] = a.y; q[2] = a.z; q[3] = a.w;
+        q[4] = b.x; q[5] = b.y; q[6] = b.z; q[7] = b.w;
+    }
+};
+
+// Staged sources j = a + 2u + h (j < e; a and e multiples of 16) against
+// this lane's T targets; h is the lane's half-warp.
+template <int NR, int T, bool kSelf>
+__device__ __forceinline__ void run(const float4 *spos, const float *sq, int a, int e, int h,
+                                    const float3 (&x)[T], float (&part)[T][NR]) {
+    for (int j = a + h; j < e; j += 16) {
 #pragma unroll
-    for (int r = 0; r < NR; ++r) part[r] = 0.f;
-    for (int j = 0; j < cnt; ++j) {
-        const float4 p = spos[j];
-        const float dx = p.x - tx, dy = p.y - ty, dz = p.z - tz;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float inv = r2 > 0.f ? KIFMM_RSQRT(r2) : 0.f;
-        if (NR == 1) {
-            part[0] = fmaf(p.w, inv, part[0]);
-        } else {
+        for (int u = 0; u < 8; ++u) {
+            const float4 p = spos[j + 2 * u];
+            float q[NR];
+            if constexpr (NR == 1) {
+                q[0] = p.w;
+            } else {
+                Charges<NR>::get(sq, j + 2 * u, q);
+            }
 #pragma unroll
-            for (int r = 0; r < NR; ++r) part[r] = fmaf(sq[r][j], inv, part[r]);
+            for (int i = 0; i < T; ++i) {
+                const float dx = p.x - x[i].x, dy = p.y - x[i].y, dz = p.z - x[i].z;
+                // Outside B's own points a pair is never coincident in exact
+                // arithmetic; the 1e-30 floor keeps one that rounds to r = 0
+                // in FP32 finite.
+                const float r2 =
+                    fmaf(dx, dx, fmaf(dy, dy, kSelf ? dz * dz : fmaf(dz, dz, 1e-30f)));
+                float inv = KIFMM_RSQRT(r2);
+                if (kSelf) inv = r2 > 0.f ? inv : 0.f;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) part[i][r] = fmaf(q[r], inv, part[i][r]);
+            }
         }
     }
+}
+
+template <int NR> struct Smem {
+    union {
+        struct {
+            float4 spos[Cfg<NR>::cap];
+            float sq[NR > 1 ? Cfg<NR>::cap * NR : 4];
+        } st;
+        // partial sums of the source slices (used after the last round)
+        float2 red[kWarps][kTMax * NR][16];
+    } u;
+    float4 seg_off[kSegCap];  // centre offset, surface radius
+    int seg_node[kSegCap], seg_kind[kSegCap], seg_start[kSegCap + 1];
+    int warp_sum[kWarps];
+};
+
+template <int NR, int T>
+__device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const DevWork &w, int r0,
+                                     Smem<NR> &sm, int b, int2 rb, int nt) {
+    constexpr int CAP = Cfg<NR>::cap;
+    static_assert(CAP % (64 * kWarps) == 0, "rounds must hold whole runs for every slicing");
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tl = lane & 15, half = lane >> 4;
+    const float4 gb = t.geom[b];
+    const int u0 = t.u_ptr[b], nu = t.u_ptr[b + 1] - u0;
+    const int w0 = t.w_ptr[b], nw = t.w_ptr[b + 1] - w0;
+    const int nl2p = t.level[b] >= 2 ? 1 : 0;
+    const int nseg = nu + nl2p + nw;
+    const int ns = o.ns, nsp = (o.ns + 3) & ~3;
+
+    // warp roles: nsplit source slices x CW target-chunk workers
+    constexpr int CH = 16 * T;
+    const int nchunk = (nt + CH - 1) / CH;
+    const int nsplit = nchunk >= kWarps ? 1 : kWarps / nchunk;
+    const int CW = kWarps / nsplit;
+    const int split = wid / CW, cw = wid - split * CW;
+    const int npass = (nchunk + CW - 1) / CW;
+    const int self_end16 = (nt + 15) & ~15;
+
+    for (int pass = 0; pass < npass; ++pass) {
+        const int chunk = pass * CW + cw;
+        const bool active = chunk < nchunk;
+        float3 x[T];
+        bool valid[T];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) acc[r].add(part[r]);
+        for (int i = 0; i < T; ++i) {
+            const int tt = chunk * CH + tl + 16 * i;
+            valid[i] = active && tt < nt;
+            x[i] = make_float3(-kFar, -kFar, -kFar);
+            if (valid[i]) {
+                const float4 p = t.pts[rb.x + tt];
+                x[i] = make_float3(p.x, p.y, p.z);
+            }
+        }
+        Kahan acc[T][NR];
+
+        for (int sw = 0; sw < nseg; sw += kSegCap) {
+            const int nsegw = min(kSegCap, nseg - sw);
+            // ---- segment table: logical order [B] + U\{B} + [DE(B)] + W
+            int cnt2[2];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int s = 2 * tid + hh;
+                int c = 0;
+                if (s < nsegw) {
+                    const int ls = sw + s;
+                    int node, kind;
+                    if (ls < nu) {
+                        node = ls == 0 ? b : t.u_idx[u0 + ls];
+                        if (ls > 0 && node == b) node = t.u_idx[u0];
+                        kind = 0;
+                    } else if (ls < nu + nl2p) {
+                        node = b;
+                        kind = 1;
+                    } else {
+                        node = t.w_idx[w0 + ls - nu - nl2p];
+                        kind = 2;
+                    }
+                    const float4 ga = t.geom[node];
+                    float rad = 0.f;
+                    if (kind == 0) {
+                        const int2 ra = t.range[node];
+                        c = ra.y - ra.x;
+                        sm.seg_node[s] = ra.x;
+                    } else {
+                        c = ns;
+                        sm.seg_node[s] = node;
+                        rad = kind == 1 ? o.ao * gb.w : o.ai * ga.w;
+                    }
+                    sm.seg_kind[s] = kind;
+                    sm.seg_off[s] = make_float4(ga.x - gb.x, ga.y - gb.y, ga.z - gb.z, rad);
+                }
+                cnt2[hh] = c;
+            }
+            // block exclusive scan of the per-thread pair sums
+            const int mine = cnt2[0] + cnt2[1];
+            int incl = mine;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += v;
+            }
+            if (lane == 31) sm.warp_sum[wid] = incl;
+            __syncthreads();
+            int base_w = 0, total = 0;
+#pragma unroll
+            for (int k = 0; k < kWarps; ++k) {
+                const int v = sm.warp_sum[k];
+                if (k < wid) base_w += v;
+                total += v;
+            }
+            const int excl = base_w + incl - mine;
+            if (2 * tid < nsegw) sm.seg_start[2 * tid] = excl;
+            if (2 * tid + 1 < nsegw) sm.seg_start[2 * tid + 1] = excl + cnt2[0];
+            if (tid == 0) sm.seg_start[nsegw] = total;
+            __syncthreads();
+
+            // ---- rounds of at most CAP staged sources
+            int seg = 0;  // segment of this thread's next source (sources ascend)
+            for (int base = 0; base < total; base += CAP) {
+                const int m = min(CAP, total - base);
+                const int mp = (m + 15) & ~15;
+#pragma unroll 4
+                for (int it = 0; it < CAP / kThreads; ++it) {
+                    const int k = tid + it * kThreads;
+                    if (k >= mp) break;
+                    float4 pos = make_float4(kFar, kFar, kFar, 0.f);
+                    float q[NR];
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) q[r] = 0.f;
+                    if (k < m) {
+                        // f < total = seg_start[nsegw], so the scan stops at
+                        // a segment index below nsegw
+                        const int f = base + k;
+                        while (sm.seg_start[seg + 1] <= f) ++seg;
+                        const int off = f - sm.seg_start[seg];
+                        const float4 so = sm.seg_off[seg];
+                        const int kind = sm.seg_kind[seg];
+                        if (kind == 0) {
+                            const int i = sm.seg_node[seg] + off;
+                            const float4 p = __ldg(t.pts + i);
+                            pos = make_float4(p.x + so.x, p.y + so.y, p.z + so.z, 0.f);
+                            const float *qi = w.qs + (size_t)i * w.nrhs + r0;
+#pragma unroll
+                            for (int r = 0; r < NR; ++r) q[r] = __ldg(qi + r);
+                        } else {
+                            const float4 sp = __ldg(o.surf + off);
+                            pos = make_float4(fmaf(so.w, sp.x, so.x), fmaf(so.w, sp.y, so.y),
+                                              fmaf(so.w, sp.z, so.z), 0.f);
+                            const float *dens = kind == 1 ? w.down : w.up;
+                            const float *d =
+                                dens + ((size_t)sm.seg_node[seg] * w.nrhs + r0) * nsp + off;
+#pragma unroll
+                            for (int r = 0; r < NR; ++r) q[r] = __ldg(d + (size_t)r * nsp);
+                        }
+                    }
+                    if constexpr (NR == 1) {
+                        pos.w = q[0];
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) sm.u.st.sq[k * NR + r] = q[r];
+                    }
+                    sm.u.st.spos[k] = pos;
+                }
+                __syncthreads();
+                if (active) {
+                    // runs of 64 sources (32 per half-warp) go round-robin to
+                    // the slices; CAP is a multiple of 256, so which slice sums
+                    // which run (and so the rounding) depends on the source
+                    // order only
+                    const int self_hi = sw == 0 ? self_end16 - base : 0;
+                    for (int j0 = 64 * split; j0 < mp; j0 += 64 * nsplit) {
+                        const int j1 = min(j0 + 64, mp);
+                        const int js = min(max(self_hi, j0), j1);
+                        float part[T][NR];
+#pragma unroll
+                        for (int i = 0; i < T; ++i)
+#pragma unroll
+                            for (int r = 0; r < NR; ++r) part[i][r] = 0.f;
+                        if (js > j0) run<NR, T, true>(sm.u.st.spos, sm.u.st.sq, j0, js, half, x, part);
+                        run<NR, T, false>(sm.u.st.spos, sm.u.st.sq, js, j1, half, x, part);
+#pragma unroll
+                        for (int i = 0; i < T; ++i)
+#pragma unroll
+                            for (int r = 0; r < NR; ++r) acc[i][r].add(part[i][r]);
+                    }
+                }
+                __syncthreads();
+            }
+        }
+
+        // ---- merge the upper half-warp into the lower, then the slices
+#pragma unroll
+        for (int i = 0; i < T; ++i)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const float s2 = __shfl_down_sync(0xffffffffu, acc[i][r].s, 16);
+                const float c2 = __shfl_down_sync(0xffffffffu, acc[i][r].c, 16);
+                if (half == 0) acc[i][r].merge(s2, c2);
+            }
+        if (nsplit > 1 && split > 0 && active && half == 0) {
+#pragma unroll
+            for (int i = 0; i < T; ++i)
+#pragma unroll
+                for (int r = 0; r < NR; ++r)
+                    sm.u.red[wid][i * NR + r][tl] = make_float2(acc[i][r].s, acc[i][r].c);
+        }
+        __syncthreads();
+        if (split == 0 && active && half == 0) {
+            for (int s = 1; s < nsplit; ++s) {
+#pragma unroll
+                for (int i = 0; i < T; ++i)
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const float2 v = sm.u.red[s * CW + cw][i * NR + r][tl];
+                        acc[i][r].merge(v.x, v.y);
+                    }
+            }
+#pragma unroll
+            for (int i = 0; i < T; ++i) {
+                if (!valid[i]) continue;
+                const int tt = chunk * CH + tl + 16 * i;
+                double *out = w.pot_user + (size_t)t.perm[rb.x + tt] * w.nrhs + r0;
+#pragma unroll
+                for (int r = 0; r < NR; ++r)
+                    out[r] = ((double)acc[i][r].s - (double)acc[i][r].c) * w.scale;
+            }
+        }
+        __syncthreads();
+    }
 }
 
 template <int NR>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock)
-    k_eval(DevTree t, DevOps o, DevWork w, int r0) {
-    __shared__ float4 s_pos[kWarpsPerBlock][32];
-    __shared__ float s_q[kWarpsPerBlock][NR][32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    float4 *spos = s_pos[wid];
-    float(*sq)[32] = s_q[wid];
-    const int gwarp = blockIdx.x * kWarpsPerBlock + wid;
-    const int nwarps = gridDim.x * kWarpsPerBlock;
-    const int ns = o.ns, nsp = (o.ns + 3) & ~3;  // surface rows are padded to nsp
-    for (int li = gwarp; li < t.nleaves; li += nwarps) {
-        const int b = t.leaves[li];
-        const float4 gb = t.geom[b];
-        const int2 rb = t.range[b];
-        const int lvl = t.level[b];
-        for (int t0 = rb.x; t0 < rb.y; t0 += 32) {
-            const int ti = t0 + lane;
-            const bool valid = ti < rb.y;
-            float4 xt = valid ? t.pts[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
-            Kahan acc[NR];
-            // near field: U list (the leaf itself included)
-            for (int e = t.u_ptr[b]; e < t.u_ptr[b + 1]; ++e) {
-                const int a = t.u_idx[e];
-                const float4 ga = t.geom[a];
-                const float sx = ga.x - gb.x, sy = ga.y - gb.y, sz = ga.z - gb.z;
-                const int2 ra = t.range[a];
-                for (int s0 = ra.x; s0 < ra.y; s0 += 32) {
-                    const int si = s0 + lane;
-                    __syncwarp();
-                    if (si < ra.y) {
-                        float4 p = t.pts[si];
-                        const float *q = w.qs + (size_t)si * w.nrhs + r0;
-                        spos[lane] = make_float4(p.x + sx, p.y + sy, p.z + sz,
-                                                 NR == 1 ? __ldg(q) : 0.f);
-                        if (NR > 1) {
-#pragma unroll
-                            for (int r = 0; r < NR; ++r) sq[r][lane] = __ldg(q + r);
-                        }
-                    }
-                    __syncwarp();
-                    batch<NR>(spos, sq, min(32, ra.y - s0), xt.x, xt.y, xt.z, acc);
-                }
-            }
-            // L2P: the leaf's downward density on its downward equivalent surface
-            if (lvl >= 2) {
-                const float rad = o.ao * gb.w;
-                for (int s0 = 0; s0 < ns; s0 += 32) {
-                    const int j = s0 + lane;
-                    __syncwarp();
-                    if (j < ns) {
-                        float4 s = o.surf[j];
-                        const float *d = w.down + ((size_t)b * w.nrhs + r0) * nsp + j;
-                        spos[lane] = make_float4(rad * s.x, rad * s.y, rad * s.z,
-                                                 NR == 1 ? d[0] : 0.f);
-                        if (NR > 1) {
-#pragma unroll
-                            for (int r = 0; r < NR; ++r) sq[r][lane] = d[(size_t)r * nsp];
-                        }
-                    }
-                    __syncwarp();
-                    batch<NR>(spos, sq, min(32, ns - s0), xt.x, xt.y, xt.z, acc);
-                }
-            }
-            // M2P: upward densities of the W list on their upward equivalent surfaces
-            for (int e = t.w_ptr[b]; e < t.w_ptr[b + 1]; ++e) {
-                const int a = t.w_idx[e];
-                const float4 ga = t.geom[a];
-                const float sx = ga.x - gb.x, sy = ga.y - gb.y, sz = ga.z - gb.z;
-                const float rad = o.ai * ga.w;
-                for (int s0 = 0; s0 < ns; s0 += 32) {
-                    const int j = s0 + lane;
-                    __syncwarp();
-                    if (j < ns) {
-                        float4 s = o.surf[j];
-                        const float *d = w.up + ((size_t)a * w.nrhs + r0) * nsp + j;
-                        spos[lane] = make_float4(sx + rad * s.x, sy + rad * s.y,
-                                                 sz + rad * s.z, NR == 1 ? d[0] : 0.f);
-                        if (NR > 1) {
-#pragma unroll
-                            for (int r = 0; r < NR; ++r) sq[r][lane] = d[(size_t)r * nsp];
-                        }
-                    }
-                    __syncwarp();
-                    batch<NR>(spos, sq, min(32, ns - s0), xt.x, xt.y, xt.z, acc);
-                }
-            }
-            if (valid) {
-                double *out = w.pot_user + (size_t)t.perm[ti] * w.nrhs + r0;
-#pragma unroll
-                for (int r = 0; r < NR; ++r) out[r] = acc[r].value() * w.scale;
-            }
-        }
-    }
+__global__ void __launch_bounds__(kThreads, Cfg<NR>::minb) k_eval(DevTree t, DevOps o, DevWork w, int r0) {
+    __shared__ __align__(16) Smem<NR> sm;
+    const int b = t.leaves[blockIdx.x];
+    const int2 rb = t.range[b];
+    const int nt = rb.y - rb.x;
+    if (nt <= 0) return;
+    static_assert(kTMax == 4, "dispatch below covers T = 1..4");
+    const int T = min(kTMax, (nt + 15) >> 4);
+    if (T == 1) leaf<NR, 1>(t, o, w, r0, sm, b, rb, nt);
+    else if (T == 2) leaf<NR, 2>(t, o, w, r0, sm, b, rb, nt);
+    else if (T == 3) leaf<NR, 3>(t, o, w, r0, sm, b, rb, nt);
+    else leaf<NR, 4>(t, o, w, r0, sm, b, rb, nt);
 }
 
 template <int NR>
 cudaError_t launch_eval_nr(const DevTree &t, const DevOps &o, const DevWork &w, int r0,
                            cudaStream_t s) {
-    int blocks = (t.nleaves + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    if (blocks < 1) blocks = 1;
-    k_eval<NR><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(t, o, w, r0);
+    if (t.nleaves <= 0) return cudaSuccess;
+    k_eval<NR><<<t.nleaves, kThreads, 0, s>>>(t, o, w, r0);
     return cudaGetLastError();
 }
 
