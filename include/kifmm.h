@@ -75,8 +75,12 @@ void fmm_options_init(fmm_options *opts);
  *
  * sources  n x 3 row-major FP64 positions, host or device pointer (detected).
  * targets  NULL or equal to sources: the targets are the sources, as in
- *          Eq. (1).  Any other value returns FMM_ERR_UNSUPPORTED.
- * n        number of points, >= 1.
+ *          Eq. (1), and a pair at distance 0 (the point itself, or a
+ *          coincident duplicate) is skipped.  Otherwise n x 3 FP64 target
+ *          positions (host or device): the tree is built on the union of
+ *          the 2n points, targets carry no charge, and the potential at
+ *          each target sums every source at a non-zero distance.
+ * n        number of sources (and of targets), >= 1.
  * p        expansion order, 2 <= p <= 10 (surface points 6(p-1)^2 + 2).
  * ncrit    largest number of points in a leaf before it is split, >= 1.
  * out      receives the plan; untouched on failure.
@@ -91,6 +95,29 @@ fmm_status fmm_plan_create(const double *sources, const double *targets,
 fmm_status fmm_plan_create_ex(const double *sources, const double *targets,
                               int64_t n, int p, int ncrit,
                               const fmm_options *opts, fmm_plan_t *out);
+
+/*
+ * Build one plan for `nproblems` independent problems (batched evaluation).
+ * The paper states one problem, Eq. (1); evaluating many of uneven size in
+ * the same launches is this library's batching form of it.  Problem i has
+ * n[i] >= 1 sources at sources[i] (n[i] x 3 FP64, host or device) and
+ * targets[i] (NULL, or NULL array, or equal to sources[i]: the sources
+ * themselves; else n[i] x 3 FP64 targets, as in fmm_plan_create).  The
+ * problems share nothing but the launches: each has its own root cube,
+ * octree and lists, and no interaction crosses problems.
+ *
+ * fmm_evaluate on such a plan takes charges of sum(n) x nrhs rows, problem
+ * 0's rows first, and writes potentials in the same row order.
+ * 1 <= nproblems <= 65536; sum(n) obeys the limit of fmm_plan_create.
+ */
+fmm_status fmm_plan_create_batch(const double *const *sources, const double *const *targets,
+                                 const int64_t *n, int nproblems, int p, int ncrit,
+                                 fmm_plan_t *out);
+/* As fmm_plan_create_batch, with options (NULL = defaults). */
+fmm_status fmm_plan_create_batch_ex(const double *const *sources,
+                                    const double *const *targets, const int64_t *n,
+                                    int nproblems, int p, int ncrit,
+                                    const fmm_options *opts, fmm_plan_t *out);
 
 /* Evaluation-time options that may change after creation. */
 enum {
@@ -153,7 +180,7 @@ const char *fmm_last_error(void);
 
 /* Integer facts about a plan. */
 enum {
-    FMM_INFO_N = 0,           /* points */
+    FMM_INFO_N = 0,           /* rows of charges / potentials (sum of n) */
     FMM_INFO_NODES = 1,       /* boxes that hold points */
     FMM_INFO_LEAVES = 2,      /* leaves that hold points */
     FMM_INFO_DEPTH = 3,       /* deepest level */
@@ -169,18 +196,24 @@ enum {
     FMM_INFO_P2P_PAIRS = 12,  /* near-field (target, source) pairs */
     FMM_INFO_M2L_TILES = 13,  /* M2L target tiles */
     FMM_INFO_M2L_ENTRIES = 14,/* M2L (tile, offset) entries */
-    FMM_INFO_LAST_LAUNCHES = 15 /* kernels the last evaluation launched */
+    FMM_INFO_LAST_LAUNCHES = 15,/* kernels the last evaluation launched */
+    FMM_INFO_POINTS = 16,     /* points in the tree (2n with distinct
+                                 targets) */
+    FMM_INFO_PROBLEMS = 17    /* independent problems */
 };
 fmm_status fmm_plan_info(fmm_plan_t plan, int key, int64_t *value);
 
 /* Arrays a plan can export.  Sizes are in elements of the stated type. */
 enum {
     FMM_ARRAY_NODE_KEYS = 0, /* int32 [nodes][4]: level, ix, iy, iz, in
-                                plan order (level, then Morton order) */
+                                plan order (level, then problem, then
+                                Morton order) */
     FMM_ARRAY_NODE_RANGE = 1,/* int64 [nodes][2]: first, end point index in
                                 the sorted order */
     FMM_ARRAY_LEAF_FLAG = 2, /* int32 [nodes] */
-    FMM_ARRAY_PERM = 3,      /* int64 [n]: sorted position -> caller index */
+    FMM_ARRAY_PERM = 3,      /* int64 [points]: sorted position -> input
+                                point (sources, then targets if distinct;
+                                problems concatenated) */
     FMM_ARRAY_U_PTR = 4,     /* int64 [nodes+1]: CSR offsets of U lists */
     FMM_ARRAY_U_IDX = 5,     /* int32 [U pairs]: node indices */
     FMM_ARRAY_V_PTR = 6,
@@ -195,7 +228,13 @@ enum {
     FMM_ARRAY_M2L_S = 15,    /* double [316][k][k]: S_t = U_k^T K_t V_k,
                                 offsets t in lexicographic (tx,ty,tz) order
                                 over {-3..3}^3 minus {-1..1}^3 */
-    FMM_ARRAY_ROOT = 16      /* double [4]: root centre x, y, z, half-width */
+    FMM_ARRAY_ROOT = 16,     /* double [problems][4]: root centre x, y, z,
+                                half-width */
+    FMM_ARRAY_CHARGE_ROW = 17,/* int64 [points]: charge row of each sorted
+                                point, -1 for a target only */
+    FMM_ARRAY_OUTPUT_ROW = 18,/* int64 [points]: potential row of each sorted
+                                point, -1 for a source only */
+    FMM_ARRAY_NODE_PROBLEM = 19 /* int32 [nodes]: problem of each box */
 };
 /* Copy array `which` into dst (capacity `bytes`).  *needed receives the
  * size in bytes (may be NULL).  dst == NULL only queries the size. */

@@ -20,17 +20,18 @@ OPT_M2L_MODE = 1
 INFO = {"n": 0, "nodes": 1, "leaves": 2, "depth": 3, "nsurf": 4, "rank_m2l": 5,
         "rank_up": 6, "rank_down": 7, "u_pairs": 8, "v_pairs": 9, "w_pairs": 10,
         "x_pairs": 11, "p2p_pairs": 12, "m2l_tiles": 13, "m2l_entries": 14,
-        "last_launches": 15}
+        "last_launches": 15, "points": 16, "problems": 17}
 ARRAYS = {"node_keys": (0, "i4"), "node_range": (1, "i8"), "leaf_flag": (2, "i4"),
           "perm": (3, "i8"), "u_ptr": (4, "i8"), "u_idx": (5, "i4"),
           "v_ptr": (6, "i8"), "v_idx": (7, "i4"), "w_ptr": (8, "i8"),
           "w_idx": (9, "i4"), "x_ptr": (10, "i8"), "x_idx": (11, "i4"),
           "surface": (12, "f8"), "m2l_u": (13, "f8"), "m2l_v": (14, "f8"),
-          "m2l_s": (15, "f8"), "root": (16, "f8")}
+          "m2l_s": (15, "f8"), "root": (16, "f8"), "charge_row": (17, "i8"),
+          "output_row": (18, "i8"), "node_problem": (19, "i4")}
 
 # every symbol include/kifmm.h declares
 EXPORTS = ("fmm_options_init", "fmm_plan_create", "fmm_plan_create_ex",
-           "fmm_plan_set_option", "fmm_evaluate", "fmm_evaluate_noalloc", "fmm_destroy",
+           "fmm_plan_create_batch", "fmm_plan_create_batch_ex", "fmm_plan_set_option", "fmm_evaluate", "fmm_evaluate_noalloc", "fmm_destroy",
            "fmm_last_error", "fmm_plan_info", "fmm_plan_get_array", "fmm_plan_phase_ms")
 
 
@@ -66,6 +67,12 @@ def lib():
     L.fmm_plan_create.argtypes = [dp, dp, i64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
     L.fmm_plan_create_ex.argtypes = [dp, dp, i64, ctypes.c_int, ctypes.c_int,
                                      ctypes.POINTER(Options), ctypes.POINTER(vp)]
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    L.fmm_plan_create_batch.argtypes = [pp, pp, ctypes.POINTER(i64), ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.POINTER(vp)]
+    L.fmm_plan_create_batch_ex.argtypes = [pp, pp, ctypes.POINTER(i64), ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_int, ctypes.POINTER(Options),
+                                           ctypes.POINTER(vp)]
     L.fmm_plan_set_option.argtypes = [vp, ctypes.c_int, ctypes.c_double]
     L.fmm_evaluate.argtypes = [vp, fp, ctypes.c_int, dp, vp]
     L.fmm_evaluate_noalloc.argtypes = [vp, fp, ctypes.c_int, dp, vp]
@@ -76,7 +83,8 @@ def lib():
     L.fmm_plan_info.argtypes = [vp, ctypes.c_int, ctypes.POINTER(i64)]
     L.fmm_plan_get_array.argtypes = [vp, ctypes.c_int, vp, i64, ctypes.POINTER(i64)]
     L.fmm_plan_phase_ms.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
-    for name in ("fmm_plan_create", "fmm_plan_create_ex", "fmm_plan_set_option",
+    for name in ("fmm_plan_create", "fmm_plan_create_ex", "fmm_plan_create_batch",
+                 "fmm_plan_create_batch_ex", "fmm_plan_set_option",
                  "fmm_evaluate", "fmm_evaluate_noalloc", "fmm_plan_info", "fmm_plan_get_array", "fmm_plan_phase_ms"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L

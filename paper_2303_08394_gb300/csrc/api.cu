@@ -57,6 +57,7 @@ std::vector<float> to_f32(const std::vector<double> &v) {
 struct fmm_plan_s {
     fmm_options opts;
     int p = 0, ncrit = 0, device = 0;
+    int64_t rows = 0;             // caller rows of charges and potentials
     Tree tree;
     M2LTable m2l;
     Schedules sched;
@@ -266,9 +267,24 @@ fmm_status upload_plan(fmm_plan_s *P) {
     float4 *dp;
     if ((s = P->upload(pts, &dp))) return s;
     d.pts = dp;
-    int64_t *dperm;
-    if ((s = P->upload(t.perm, &dperm))) return s;
-    d.perm = dperm;
+    int64_t *dq, *dout;
+    if ((s = P->upload(t.qidx, &dq))) return s;
+    if (t.oidx == t.qidx) {
+        dout = dq;
+    } else if ((s = P->upload(t.oidx, &dout))) {
+        return s;
+    }
+    d.qidx = dq;
+    d.oidx = dout;
+    {
+        // 1 / (4 pi hw) of each box's problem (positions are in root units)
+        std::vector<double> sc(nn);
+        for (int64_t b = 0; b < nn; ++b)
+            sc[b] = 1.0 / (4.0 * M_PI * t.roots[4 * (size_t)t.node_problem[b] + 3]);
+        double *dsc;
+        if ((s = P->upload(sc, &dsc))) return s;
+        d.node_scale = dsc;
+    }
     float4 *dg;
     if ((s = P->upload(geom, &dg))) return s;
     d.geom = dg;
@@ -515,7 +531,6 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
     w.xchk = b.xchk;
     w.pot_user = pot;
     if (!b.chk || !b.ybuf || !b.yp) return fail(FMM_ERR_INVALID_ARG, "workspace is incomplete");
-    w.scale = 1.0 / (4.0 * M_PI * t.hw);
     int64_t launches = 0;
     if (P->timing) CK(cudaEventRecord(P->ev[0], st));
     CK(launch_gather_charges(P->dt, w, st));
@@ -710,37 +725,51 @@ bool kifmm::plan_host_only(const fmm_plan_s *P) { return P->opts.host_only != 0;
 
 namespace {
 
-} // namespace
-
-extern "C" {
-
-void fmm_options_init(fmm_options *o) {
-    if (!o) return;
-    std::memset(o, 0, sizeof(*o));
-    o->alpha_inner = 1.05;
-    o->alpha_outer = 2.95;
-    o->rcond = 1e-7;
-    o->eps_svd = 1e-7;
-    o->max_level = kKeyBits;
-    o->balance = 1;
-    o->m2l_mode = FMM_M2L_FP32;
-    o->host_only = 0;
-    o->device = -1;
+// Host copy of n x 3 positions (device pointers are copied down).
+fmm_status host_points(const double *src, int64_t n, bool may_be_device,
+                       std::vector<double> &buf, const double **out) {
+    *out = src;
+    if (may_be_device && is_device_pointer(src)) {
+        buf.resize((size_t)3 * n);
+        CK(cudaMemcpy(buf.data(), src, buf.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        *out = buf.data();
+    }
+    return FMM_OK;
 }
 
-fmm_status fmm_plan_create(const double *sources, const double *targets, int64_t n, int p,
-                           int ncrit, fmm_plan_t *out) {
-    return fmm_plan_create_ex(sources, targets, n, p, ncrit, nullptr, out);
+// Tree, lists and point roles of one problem from host positions
+// (optional distinct targets: the tree is built on their union).
+void build_problem(const double *xs, const double *xt, int64_t n, const TreeOptions &to,
+                   Tree &t) {
+    if (xt) {
+        std::vector<double> all((size_t)6 * n);
+        std::copy(xs, xs + 3 * n, all.begin());
+        std::copy(xt, xt + 3 * n, all.begin() + 3 * n);
+        build_tree(all.data(), 2 * n, to, t);
+    } else {
+        build_tree(xs, n, to, t);
+    }
+    build_lists(t);
+    set_point_roles(t, n, xt != nullptr);
 }
 
-fmm_status fmm_plan_create_ex(const double *sources, const double *targets, int64_t n, int p,
-                              int ncrit, const fmm_options *opts, fmm_plan_t *out) {
+fmm_status create_plan(const double *const *sources, const double *const *targets,
+                       const int64_t *n, int nproblems, int p, int ncrit,
+                       const fmm_options *opts, fmm_plan_t *out) {
     if (!out) return fail(FMM_ERR_INVALID_ARG, "out is NULL");
-    if (!sources) return fail(FMM_ERR_INVALID_ARG, "sources is NULL");
-    if (targets && targets != sources)
-        return fail(FMM_ERR_UNSUPPORTED, "targets distinct from sources are not supported");
-    if (n < 1) return fail(FMM_ERR_INVALID_ARG, "n must be >= 1");
-    if (n > INT32_MAX / 2) return fail(FMM_ERR_UNSUPPORTED, "n too large for 32-bit ranges");
+    if (!sources || !n) return fail(FMM_ERR_INVALID_ARG, "sources or n is NULL");
+    if (nproblems < 1 || nproblems > 65536)
+        return fail(FMM_ERR_INVALID_ARG, "nproblems must be in [1, 65536]");
+    int64_t rows = 0, points = 0;
+    for (int i = 0; i < nproblems; ++i) {
+        if (!sources[i]) return fail(FMM_ERR_INVALID_ARG, "sources is NULL");
+        if (n[i] < 1) return fail(FMM_ERR_INVALID_ARG, "n must be >= 1");
+        const bool distinct = targets && targets[i] && targets[i] != sources[i];
+        rows += n[i];
+        points += distinct ? 2 * n[i] : n[i];
+        if (points > INT32_MAX / 2)
+            return fail(FMM_ERR_UNSUPPORTED, "too many points for 32-bit ranges");
+    }
     if (p < 2 || p > 10) return fail(FMM_ERR_INVALID_ARG, "p must be in [2, 10]");
     if (ncrit < 1) return fail(FMM_ERR_INVALID_ARG, "ncrit must be >= 1");
     fmm_options o;
@@ -762,10 +791,9 @@ fmm_status fmm_plan_create_ex(const double *sources, const double *targets, int6
         P->opts = o;
         P->p = p;
         P->ncrit = ncrit;
+        P->rows = rows;
         const char *tm = std::getenv("FMM_TIMING");
         P->timing = tm && tm[0] == '1' && !o.host_only;
-        std::vector<double> host;
-        const double *xyz = sources;
         if (!o.host_only) {
             int dev = o.device;
             if (dev < 0) {
@@ -781,23 +809,45 @@ fmm_status fmm_plan_create_ex(const double *sources, const double *targets, int6
                 delete P;
                 return fail(FMM_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
             }
-            if (is_device_pointer(sources)) {
-                host.resize((size_t)3 * n);
-                e = cudaMemcpy(host.data(), sources, host.size() * sizeof(double),
-                               cudaMemcpyDeviceToHost);
-                if (e != cudaSuccess) {
-                    delete P;
-                    return fail(FMM_ERR_CUDA, std::string("copy sources: ") + cudaGetErrorString(e));
-                }
-                xyz = host.data();
-            }
         }
         TreeOptions to;
         to.ncrit = ncrit;
         to.max_level = o.max_level;
         to.balance = o.balance != 0;
-        build_tree(xyz, n, to, P->tree);
-        build_lists(P->tree);
+        // host views of every problem's points (device arrays copied down)
+        std::vector<std::vector<double>> buf(2 * (size_t)nproblems);
+        std::vector<const double *> xs(nproblems), xt(nproblems, nullptr);
+        for (int i = 0; i < nproblems; ++i) {
+            fmm_status e = host_points(sources[i], n[i], !o.host_only, buf[2 * i], &xs[i]);
+            if (e == FMM_OK && targets && targets[i] && targets[i] != sources[i])
+                e = host_points(targets[i], n[i], !o.host_only, buf[2 * i + 1], &xt[i]);
+            if (e != FMM_OK) {
+                delete P;
+                return e;
+            }
+        }
+        if (nproblems == 1) {
+            build_problem(xs[0], xt[0], n[0], to, P->tree);
+        } else {
+            std::vector<Tree> parts(nproblems);
+            std::vector<int64_t> row_off(nproblems, 0);
+            for (int i = 1; i < nproblems; ++i) row_off[i] = row_off[i - 1] + n[i - 1];
+            std::vector<std::string> msg(nproblems);
+            bool bad = false;
+#pragma omp parallel for schedule(dynamic, 1) reduction(|| : bad)
+            for (int i = 0; i < nproblems; ++i) {
+                try {
+                    build_problem(xs[i], xt[i], n[i], to, parts[i]);
+                } catch (const std::exception &ex) {
+                    msg[i] = std::string("problem ") + std::to_string(i) + ": " + ex.what();
+                    bad = true;
+                }
+            }
+            if (bad)
+                for (int i = 0; i < nproblems; ++i)
+                    if (!msg[i].empty()) throw std::runtime_error(msg[i]);
+            merge_forest(parts, row_off, P->tree);
+        }
         build_m2l_table(P->tree, P->m2l);
         build_schedules(P->tree, kDownChunk, P->sched);
         P->ops = get_operators(p, o.alpha_inner, o.alpha_outer, o.rcond, o.eps_svd);
@@ -818,6 +868,47 @@ fmm_status fmm_plan_create_ex(const double *sources, const double *targets, int6
     }
     *out = P;
     return FMM_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+void fmm_options_init(fmm_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->alpha_inner = 1.05;
+    o->alpha_outer = 2.95;
+    o->rcond = 1e-7;
+    o->eps_svd = 1e-7;
+    o->max_level = kKeyBits;
+    o->balance = 1;
+    o->m2l_mode = FMM_M2L_FP32;
+    o->host_only = 0;
+    o->device = -1;
+}
+
+fmm_status fmm_plan_create(const double *sources, const double *targets, int64_t n, int p,
+                           int ncrit, fmm_plan_t *out) {
+    return create_plan(&sources, &targets, &n, 1, p, ncrit, nullptr, out);
+}
+
+fmm_status fmm_plan_create_ex(const double *sources, const double *targets, int64_t n, int p,
+                              int ncrit, const fmm_options *opts, fmm_plan_t *out) {
+    return create_plan(&sources, &targets, &n, 1, p, ncrit, opts, out);
+}
+
+fmm_status fmm_plan_create_batch(const double *const *sources, const double *const *targets,
+                                 const int64_t *n, int nproblems, int p, int ncrit,
+                                 fmm_plan_t *out) {
+    return create_plan(sources, targets, n, nproblems, p, ncrit, nullptr, out);
+}
+
+fmm_status fmm_plan_create_batch_ex(const double *const *sources,
+                                    const double *const *targets, const int64_t *n,
+                                    int nproblems, int p, int ncrit, const fmm_options *opts,
+                                    fmm_plan_t *out) {
+    return create_plan(sources, targets, n, nproblems, p, ncrit, opts, out);
 }
 
 fmm_status fmm_plan_set_option(fmm_plan_t plan, int key, double value) {
@@ -851,16 +942,16 @@ fmm_status fmm_evaluate(fmm_plan_t P, const float *charges, int nrhs, double *po
     if (s != FMM_OK) return s;
     s = ensure_split(P, nrhs);
     if (s != FMM_OK) return s;
-    const size_t nq = (size_t)P->tree.n * nrhs;
+    const size_t nq = (size_t)P->rows * nrhs;
     const float *dq_ptr = charges;
     double *dp_ptr = potentials;
     if (!dq) {
-        if (!P->charges_stage) CK(cudaMalloc((void **)&P->charges_stage, (size_t)P->tree.n * P->nrhs_cap * sizeof(float)));
+        if (!P->charges_stage) CK(cudaMalloc((void **)&P->charges_stage, (size_t)P->rows * P->nrhs_cap * sizeof(float)));
         CK(cudaMemcpyAsync(P->charges_stage, charges, nq * sizeof(float), cudaMemcpyHostToDevice, st));
         dq_ptr = P->charges_stage;
     }
     if (!dp) {
-        if (!P->pot_stage) CK(cudaMalloc((void **)&P->pot_stage, (size_t)P->tree.n * P->nrhs_cap * sizeof(double)));
+        if (!P->pot_stage) CK(cudaMalloc((void **)&P->pot_stage, (size_t)P->rows * P->nrhs_cap * sizeof(double)));
         dp_ptr = P->pot_stage;
     }
     s = enqueue(P, dq_ptr, nrhs, dp_ptr, st);
@@ -882,7 +973,9 @@ fmm_status fmm_plan_info(fmm_plan_t P, int key, int64_t *value) {
     if (!P || !value) return fail(FMM_ERR_INVALID_ARG, "NULL argument");
     const Tree &t = P->tree;
     switch (key) {
-    case FMM_INFO_N: *value = t.n; break;
+    case FMM_INFO_N: *value = P->rows; break;
+    case FMM_INFO_POINTS: *value = t.n; break;
+    case FMM_INFO_PROBLEMS: *value = t.nproblems; break;
     case FMM_INFO_NODES: *value = t.nodes(); break;
     case FMM_INFO_LEAVES: *value = (int64_t)t.leaves.size(); break;
     case FMM_INFO_DEPTH: *value = t.depth; break;
@@ -912,7 +1005,6 @@ fmm_status fmm_plan_get_array(fmm_plan_t P, int which, void *dst, int64_t bytes,
     size_t size = 0;
     std::vector<int64_t> range;
     std::vector<int32_t> leaf32;
-    std::vector<double> root;
     switch (which) {
     case FMM_ARRAY_NODE_KEYS: src = t.key.data(); size = t.key.size() * 4; break;
     case FMM_ARRAY_NODE_RANGE:
@@ -942,10 +1034,12 @@ fmm_status fmm_plan_get_array(fmm_plan_t P, int which, void *dst, int64_t bytes,
     case FMM_ARRAY_M2L_U: src = o.Uk.data(); size = o.Uk.size() * 8; break;
     case FMM_ARRAY_M2L_V: src = o.Vk.data(); size = o.Vk.size() * 8; break;
     case FMM_ARRAY_M2L_S: src = o.S.data(); size = o.S.size() * 8; break;
-    case FMM_ARRAY_ROOT:
-        root = {t.centre[0], t.centre[1], t.centre[2], t.hw};
-        src = root.data();
-        size = 32;
+    case FMM_ARRAY_ROOT: src = t.roots.data(); size = t.roots.size() * 8; break;
+    case FMM_ARRAY_CHARGE_ROW: src = t.qidx.data(); size = t.qidx.size() * 8; break;
+    case FMM_ARRAY_OUTPUT_ROW: src = t.oidx.data(); size = t.oidx.size() * 8; break;
+    case FMM_ARRAY_NODE_PROBLEM:
+        src = t.node_problem.data();
+        size = t.node_problem.size() * 4;
         break;
     default: return fail(FMM_ERR_INVALID_ARG, "unknown array");
     }

@@ -28,7 +28,10 @@ struct DevTree {
     int64_t n;
     int nnodes, depth;
     const float4 *pts;      // n: position relative to the leaf centre (root units)
-    const int64_t *perm;    // n: sorted position -> caller index
+    const int64_t *qidx;    // n: charge row of each sorted point (-1 none)
+    const int64_t *oidx;    // n: potential row of each sorted point (-1 none)
+    const double *node_scale;  // nodes: 1 / (4 pi root half-width) of the
+                               // box's problem (positions are in root units)
     const float4 *geom;     // nodes: centre x, y, z (root units), half-width
     const int2 *range;      // nodes: sorted point range [x, y)
     const int *level;       // nodes
@@ -75,13 +78,12 @@ struct DevM2L {
 // [x slot][rhs][round4(ns)].
 struct DevWork {
     int nrhs;
-    const float *charges_user;  // n x nrhs, caller order
+    const float *charges_user;  // rows x nrhs, caller order
     float *qs;                  // n x nrhs, sorted order
     float *up, *down;           // nodes x nrhs x ns
     float *qhat, *chat;         // nodes x nrhs x kpad
     float *xchk;                // x nodes x nrhs x ns
-    double *pot_user;           // n x nrhs, caller order
-    double scale;               // 1 / (4 pi root half-width)
+    double *pot_user;           // rows x nrhs, caller order
 };
 
 // Batched operator x gathered-vector products (k_vgemm.cu):

@@ -26,7 +26,8 @@
 // compensation) pair; the pairs of the two half-warps and of the source
 // slices are merged with further Kahan additions in a fixed order, and the
 // potential is formed in FP64 (sum - compensation), scaled by 1/(4 pi hw)
-// and written in the caller's point order.  Runs are assigned from the
+// of the leaf's problem and written in the caller's row order (points that
+// are sources only are not written).  Runs are assigned from the
 // source order alone, so every right-hand side gets bit-identical
 // arithmetic whatever NR it is batched in.
 #include "device.cuh"
@@ -333,14 +334,16 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
                         acc[i][r].merge(v.x, v.y);
                     }
             }
+            const double scale = t.node_scale[b];
 #pragma unroll
             for (int i = 0; i < T; ++i) {
                 if (!valid[i]) continue;
-                const int tt = chunk * CH + tl + 16 * i;
-                double *out = w.pot_user + (size_t)t.perm[rb.x + tt] * w.nrhs + r0;
+                const int64_t row = t.oidx[rb.x + chunk * CH + tl + 16 * i];
+                if (row < 0) continue;  // a source only
+                double *out = w.pot_user + (size_t)row * w.nrhs + r0;
 #pragma unroll
                 for (int r = 0; r < NR; ++r)
-                    out[r] = ((double)acc[i][r].s - (double)acc[i][r].c) * w.scale;
+                    out[r] = ((double)acc[i][r].s - (double)acc[i][r].c) * scale;
             }
         }
         __syncthreads();

@@ -4,7 +4,8 @@
 //   P2L        X-list points -> downward check potential (radius ai)
 // both in coordinates normalised by the receiving box's half-width; the
 // matrix products that follow them run in k_vgemm.cu.  Also the gather of
-// the caller's charges into tree order.
+// the caller's charges into tree order (points that are targets only get
+// charge 0).
 #include <algorithm>
 
 #include "device.cuh"
@@ -107,7 +108,8 @@ __global__ void k_gather_charges(DevTree t, DevWork w) {
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = idx / w.nrhs, r = idx - i * w.nrhs;
-        w.qs[idx] = w.charges_user[t.perm[i] * w.nrhs + r];
+        const int64_t c = t.qidx[i];
+        w.qs[idx] = c >= 0 ? w.charges_user[c * w.nrhs + r] : 0.f;
     }
 }
 

@@ -71,6 +71,14 @@ struct Tree {
     std::vector<int32_t> u_idx, v_idx, w_idx, x_idx;
     std::vector<int16_t> v_off;             // offset index of each V entry
     int64_t p2p_pairs = 0;
+    // caller rows of each sorted point: charge row (-1: a target only) and
+    // output row (-1: a source only)
+    std::vector<int64_t> qidx, oidx;
+    // independent problems sharing the tree arrays (a forest): root cube of
+    // each (centre x, y, z, half-width) and the problem of every node
+    int nproblems = 1;
+    std::vector<double> roots;
+    std::vector<int32_t> node_problem;
 
     int64_t nodes() const { return (int64_t)parent.size(); }
     double node_centre(int64_t node, int d) const;   // root units
@@ -88,6 +96,18 @@ void build_tree(const double *xyz, int64_t n, const TreeOptions &opt,
                 Tree &tree);
 // Fill U, V, W, X lists.
 void build_lists(Tree &tree);
+// Point roles and the single root of a one-problem tree.  With
+// distinct = false every point is a source and a target (qidx = oidx =
+// perm); otherwise the first nsrc input points are the sources and the next
+// nsrc the targets.
+void set_point_roles(Tree &tree, int64_t nsrc, bool distinct);
+// Merge trees of independent problems (lists built, roles set) into one
+// forest.  Nodes are ordered by level, then problem, then the problem's own
+// order, so every per-level range still covers one contiguous block; point
+// ranges, lists and schedules are renumbered and the caller rows of problem
+// i are shifted by row_offset[i].
+void merge_forest(const std::vector<Tree> &parts, const std::vector<int64_t> &row_offset,
+                  Tree &out);
 
 // M2L work decomposition: per level, targets grouped by parity class and
 // chunked into tiles of kTileRows; each tile lists the offsets any of its

@@ -20,6 +20,7 @@
 //    adjacent same-level boxes that are not adjacent to B but whose parent
 //    is; X(B) = {A : B in W(A)}.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <deque>
@@ -374,6 +375,129 @@ void build_lists(Tree &t) {
             int32_t a = t.u_idx[e];
             t.p2p_pairs += (t.end[b] - t.begin[b]) * (t.end[a] - t.begin[a]);
         }
+}
+
+void set_point_roles(Tree &t, int64_t nsrc, bool distinct) {
+    t.qidx.resize(t.n);
+    t.oidx.resize(t.n);
+    for (int64_t s = 0; s < t.n; ++s) {
+        const int64_t c = t.perm[s];
+        if (!distinct) {
+            t.qidx[s] = t.oidx[s] = c;
+        } else {
+            t.qidx[s] = c < nsrc ? c : -1;
+            t.oidx[s] = c >= nsrc ? c - nsrc : -1;
+        }
+    }
+    t.nproblems = 1;
+    t.roots = {t.centre[0], t.centre[1], t.centre[2], t.hw};
+    t.node_problem.assign(t.nodes(), 0);
+}
+
+void merge_forest(const std::vector<Tree> &parts, const std::vector<int64_t> &row_offset,
+                  Tree &m) {
+    const int np = (int)parts.size();
+    if (np < 1 || (int)row_offset.size() != np)
+        throw std::runtime_error("merge_forest: bad arguments");
+    m = Tree();
+    m.nproblems = np;
+    int depth = 0;
+    std::vector<int64_t> pt_base(np + 1, 0);
+    for (int i = 0; i < np; ++i) {
+        depth = std::max(depth, parts[i].depth);
+        pt_base[i + 1] = pt_base[i] + parts[i].n;
+    }
+    m.depth = depth;
+    m.n = pt_base[np];
+    // new node ids: level-major, then problem, then the problem's order
+    std::vector<std::vector<int32_t>> newid(np);
+    int64_t nn = 0;
+    m.level_ptr.assign(depth + 2, 0);
+    for (int l = 0; l <= depth; ++l) {
+        m.level_ptr[l] = (int32_t)nn;
+        for (int i = 0; i < np; ++i) {
+            const Tree &t = parts[i];
+            if ((int)newid[i].size() != t.nodes()) newid[i].assign(t.nodes(), -1);
+            if (l > t.depth) continue;
+            for (int32_t b = t.level_ptr[l]; b < t.level_ptr[l + 1]; ++b) newid[i][b] = (int32_t)nn++;
+        }
+    }
+    m.level_ptr[depth + 1] = (int32_t)nn;
+    if (nn > INT32_MAX / 8) throw std::runtime_error("merge_forest: too many nodes");
+    m.key.assign((size_t)4 * nn, 0);
+    m.begin.assign(nn, 0);
+    m.end.assign(nn, 0);
+    m.parent.assign(nn, -1);
+    m.child.assign((size_t)8 * nn, -1);
+    m.leaf.assign(nn, 0);
+    m.node_problem.assign(nn, 0);
+    m.perm.resize(m.n);
+    m.rel.resize((size_t)4 * m.n);
+    m.qidx.resize(m.n);
+    m.oidx.resize(m.n);
+    for (int i = 0; i < np; ++i) {
+        const Tree &t = parts[i];
+        const int64_t pb = pt_base[i], ro = row_offset[i];
+        m.roots.insert(m.roots.end(), {t.centre[0], t.centre[1], t.centre[2], t.hw});
+        for (int64_t s = 0; s < t.n; ++s) {
+            m.perm[pb + s] = pb + t.perm[s];
+            m.qidx[pb + s] = t.qidx[s] >= 0 ? ro + t.qidx[s] : -1;
+            m.oidx[pb + s] = t.oidx[s] >= 0 ? ro + t.oidx[s] : -1;
+        }
+        std::copy(t.rel.begin(), t.rel.end(), m.rel.begin() + 4 * pb);
+        const auto &id = newid[i];
+        for (int64_t b = 0; b < t.nodes(); ++b) {
+            const int32_t q = id[b];
+            for (int d = 0; d < 4; ++d) m.key[4 * (size_t)q + d] = t.key[4 * b + d];
+            m.begin[q] = pb + t.begin[b];
+            m.end[q] = pb + t.end[b];
+            m.parent[q] = t.parent[b] >= 0 ? id[t.parent[b]] : -1;
+            for (int c = 0; c < 8; ++c) {
+                const int32_t ch = t.child[8 * b + c];
+                m.child[8 * (size_t)q + c] = ch >= 0 ? id[ch] : -1;
+            }
+            m.leaf[q] = t.leaf[b];
+            m.node_problem[q] = i;
+        }
+        m.p2p_pairs += t.p2p_pairs;
+    }
+    for (int64_t q = 0; q < nn; ++q)
+        if (m.leaf[q]) m.leaves.push_back((int32_t)q);
+    // lists: each node keeps its own problem's list, renumbered (the map is
+    // increasing within a problem, so sorted lists stay sorted)
+    std::vector<int32_t> owner_problem(nn), owner_local(nn);
+    for (int i = 0; i < np; ++i)
+        for (int64_t b = 0; b < parts[i].nodes(); ++b) {
+            owner_problem[newid[i][b]] = i;
+            owner_local[newid[i][b]] = (int32_t)b;
+        }
+    auto merge_list = [&](std::vector<int64_t> Tree::*ptr, std::vector<int32_t> Tree::*idx,
+                          std::vector<int16_t> *off) {
+        std::vector<int64_t> &mp = m.*ptr;
+        std::vector<int32_t> &mi = m.*idx;
+        mp.assign(nn + 1, 0);
+        for (int64_t q = 0; q < nn; ++q) {
+            const Tree &t = parts[owner_problem[q]];
+            const int32_t b = owner_local[q];
+            mp[q + 1] = mp[q] + ((t.*ptr)[b + 1] - (t.*ptr)[b]);
+        }
+        mi.resize(mp[nn]);
+        if (off) off->resize(mp[nn]);
+        for (int64_t q = 0; q < nn; ++q) {
+            const int i = owner_problem[q];
+            const Tree &t = parts[i];
+            const int32_t b = owner_local[q];
+            int64_t o = mp[q];
+            for (int64_t e = (t.*ptr)[b]; e < (t.*ptr)[b + 1]; ++e, ++o) {
+                mi[o] = newid[i][(t.*idx)[e]];
+                if (off) (*off)[o] = t.v_off[e];
+            }
+        }
+    };
+    merge_list(&Tree::u_ptr, &Tree::u_idx, nullptr);
+    merge_list(&Tree::v_ptr, &Tree::v_idx, &m.v_off);
+    merge_list(&Tree::w_ptr, &Tree::w_idx, nullptr);
+    merge_list(&Tree::x_ptr, &Tree::x_idx, nullptr);
 }
 
 void build_m2l_table(const Tree &t, M2LTable &m) {

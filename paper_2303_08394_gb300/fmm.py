@@ -19,39 +19,102 @@ def _ptr(a):
     return a.data_ptr()
 
 
-class FMMPlan:
-    """A KIFMM plan over n points (sources are also the targets, Eq. (1)).
+def _points(a, what="points"):
+    """(n, 3) float64 numpy array or torch tensor, contiguous."""
+    if isinstance(a, np.ndarray):
+        pts = np.ascontiguousarray(a, dtype=np.float64)
+        if pts.ndim != 2 or pts.shape[1] != 3:
+            raise ValueError(f"{what} must be (n, 3)")
+        return pts
+    pts = a.contiguous()
+    if str(pts.dtype) != "torch.float64" or pts.dim() != 2 or pts.shape[1] != 3:
+        raise ValueError(f"{what} must be a (n, 3) float64 tensor")
+    return pts
 
-    points: (n, 3) float64, numpy (host) or torch tensor (host or CUDA).
+
+def _options(options):
+    L = N.lib()
+    opts = N.Options()
+    L.fmm_options_init(ctypes.byref(opts))
+    for k, v in options.items():
+        if not hasattr(opts, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(opts, k, v)
+    return opts
+
+
+class FMMPlan:
+    """A KIFMM plan over n points.
+
+    points: (n, 3) float64, numpy (host) or torch tensor (host or CUDA); the
+    sources, which are also the targets (Eq. (1)) unless ``targets`` gives n
+    distinct target points (the tree is then built on the union).
     p: expansion order; ncrit: largest leaf before a split.
     Options (see include/kifmm.h): alpha_inner, alpha_outer, rcond, eps_svd,
     max_level, balance, m2l_mode, host_only, device.
     """
 
-    def __init__(self, points, p: int, ncrit: int, **options):
+    def __init__(self, points, p: int, ncrit: int, targets=None, **options):
         L = N.lib()
-        opts = N.Options()
-        L.fmm_options_init(ctypes.byref(opts))
-        for k, v in options.items():
-            if not hasattr(opts, k):
-                raise TypeError(f"unknown option {k}")
-            setattr(opts, k, v)
-        if isinstance(points, np.ndarray):
-            pts = np.ascontiguousarray(points, dtype=np.float64)
-            if pts.ndim != 2 or pts.shape[1] != 3:
-                raise ValueError("points must be (n, 3)")
-        else:
-            pts = points.contiguous()
-            if str(pts.dtype) != "torch.float64" or pts.dim() != 2 or pts.shape[1] != 3:
-                raise ValueError("points must be a (n, 3) float64 tensor")
-        self._keep = pts
+        opts = _options(options)
+        pts = _points(points)
+        tgt = None if targets is None else _points(targets, "targets")
+        if tgt is not None and tgt.shape[0] != pts.shape[0]:
+            raise ValueError("targets must have as many rows as points")
+        self._keep = (pts, tgt)
         self.n = int(pts.shape[0])
         self.p, self.ncrit = p, ncrit
         self.host_only = bool(options.get("host_only", 0))
+        self.sizes = [self.n]
         h = ctypes.c_void_p()
-        N.check(L.fmm_plan_create_ex(_ptr(pts), None, self.n, p, ncrit, ctypes.byref(opts),
-                                     ctypes.byref(h)))
+        N.check(L.fmm_plan_create_ex(_ptr(pts), None if tgt is None else _ptr(tgt), self.n, p,
+                                     ncrit, ctypes.byref(opts), ctypes.byref(h)))
         self._h = h
+
+    @classmethod
+    def batch(cls, point_sets, p: int, ncrit: int, target_sets=None, **options):
+        """One plan for independent problems (fmm_plan_create_batch).
+
+        point_sets: list of (n_i, 3) float64 arrays or tensors; target_sets:
+        None or a list with None (targets = sources) or (n_i, 3) per problem.
+        Evaluations take charges of sum(n_i) rows, problem 0 first; use
+        ``split`` to cut the result per problem.
+        """
+        L = N.lib()
+        opts = _options(options)
+        pts = [_points(x) for x in point_sets]
+        if not pts:
+            raise ValueError("no problems")
+        tgts = [None] * len(pts) if target_sets is None else \
+            [None if t is None else _points(t, "targets") for t in target_sets]
+        if len(tgts) != len(pts):
+            raise ValueError("one target set per problem")
+        sizes = [int(x.shape[0]) for x in pts]
+        for t, n in zip(tgts, sizes):
+            if t is not None and int(t.shape[0]) != n:
+                raise ValueError("targets must have as many rows as the problem's points")
+        self = cls.__new__(cls)
+        self._keep = (pts, tgts)
+        self.sizes = sizes
+        self.n = sum(sizes)
+        self.p, self.ncrit = p, ncrit
+        self.host_only = bool(options.get("host_only", 0))
+        src_arr = (ctypes.c_void_p * len(pts))(*[_ptr(x) for x in pts])
+        tgt_arr = (ctypes.c_void_p * len(pts))(*[None if t is None else _ptr(t) for t in tgts])
+        n_arr = (ctypes.c_int64 * len(pts))(*sizes)
+        h = ctypes.c_void_p()
+        N.check(L.fmm_plan_create_batch_ex(src_arr, tgt_arr, n_arr, len(pts), p, ncrit,
+                                           ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+        return self
+
+    def split(self, result):
+        """Cut an evaluation result (rows of all problems) per problem."""
+        out, r = [], 0
+        for n in self.sizes:
+            out.append(result[r:r + n])
+            r += n
+        return out
 
     # ---------------------------------------------------------------
     def close(self):

@@ -55,6 +55,14 @@ def log_uniform_sizes(count: int, seed: int, lo: float = 1e3, hi: float = 1e5):
     return np.rint(10.0 ** e).astype(np.int64)
 
 
+def batch_problems(count: int, seed: int, nrhs: int = 1, lo: float = 1e3, hi: float = 1e5):
+    """`count` independent problems, N_i log-uniform in [lo, hi], each N_i
+    points uniform in [0,1]^3 with charges uniform in [-1,1]; list of
+    (x_i, q_i)."""
+    sizes = log_uniform_sizes(count, seed, lo, hi)
+    return [uniform_cube(int(n), 1_000_000 * (seed + 1) + i, nrhs) for i, n in enumerate(sizes)]
+
+
 def sample_targets(n: int, m: int, seed: int):
     """m distinct target indices out of n (sorted), for sampled error checks."""
     rng = np.random.default_rng(seed + 1_000_003)

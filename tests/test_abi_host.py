@@ -137,16 +137,105 @@ def test_invalid_arguments():
     with pytest.raises(N.FMMError):
         FMMPlan(bad, 4, 8, host_only=1)
     L = N.lib()
-    h = ctypes.c_void_p()
-    pts = np.ascontiguousarray(x)
-    other = pts.copy()
-    st = L.fmm_plan_create(pts.ctypes.data, other.ctypes.data, 10, 4, 8, ctypes.byref(h))
-    assert st == N.FMM_ERR_UNSUPPORTED
-    assert b"targets" in L.fmm_last_error()
     P = FMMPlan(x, 4, 8, host_only=1)
     with pytest.raises(N.FMMError):
         P.evaluate(np.ones(10, dtype=np.float32))
     L.fmm_destroy(None)
+    # batch: no problems, an empty problem, a NULL source array
+    h = ctypes.c_void_p()
+    opts = N.Options()
+    L.fmm_options_init(ctypes.byref(opts))
+    opts.host_only = 1
+    pts = np.ascontiguousarray(x)
+    src = (ctypes.c_void_p * 2)(pts.ctypes.data, pts.ctypes.data)
+    assert L.fmm_plan_create_batch_ex(src, None, (ctypes.c_int64 * 2)(10, 10), 0, 4, 8,
+                                      ctypes.byref(opts), ctypes.byref(h)) == N.FMM_ERR_INVALID_ARG
+    assert L.fmm_plan_create_batch_ex(src, None, (ctypes.c_int64 * 2)(10, 0), 2, 4, 8,
+                                      ctypes.byref(opts), ctypes.byref(h)) == N.FMM_ERR_INVALID_ARG
+    bad_src = (ctypes.c_void_p * 2)(pts.ctypes.data, None)
+    assert L.fmm_plan_create_batch_ex(bad_src, None, (ctypes.c_int64 * 2)(10, 10), 2, 4, 8,
+                                      ctypes.byref(opts), ctypes.byref(h)) == N.FMM_ERR_INVALID_ARG
+    assert not h.value
+
+
+def test_distinct_targets_build_the_tree_on_the_union():
+    """Targets distinct from the sources: the octree and lists are the
+    oracle's on the 2n points, sources keep their charge rows and targets
+    get the potential rows."""
+    x, _ = wl.uniform_cube(1500, 5)
+    y, _ = wl.gaussian_mixture(1500, 6)
+    n = len(x)
+    P = FMMPlan(x, 4, 16, targets=y, host_only=1)
+    assert P.info("n") == n and P.info("points") == 2 * n and P.info("problems") == 1
+    u = np.vstack([x, y])
+    tree = ok.Octree(u, 16)
+    U, V, W, X = ok.build_lists(tree)
+    keys = _plan_keys(P)
+    assert set(keys) == tree.nonempty
+    for name, ref in (("u", U), ("v", V), ("w", W), ("x", X)):
+        assert _csr(P, name, keys) == {k: sorted(v) for k, v in ref.items()}, name
+    perm = P.array("perm")
+    qrow, orow = P.array("charge_row"), P.array("output_row")
+    src = perm < n
+    np.testing.assert_array_equal(qrow[src], perm[src])
+    np.testing.assert_array_equal(orow[src], -1)
+    np.testing.assert_array_equal(qrow[~src], -1)
+    np.testing.assert_array_equal(orow[~src], perm[~src] - n)
+    # targets given as the sources themselves: one point set
+    Q = FMMPlan(x, 4, 16, targets=x, host_only=1)
+    assert Q.info("points") == n
+    np.testing.assert_array_equal(Q.array("charge_row"), Q.array("perm"))
+    np.testing.assert_array_equal(Q.array("output_row"), Q.array("perm"))
+
+
+def _batch_sets():
+    sizes = [700, 37, 2500, 1, 1200]
+    gens = [wl.uniform_cube, wl.sphere_surface, wl.gaussian_mixture, wl.uniform_cube,
+            wl.sphere_surface]
+    return [g(n, 40 + i)[0] for i, (g, n) in enumerate(zip(gens, sizes))]
+
+
+def test_batch_plan_is_the_forest_of_single_plans():
+    """A batch plan holds every problem's own tree and lists, renumbered: the
+    boxes of problem i, in plan order, are the boxes of the single plan of
+    problem i, and every list maps across."""
+    sets = _batch_sets()
+    targets = [None, None, wl.uniform_cube(2500, 9)[0], None, None]
+    B = FMMPlan.batch(sets, 4, 20, target_sets=targets, host_only=1)
+    sizes = [len(x) for x in sets]
+    assert B.info("problems") == len(sets) and B.info("n") == sum(sizes)
+    assert B.info("points") == sum(sizes) + 2500
+    keys = B.array("node_keys").reshape(-1, 4)
+    assert np.all(np.diff(keys[:, 0]) >= 0)  # level-major
+    owner = B.array("node_problem")
+    rng = B.array("node_range").reshape(-1, 2)
+    perm, qrow, orow = B.array("perm"), B.array("charge_row"), B.array("output_row")
+    roots = B.array("root").reshape(-1, 4)
+    lists = {nm: (B.array(nm + "_ptr"), B.array(nm + "_idx")) for nm in "uvwx"}
+    pt_base = row_base = 0
+    pairs = {"p2p_pairs": 0, "v_pairs": 0, "u_pairs": 0}
+    for i, x in enumerate(sets):
+        S = FMMPlan(x, 4, 20, targets=targets[i], host_only=1)
+        ids = np.nonzero(owner == i)[0]
+        np.testing.assert_array_equal(keys[ids], S.array("node_keys").reshape(-1, 4))
+        np.testing.assert_array_equal(rng[ids], S.array("node_range").reshape(-1, 2) + pt_base)
+        npts = S.info("points")
+        sl = slice(pt_base, pt_base + npts)
+        np.testing.assert_array_equal(perm[sl], S.array("perm") + pt_base)
+        for got, ref in ((qrow[sl], S.array("charge_row")), (orow[sl], S.array("output_row"))):
+            np.testing.assert_array_equal(got, np.where(ref >= 0, ref + row_base, -1))
+        np.testing.assert_array_equal(roots[i], S.array("root"))
+        for nm, (bptr, bidx) in lists.items():
+            sptr, sidx = S.array(nm + "_ptr"), S.array(nm + "_idx")
+            for b, gb in enumerate(ids):
+                np.testing.assert_array_equal(bidx[bptr[gb]:bptr[gb + 1]],
+                                              ids[sidx[sptr[b]:sptr[b + 1]]])
+        for k in pairs:
+            pairs[k] += S.info(k)
+        pt_base += npts
+        row_base += len(x)
+    for k, v in pairs.items():
+        assert B.info(k) == v, k
 
 
 def test_single_point_and_duplicates():

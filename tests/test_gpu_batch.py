@@ -1,0 +1,132 @@
+"""GPU parity of batched plans and of targets distinct from the sources.
+
+* A batch plan (fmm_plan_create_batch) over problems of uneven size gives,
+  for every problem, what the oracle KIFMM gives for that problem alone
+  (relative L2 <= 1e-6 on the FP32 path, <= 1e-5 with BF16x3 M2L), and
+  agrees with the single-problem plan to FP32 rounding (the M2L tiles mix
+  problems, so the order of some FP32 sums differs).
+* Distinct targets: the tree is built on the union of sources and targets
+  and targets carry no charge, so the oracle is the oracle KIFMM on the
+  union with zero charges at the targets; the direct sum from the sources
+  to the targets bounds the error as in the single-set case.
+* The batched workload at full size (256 problems, N_i log-uniform in
+  [1e3, 1e5], p = 6, ncrit = 150): sampled targets of every problem against
+  the FP64 direct sum, in one evaluation of one plan.
+"""
+import numpy as np
+import pytest
+
+from oracle.direct import direct_sum
+from oracle.kifmm import KIFMM
+from paper_2303_08394_gb300 import FMMPlan, _native as N
+from paper_2303_08394_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP32_FLOOR = 3e-7
+BARS = {N.M2L_FP32: 1e-6, N.M2L_BF16X3: 1e-5, N.M2L_TF32X3: 1e-6}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2303_08394_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def gpu_eval(plan, q):
+    q = np.asarray(q, dtype=np.float32)
+    qd = torch.as_tensor(q.reshape(len(q), -1), device="cuda")
+    out = plan.evaluate(qd)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def _problems():
+    sizes = [900, 64, 3000, 1, 1700, 2]
+    gens = [wl.uniform_cube, wl.sphere_surface, wl.gaussian_mixture, wl.uniform_cube,
+            wl.sphere_surface, wl.gaussian_mixture]
+    return [g(n, 70 + i, nrhs=2) for i, (g, n) in enumerate(zip(gens, sizes))]
+
+
+@pytest.mark.parametrize("mode", [N.M2L_FP32, N.M2L_BF16X3], ids=["fp32", "bf16x3"])
+def test_batch_matches_each_problem(mode):
+    probs = _problems()
+    p, ncrit = 5, 24
+    B = FMMPlan.batch([x for x, _ in probs], p, ncrit, m2l_mode=mode)
+    q = np.vstack([q for _, q in probs])
+    phi = B.split(gpu_eval(B, q))
+    for i, (x, qi) in enumerate(probs):
+        ora = KIFMM(x, p, ncrit)
+        single = FMMPlan(x, p, ncrit, m2l_mode=mode)
+        phi_s = gpu_eval(single, qi)
+        for r in range(qi.shape[1]):
+            phi_o = ora.evaluate(qi[:, r])
+            if len(x) == 1:  # one point: no pair, potential 0
+                assert phi[i][0, r] == 0.0 and phi_s[0, r] == 0.0
+                continue
+            assert rel(phi[i][:, r], phi_o) <= BARS[mode], (i, r)
+            assert rel(phi[i][:, r], phi_s[:, r]) <= BARS[mode], (i, r)
+
+
+def test_batch_upward_and_leaf_work_is_per_problem_exact():
+    """Problems whose trees have no V list (too shallow for M2L) go through
+    the same level products and leaf kernel as alone: bit-identical."""
+    probs = [wl.uniform_cube(n, 90 + n, nrhs=1) for n in (30, 200, 5, 120)]
+    B = FMMPlan.batch([x for x, _ in probs], 4, 64)
+    assert B.info("v_pairs") == 0
+    phi = B.split(gpu_eval(B, np.vstack([q for _, q in probs])))
+    for (x, q), got in zip(probs, phi):
+        np.testing.assert_array_equal(got, gpu_eval(FMMPlan(x, 4, 64), q))
+
+
+@pytest.mark.parametrize("mode", [N.M2L_FP32, N.M2L_TF32X3], ids=["fp32", "tf32x3"])
+def test_distinct_targets(mode):
+    x, q = wl.uniform_cube(6000, 12)
+    y, _ = wl.gaussian_mixture(6000, 13)
+    q = q[:, 0]
+    y = y.copy()
+    y[:5] = x[:5]  # a few targets on top of sources: those pairs are skipped
+    p, ncrit = 6, 40
+    plan = FMMPlan(x, p, ncrit, targets=y, m2l_mode=mode)
+    phi = gpu_eval(plan, q)[:, 0]
+    ora = KIFMM(np.vstack([x, y]), p, ncrit)
+    phi_o = ora.evaluate(np.concatenate([q, np.zeros(len(y))]))[len(x):]
+    ref = direct_sum(x, q, y)
+    e_gpu_ora, e_gpu, e_ora = rel(phi, phi_o), rel(phi, ref), rel(phi_o, ref)
+    assert e_gpu_ora <= BARS[mode], (e_gpu_ora, e_gpu, e_ora)
+    assert e_gpu <= 1.5 * e_ora + FP32_FLOOR, (e_gpu, e_ora)
+
+
+def test_batch_with_distinct_targets_and_host_buffers():
+    (x0, q0), (x1, q1) = wl.uniform_cube(2500, 21), wl.sphere_surface(1800, 22)
+    y1, _ = wl.uniform_cube(1800, 23)
+    B = FMMPlan.batch([x0, x1], 5, 32, target_sets=[None, y1])
+    q = np.concatenate([q0[:, 0], q1[:, 0]]).astype(np.float32)
+    phi = B.split(B.evaluate(q))  # numpy in, numpy out (staged by the library)
+    assert rel(phi[0], KIFMM(x0, 5, 32).evaluate(q0[:, 0])) <= 1e-6
+    u = np.vstack([x1, y1])
+    ref1 = KIFMM(u, 5, 32).evaluate(np.concatenate([q1[:, 0], np.zeros(len(y1))]))[len(x1):]
+    assert rel(phi[1], ref1) <= 1e-6
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mode", [N.M2L_FP32, N.M2L_BF16X3], ids=["fp32", "bf16x3"])
+def test_256_problem_batch_sampled_against_direct_sum(mode):
+    probs = wl.batch_problems(256, 0)
+    B = FMMPlan.batch([x for x, _ in probs], 6, 150, m2l_mode=mode)
+    assert B.info("problems") == 256
+    q = np.vstack([q for _, q in probs])
+    phi = B.split(gpu_eval(B, q))
+    got, ref = [], []
+    for i, (x, qi) in enumerate(probs):
+        idx = wl.sample_targets(len(x), 8, i)
+        ref.append(direct_sum(x, qi[:, 0], x[idx]))
+        got.append(phi[i][idx, 0])
+    err = rel(np.concatenate(got), np.concatenate(ref))
+    assert err <= 1e-5, err
