@@ -2,10 +2,13 @@
 """Benchmark: Laplace KIFMM points/s on one GB300 (or N independent ones).
 
 Workload (default): 10^6 points uniform in the unit cube, charges uniform in
-[-1, 1], p = 6, ncrit = 150, adaptive octree, FP32 path.  One step is one
-full ``fmm_evaluate`` (every operator, the M2L and P2P hot path included)
-with inputs resident in device memory; L2 is flushed (256 MB write) before
-every timed step, outside the timed events.
+[-1, 1], p = 6, ncrit = 150, adaptive octree.  One step is one full
+``fmm_evaluate`` (every operator, the M2L and P2P hot path included) with
+inputs resident in device memory, replayed as a CUDA graph on a side
+stream; L2 is flushed (256 MB write) before every timed step, outside the
+timed events.  The headline runs the M2L in BF16x3 split precision on the
+tensor cores (mixed); the plain FP32 path is timed on the same plan with
+the same protocol and reported beside it.
 
 Printed: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on a bounded sample of the same workload instead.
@@ -24,7 +27,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "Laplace FMM points/s at rel L2 err <=1e-5 (M2L mode {mode}); M2L % of peak"
+METRIC = "Laplace FMM points/s at rel L2 err \u22641e-5, mixed vs FP32; M2L % tensor peak"
 UNIT = "points/s"
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
@@ -34,11 +37,11 @@ CPU_SAMPLE_N = 40_000
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="cube_n1e6_p6_ncrit150")
-    ap.add_argument("--m2l", default="fp32", choices=["fp32", "bf16x3", "tf32x3"])
+    ap.add_argument("--m2l", default="bf16x3", choices=["fp32", "bf16x3", "tf32x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error-check", action="store_true")
     ap.add_argument("--quick", action="store_true",
@@ -170,13 +173,44 @@ def direct_sum_sampled(x, q, idx, block=4):
 
 
 # ---------------------------------------------------------------------------
+def time_mode(plan, qd, out, flush, stream, steps, warmup, world):
+    """Warm up, then time `steps` evaluations (CUDA events on `stream`, L2
+    flushed before each step outside the events); returns per-step ms, the
+    per-phase ms of every step and the launches of one evaluation."""
+    import torch
+    import torch.distributed as dist
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            plan.evaluate(qd, out=out, stream=stream)
+    torch.cuda.synchronize()
+    launches = plan.info("last_launches")
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    phases = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            flush.fill_(float(i))
+            starts[i].record(stream)
+            plan.evaluate(qd, out=out, stream=stream)
+            ends[i].record(stream)
+            phases.append(plan.phase_ms())
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)], phases, launches
+
+
 def main():
     a = parse()
     rank, world, local = dist_env()
     from paper_2303_08394_gb300 import workloads as wl
     w = wl.WORKLOADS[a.workload]
     config = {"workload": w.name, "n": w.n, "p": w.p, "ncrit": w.ncrit, "nrhs": w.nrhs,
-              "points": w.kind, "m2l": a.m2l, "l2_flush": "256 MB write before every step",
+              "points": w.kind, "m2l": a.m2l, "graph": "CUDA graph replay on a side stream",
+              "l2_flush": "256 MB write before every step",
               "per_rank": "independent problem (seed = rank)"}
 
     if a.impl == "reference":
@@ -187,7 +221,7 @@ def main():
         times = res["times"][a.warmup:]
         total = sum(times)
         value = res["n"] * res["nrhs"] * len(times) / total
-        line = {"impl": "reference", "metric": METRIC.format(mode=a.m2l), "value": value,
+        line = {"impl": "reference", "metric": METRIC, "value": value,
                 "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
                 "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -212,42 +246,23 @@ def main():
     from paper_2303_08394_gb300 import FMMPlan, build, _native as N
     if not os.path.exists(N.LIB_PATH):
         build.build()
-    mode = {"fp32": N.M2L_FP32, "bf16x3": N.M2L_BF16X3, "tf32x3": N.M2L_TF32X3}[a.m2l]
+    modes = {"fp32": N.M2L_FP32, "bf16x3": N.M2L_BF16X3, "tf32x3": N.M2L_TF32X3}
     x, q = w.generate(rank)
     t0 = time.perf_counter()
-    plan = FMMPlan(x, w.p, w.ncrit, m2l_mode=mode)
+    plan = FMMPlan(x, w.p, w.ncrit, m2l_mode=modes[a.m2l])
     plan_s = time.perf_counter() - t0
     qd = torch.as_tensor(q.astype(np.float32), device=dev)
     out = torch.empty((w.n, w.nrhs), dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
-
-    for _ in range(a.warmup):
-        plan.evaluate(qd, out=out, stream=stream)
-    torch.cuda.synchronize()
-    launches_per_step = plan.info("last_launches")
+    stream = torch.cuda.Stream(device=dev)
 
     clocks = ClockSampler(local)
     clocks.start()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
-    phases = []
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    for i in range(a.steps):
-        flush.fill_(float(i))
-        starts[i].record(stream)
-        plan.evaluate(qd, out=out, stream=stream)
-        ends[i].record(stream)
-        phases.append(plan.phase_ms())
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    step_ms, phases, launches_per_step = time_mode(plan, qd, out, flush, stream, a.steps,
+                                                   a.warmup, world)
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(total_ms, op=dist.ReduceOp.MAX)
@@ -257,11 +272,30 @@ def main():
 
     # accuracy gate on sampled targets (FP64 direct sum)
     err = None
+    idx = ref = None
     if not a.no_error_check and rank == 0:
         idx = wl.sample_targets(w.n, w.error_samples or 1000, 0)
         ref = direct_sum_sampled(x, q, idx)
         got = out.cpu().numpy()[idx]
         err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+    # the plain FP32 path on the same plan, same protocol ("mixed vs FP32")
+    fp32 = None
+    if a.m2l != "fp32" and not a.quick:
+        plan.set_m2l_mode(N.M2L_FP32)
+        f_ms, f_ph, _ = time_mode(plan, qd, out, flush, stream, a.steps, a.warmup, world)
+        f_tot = torch.tensor([sum(f_ms)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(f_tot, op=dist.ReduceOp.MAX)
+        f_tot = float(f_tot.item())
+        fp32 = {"value": w.n * w.nrhs * a.steps * world / (f_tot / 1e3),
+                "ms_per_step": f_tot / a.steps,
+                "m2l_ms": statistics.mean(ph["m2l"] for ph in f_ph)}
+        if ref is not None:
+            got = out.cpu().numpy()[idx]
+            fp32["rel_l2_err"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        fp32["mixed_over_fp32"] = value / fp32["value"]
+        plan.set_m2l_mode(modes[a.m2l])
 
     # rooflines from the library's per-phase CUDA events (each phase below is
     # one kernel launch on `stream`)
@@ -286,11 +320,16 @@ def main():
     else:
         tc_peak = peaks["bf16_tflops"] * (1.0 if a.m2l == "bf16x3" else 0.5)
         issued = 3 * m2l_flops
-        m2l_roof = {"kernel": "k_m2l_tc", "bound": "tensor", "achieved": issued / (m2l_ms / 1e3) / 1e12,
+        m2l_roof = {"kernel": "k_m2l_tc", "bound": "tensor",
+                    "achieved": issued / (m2l_ms / 1e3) / 1e12,
                     "peak": tc_peak, "unit": "TFLOP/s",
                     "frac": issued / (m2l_ms / 1e3) / 1e12 / tc_peak, "traffic": None,
-                    "peak_source": f"bf16_tflops of {peak_src}" + ("" if a.m2l == "bf16x3" else " x 1/2 (tf32)"),
-                    "flops_per_launch": issued, "ms_per_launch": m2l_ms}
+                    "peak_source": f"bf16_tflops of {peak_src}" +
+                                   ("" if a.m2l == "bf16x3" else " x 1/2 (tf32)"),
+                    "flops_per_launch": issued, "useful_flops_per_launch": m2l_flops,
+                    "useful_frac_of_bf16_peak": m2l_flops / (m2l_ms / 1e3) / 1e12 /
+                    peaks["bf16_tflops"],
+                    "ms_per_launch": m2l_ms}
     leaf_roof = {"kernel": "k_eval", "bound": "alu", "achieved": leaf_tf, "peak": fp32_peak,
                  "unit": "TFLOP/s", "frac": leaf_tf / fp32_peak, "traffic": None,
                  "flops_per_launch": near_flops, "ms_per_launch": leaf_ms,
@@ -303,11 +342,14 @@ def main():
         e2e = run_e2e(plan, q, w, a, world, dev)
 
     if rank == 0:
-        line = {"metric": METRIC.format(mode=a.m2l), "value": value, "unit": UNIT,
+        line = {"metric": METRIC, "value": value, "unit": UNIT,
                 "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
                 "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+                "vs_baseline": None,
+                "dtype": "f32" if a.m2l == "fp32" else f"f32 (M2L {a.m2l} split on tensor cores)",
+                "data": "synthetic", "config": config,
                 "rel_l2_err": err, "error_gate_1e-5": (err is not None and err <= 1e-5),
+                "fp32": fp32,
                 "roofline": dominant, "rooflines": {"m2l": m2l_roof, "leaf": leaf_roof},
                 "phase_ms": {k2: statistics.mean(ph[k2] for ph in phases) for k2 in phases[0]},
                 "e2e": e2e,
@@ -330,13 +372,16 @@ def run_e2e(plan, q, w, a, world, dev):
     import torch.distributed as dist
     qh = torch.tensor(q.astype(np.float32)).pin_memory()
     oh = torch.empty((w.n, w.nrhs), dtype=torch.float64).pin_memory()
-    plan.evaluate(qh, out=oh)
+    stream = torch.cuda.Stream(device=dev)
+    # host buffers: the library copies charges in, replays its graph and
+    # copies potentials out on `stream`, and returns when they have landed
+    plan.evaluate(qh, out=oh, stream=stream)
     steps = max(3, a.steps // 2)
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(steps):
-        plan.evaluate(qh, out=oh)
+        plan.evaluate(qh, out=oh, stream=stream)
     e2e_t = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)

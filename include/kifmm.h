@@ -121,7 +121,14 @@ fmm_status fmm_plan_create_batch_ex(const double *const *sources,
 
 /* Evaluation-time options that may change after creation. */
 enum {
-    FMM_OPT_M2L_MODE = 1 /* value: an fmm_m2l_mode */
+    FMM_OPT_M2L_MODE = 1, /* value: an fmm_m2l_mode */
+    FMM_OPT_GRAPH = 2     /* value 1 (default): fmm_evaluate captures its
+                             kernels into a CUDA graph on the first call for
+                             a given (charges, potentials, nrhs, M2L mode)
+                             and replays the graph on later calls with the
+                             same ones; 0: launch the kernels directly.  The
+                             legacy default stream (NULL) always launches
+                             directly, since it cannot be captured. */
 };
 fmm_status fmm_plan_set_option(fmm_plan_t plan, int key, double value);
 

@@ -16,6 +16,7 @@ STATUS_NAMES = {0: "FMM_OK", 1: "FMM_ERR_INVALID_ARG", 2: "FMM_ERR_CUDA",
                 3: "FMM_ERR_OOM", 4: "FMM_ERR_TIMEOUT", 5: "FMM_ERR_UNSUPPORTED"}
 M2L_FP32, M2L_BF16X3, M2L_TF32X3 = 0, 1, 2
 OPT_M2L_MODE = 1
+OPT_GRAPH = 2
 
 INFO = {"n": 0, "nodes": 1, "leaves": 2, "depth": 3, "nsurf": 4, "rank_m2l": 5,
         "rank_up": 6, "rank_down": 7, "u_pairs": 8, "v_pairs": 9, "w_pairs": 10,

@@ -94,6 +94,18 @@ struct fmm_plan_s {
     float *qh_hi = nullptr, *qh_lo = nullptr;   // split qhat (4-byte slots)
     int qh_cap = 0;                             // nrhs the split buffers hold
     int *err_host = nullptr, *err_dev = nullptr;  // mapped pinned error word
+    // CUDA graph of one evaluation, replayed while its key holds: the
+    // caller's buffers, nrhs, the M2L mode and the workspace generation
+    bool use_graph = true;
+    cudaGraphExec_t graph_exec = nullptr;
+    const void *g_charges = nullptr;
+    const void *g_pot = nullptr;
+    int g_nrhs = 0, g_mode = -1;
+    uint64_t ws_gen = 0, g_ws_gen = 0;
+    void drop_graph() {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        graph_exec = nullptr;
+    }
 
     ~fmm_plan_s() {
         if (opts.host_only) return;
@@ -108,11 +120,13 @@ struct fmm_plan_s {
         if (qh_hi) cudaFree(qh_hi);
         if (qh_lo) cudaFree(qh_lo);
         if (err_host) cudaFreeHost(err_host);
+        drop_graph();
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
         cudaSetDevice(prev);
     }
     void free_workspace() {
+        ++ws_gen;
         void *w[] = {qs, up, down, qhat, chat, xchk, charges_stage, pot_stage, chk, ybuf, yp};
         for (void *a : w)
             if (a) cudaFree(a);
@@ -236,6 +250,7 @@ fmm_status prepare_tc(fmm_plan_s *P, int mode) {
         if (r != CUDA_SUCCESS)
             return fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
     }
+    CK(configure_m2l_tc(kp, tf));
     P->tc_ready[idx] = true;
     return FMM_OK;
 }
@@ -488,6 +503,7 @@ fmm_status ensure_split(fmm_plan_s *P, int nrhs) {
     if (P->qh_lo) cudaFree(P->qh_lo);
     P->qh_hi = P->qh_lo = nullptr;
     P->qh_cap = 0;
+    ++P->ws_gen;
     const size_t bytes = ((size_t)P->tree.nodes() * nrhs + 1) * P->kpad * 4;
     CK(cudaMalloc((void **)&P->qh_hi, bytes));
     CK(cudaMalloc((void **)&P->qh_lo, bytes));
@@ -512,6 +528,63 @@ fmm_status enqueue(fmm_plan_s *P, const float *charges, int nrhs, double *pot,
     return kifmm::plan_enqueue(P, charges, nrhs, pot, b, st);
 }
 
+// One evaluation on `st`: replay the plan's graph when its key holds,
+// otherwise capture the enqueue into a new graph and launch it.  The legacy
+// default stream cannot be captured; there (and with the graph option off)
+// the kernels are launched directly.
+fmm_status run_evaluation(fmm_plan_s *P, const float *charges, int nrhs, double *pot,
+                          cudaStream_t st) {
+    const bool legacy = st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread;
+    if (!P->use_graph || legacy) return enqueue(P, charges, nrhs, pot, st);
+    const int mode = P->opts.m2l_mode;
+    if (P->graph_exec && P->g_charges == charges && P->g_pot == pot && P->g_nrhs == nrhs &&
+        P->g_mode == mode && P->g_ws_gen == P->ws_gen) {
+        CK(cudaGraphLaunch(P->graph_exec, st));
+        return FMM_OK;
+    }
+    P->drop_graph();
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = P->last_launches;
+    fmm_status s = enqueue(P, charges, nrhs, pot, st);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (s != FMM_OK) {
+        if (g) cudaGraphDestroy(g);
+        P->last_launches = before;
+        return s;
+    }
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(FMM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&P->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        P->graph_exec = nullptr;
+        return fail(FMM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    P->g_charges = charges;
+    P->g_pot = pot;
+    P->g_nrhs = nrhs;
+    P->g_mode = mode;
+    P->g_ws_gen = P->ws_gen;
+    CK(cudaGraphLaunch(P->graph_exec, st));
+    return FMM_OK;
+}
+
+} // namespace
+
+namespace {
+// Phase timing events: an external event record node when `st` is being
+// captured into a graph, a plain record otherwise.
+cudaError_t record_phase(cudaEvent_t ev, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive
+               ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal)
+               : cudaEventRecord(ev, st);
+}
 } // namespace
 
 // Enqueue every kernel of one evaluation on `st`, using the given
@@ -532,7 +605,7 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
     w.pot_user = pot;
     if (!b.chk || !b.ybuf || !b.yp) return fail(FMM_ERR_INVALID_ARG, "workspace is incomplete");
     int64_t launches = 0;
-    if (P->timing) CK(cudaEventRecord(P->ev[0], st));
+    if (P->timing) CK(record_phase(P->ev[0], st));
     CK(launch_gather_charges(P->dt, w, st));
     ++launches;
     const DevOps &o = P->dops;
@@ -614,7 +687,7 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
             if (fmm_status e = finish_up(P->d_m2m + a0, cnt)) return e;
         }
     }
-    if (P->timing) CK(cudaEventRecord(P->ev[1], st));
+    if (P->timing) CK(record_phase(P->ev[1], st));
     if (t.depth >= 2 && P->dm.ntiles > 0) {
         const int mode = P->opts.m2l_mode;
         if (mode == FMM_M2L_FP32) {
@@ -629,7 +702,7 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
             launches += 2;
         }
     }
-    if (P->timing) CK(cudaEventRecord(P->ev[2], st));
+    if (P->timing) CK(record_phase(P->ev[2], st));
     if (t.depth >= 2) {
         if (!sc.x_nodes.empty()) ++launches;
         CK(launch_p2l(P->dt, o, w, P->d_xnodes, (int)sc.x_nodes.size(), st));
@@ -683,10 +756,10 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
             if (fmm_status e = gemm(h)) return e;
         }
     }
-    if (P->timing) CK(cudaEventRecord(P->ev[3], st));
+    if (P->timing) CK(record_phase(P->ev[3], st));
     CK(launch_eval(P->dt, P->dops, w, st));
     launches += nrhs / 8 + ((nrhs % 8) >> 2) + ((nrhs % 4) >> 1) + (nrhs % 2);
-    if (P->timing) CK(cudaEventRecord(P->ev[4], st));
+    if (P->timing) CK(record_phase(P->ev[4], st));
     P->last_launches = launches;
     return FMM_OK;
 }
@@ -925,6 +998,11 @@ fmm_status fmm_plan_set_option(fmm_plan_t plan, int key, double value) {
         plan->opts.m2l_mode = mode;
         return FMM_OK;
     }
+    if (key == FMM_OPT_GRAPH) {
+        plan->use_graph = value != 0.0;
+        if (!plan->use_graph) plan->drop_graph();
+        return FMM_OK;
+    }
     return fail(FMM_ERR_INVALID_ARG, "unknown option key");
 }
 
@@ -954,7 +1032,7 @@ fmm_status fmm_evaluate(fmm_plan_t P, const float *charges, int nrhs, double *po
         if (!P->pot_stage) CK(cudaMalloc((void **)&P->pot_stage, (size_t)P->rows * P->nrhs_cap * sizeof(double)));
         dp_ptr = P->pot_stage;
     }
-    s = enqueue(P, dq_ptr, nrhs, dp_ptr, st);
+    s = run_evaluation(P, dq_ptr, nrhs, dp_ptr, st);
     if (s != FMM_OK) return s;
     P->last_stream = st;
     if (!dp) CK(cudaMemcpyAsync(potentials, dp_ptr, nq * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -137,6 +137,9 @@ cudaError_t launch_eval(const DevTree &t, const DevOps &o, const DevWork &w,
 // swizzled boxes of 128 bytes x kpad rows.  *err is set nonzero if a bounded
 // wait expired.
 size_t m2l_tc_smem(int kpad, int *stages);
+// Opt the kernel into its dynamic shared memory (once per process and
+// format, before the first launch; not stream-ordered, so outside captures).
+cudaError_t configure_m2l_tc(int kpad, bool tf32);
 cudaError_t launch_m2l_tc(const DevM2L &m, const DevOps &o, const DevWork &w, int nnodes,
                           bool tf32, const CUtensorMap &s_hi, const CUtensorMap &s_lo,
                           void *qh_hi, void *qh_lo, int *err, int num_sms, cudaStream_t st);

@@ -386,17 +386,19 @@ cudaError_t launch_m2l_tc(const DevM2L &m, const DevOps &o, const DevWork &w, in
     a.err = err;
     const size_t sm = m2l_tc_smem(kp, &a.stages);
     const int grid = std::min(a.nitems, num_sms);
-    cudaError_t e;
-    if (tf32) {
-        e = cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
+    if (tf32)
         k_m2l_tc<true><<<grid, kThreads, sm, st>>>(s_hi, s_lo, a);
-    } else {
-        e = cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
+    else
         k_m2l_tc<false><<<grid, kThreads, sm, st>>>(s_hi, s_lo, a);
-    }
     return cudaGetLastError();
+}
+
+cudaError_t configure_m2l_tc(int kpad, bool tf32) {
+    const int sm = (int)m2l_tc_smem(kpad, nullptr);
+    return tf32 ? cudaFuncSetAttribute(k_m2l_tc<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, sm)
+                : cudaFuncSetAttribute(k_m2l_tc<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 } // namespace kifmm

@@ -138,6 +138,11 @@ class FMMPlan:
     def set_m2l_mode(self, mode: int):
         N.check(N.lib().fmm_plan_set_option(self._h, N.OPT_M2L_MODE, float(mode)))
 
+    def set_graph(self, on: bool):
+        """Capture/replay evaluations as a CUDA graph (default on; never on
+        the legacy default stream)."""
+        N.check(N.lib().fmm_plan_set_option(self._h, N.OPT_GRAPH, 1.0 if on else 0.0))
+
     def evaluate(self, charges, out=None, stream=None):
         """Potentials (n, nrhs) float64 for charges (n,) or (n, nrhs) float32.
 

@@ -15,7 +15,7 @@ import pytest
 
 from oracle.direct import direct_sum
 from oracle.kifmm import KIFMM
-from paper_2303_08394_gb300 import FMMPlan
+from paper_2303_08394_gb300 import FMMPlan, _native as N
 from paper_2303_08394_gb300 import workloads as wl
 
 torch = pytest.importorskip("torch")
@@ -142,6 +142,33 @@ def test_evaluate_on_a_side_stream_and_repeat():
     s.synchronize()
     np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
     assert plan.info("last_launches") >= 5
+
+
+def test_graph_replay_matches_direct_launches():
+    """On a non-default stream an evaluation is captured into a CUDA graph and
+    replayed; the result is bit-identical to launching the kernels directly,
+    and new buffers, a new nrhs or a new M2L mode re-capture."""
+    x, q = wl.gaussian_mixture(9000, 48, nrhs=3)
+    plan = FMMPlan(x, 5, 30)
+    plan.set_graph(False)
+    direct = gpu_eval(plan, q)
+    plan.set_graph(True)
+    s = torch.cuda.Stream()
+    qd = torch.as_tensor(q.astype(np.float32), device="cuda")
+    outs = []
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            outs.append(plan.evaluate(qd).clone())
+        out1 = plan.evaluate(qd[:, :1].contiguous())      # new nrhs and buffers
+        plan.set_m2l_mode(N.M2L_TF32X3)
+        tc = plan.evaluate(qd)                             # new mode
+        plan.set_m2l_mode(N.M2L_FP32)
+        back = plan.evaluate(qd)
+    s.synchronize()
+    for o in outs + [back]:
+        np.testing.assert_array_equal(o.cpu().numpy(), direct)
+    np.testing.assert_array_equal(out1.cpu().numpy()[:, 0], direct[:, 0])
+    assert rel(tc.cpu().numpy(), direct) < 1e-6
 
 
 @pytest.mark.slow
