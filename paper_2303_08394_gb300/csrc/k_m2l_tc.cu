@@ -8,9 +8,10 @@
 //
 // Warp roles (448 threads):
 //   0-3, 10-13  gather the 128 rows of X_t for one 128-byte K chunk into
-//        shared memory in the 128-byte swizzled K-major layout (thread =
-//        row); the two sets take alternate chunks and issue a chunk's loads
-//        before waiting for its stage, so loads overlap the MMAs;
+//        shared memory in the 128-byte swizzled K-major layout (eight lanes
+//        per row, so each warp-wide load covers four whole row chunks); the
+//        two sets take alternate chunks and issue a chunk's loads before
+//        waiting for its stage, so loads overlap the MMAs;
 //   4-7  epilogue: every kGroup offsets, add the TMEM accumulator into a
 //        TMEM running total; after the tile's last offset write the total
 //        (FP32) to chat.  The two-level sum keeps the FP32 rounding of the
@@ -122,32 +123,43 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp < 4 || warp >= 10) {
         // ------------------------------------------------ X_t row gatherers
         // Two sets of 128 threads take alternate K chunks, so two chunks'
-        // loads are in flight while the MMAs consume a third.
+        // loads are in flight while the MMAs consume a third.  Within a set,
+        // eight lanes share a row (one 16-byte piece each), so one warp-wide
+        // load reads four whole 128-byte row chunks; a thread covers the
+        // rows (4 wi + i) * 4 + sub, i < 8, of its warp wi.
         const int set = warp < 4 ? 0 : 1;
-        const int r = set == 0 ? tid : tid - 320;  // row 0..127 of the tile
+        const int wi = set == 0 ? warp : warp - 10;        // warp within the set
+        const int piece = lane & 7, sub = lane >> 3;
         uint32_t j = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x) {
             const int tile = item / a.row_chunks, rc = item - tile * a.row_chunks;
-            const int g = rc * 128 + r;
-            const int slot = g / a.nrhs, rhs = g - slot * a.nrhs;
             const int e0 = a.m.tile_entry_ptr[tile], e1 = a.m.tile_entry_ptr[tile + 1];
             for (int e = e0; e < e1 && ok; ++e) {
-                const int src = a.m.entry_src[(size_t)e * kTileRows + slot];
-                const int qrow = src >= 0 ? src * a.nrhs + rhs : a.zero_row;
-                const uint4 *hi = a.qh_hi + (size_t)qrow * (kp * F::esize / 16);
-                const uint4 *lo = a.qh_lo + (size_t)qrow * (kp * F::esize / 16);
+                // source row of each of this thread's eight tile rows, as an
+                // offset in 16-byte pieces
+                const int row16 = kp * F::esize / 16;
+                uint32_t qoff[8];   // < 2^32: checked by the launcher
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int r = (wi * 8 + i) * 4 + sub;
+                    const int g = rc * 128 + r;
+                    const int slot = g / a.nrhs, rhs = g - slot * a.nrhs;
+                    const int src = a.m.entry_src[(size_t)e * kTileRows + slot];
+                    const int qrow = src >= 0 ? src * a.nrhs + rhs : a.zero_row;
+                    qoff[i] = (uint32_t)qrow * (uint32_t)row16 + (uint32_t)piece;
+                }
                 for (int c = 0; c < a.nch && ok; ++c, ++j) {
                     if ((int)(j & 1) != set) continue;
                     const int s = j % S;
                     const int valid = min(F::kc, kp - c * F::kc);   // elements in this chunk
-                    const int pieces = valid * F::esize / 16;        // 16-byte pieces (<= 8)
+                    const bool mine = piece * 16 < valid * F::esize; // this lane's piece exists
                     uint4 vh[8], vl[8];
 #pragma unroll
-                    for (int p = 0; p < 8; ++p)
-                        if (p < pieces) {
-                            vh[p] = __ldg(hi + c * 8 + p);
-                            vl[p] = __ldg(lo + c * 8 + p);
+                    for (int i = 0; i < 8; ++i)
+                        if (mine) {
+                            vh[i] = __ldg(a.qh_hi + qoff[i] + c * 8);
+                            vl[i] = __ldg(a.qh_lo + qoff[i] + c * 8);
                         }
                     ok = tc::mbar_wait(&empty[s], ((j / S) & 1) ^ 1, abort_flag, kWaitLimit);
                     if (!ok) {
@@ -155,13 +167,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     unsigned char *th = a_tile(s, 0), *tl = a_tile(s, 1);
-                    const uint32_t row_off = (r >> 3) * 1024 + (r & 7) * 128;
 #pragma unroll
-                    for (int p = 0; p < 8; ++p)
-                        if (p < pieces) {
-                            const uint32_t off = row_off + ((p ^ (r & 7)) << 4);
-                            *reinterpret_cast<uint4 *>(th + off) = vh[p];
-                            *reinterpret_cast<uint4 *>(tl + off) = vl[p];
+                    for (int i = 0; i < 8; ++i)
+                        if (mine) {
+                            const int r = (wi * 8 + i) * 4 + sub;
+                            const uint32_t off = (r >> 3) * 1024 + (r & 7) * 128 +
+                                                 ((piece ^ (r & 7)) << 4);
+                            *reinterpret_cast<uint4 *>(th + off) = vh[i];
+                            *reinterpret_cast<uint4 *>(tl + off) = vl[i];
                         }
                     tc::fence_proxy_async_smem();
                     tc::mbar_arrive(&full_a[s]);
@@ -357,6 +370,9 @@ cudaError_t launch_m2l_tc(const DevM2L &m, const DevOps &o, const DevWork &w, in
     if (m.ntiles == 0) return cudaSuccess;
     const int kp = o.kpad;
     const int64_t nrows = (int64_t)nnodes * w.nrhs;
+    // the gatherers address operand rows in 32-bit units of 16 bytes
+    if ((nrows + 1) * (int64_t)kp * (tf32 ? 4 : 2) / 16 >= (int64_t)UINT32_MAX)
+        return cudaErrorInvalidValue;
     // 1. operand split of the compressed multipoles
     {
         int64_t total = (nrows + 1) * kp;
