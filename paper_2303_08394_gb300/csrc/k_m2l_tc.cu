@@ -7,12 +7,13 @@
 // issues x_hi*S_hi + x_hi*S_lo + x_lo*S_hi with FP32 accumulation in TMEM.
 //
 // Warp roles (448 threads):
-//   0-3, 10-13  gather the 128 rows of X_t for one 128-byte K chunk into
-//        shared memory in the 128-byte swizzled K-major layout (eight lanes
-//        per row, so each warp-wide load covers four whole row chunks); the
-//        two sets take alternate chunks and issue a chunk's loads before
-//        waiting for its stage, so loads overlap the MMAs;
-//   4-7  epilogue: every kGroup offsets, add the TMEM accumulator into a
+//   0-3, 10-13  two sets that gather the 128 rows of X_t for one
+//        128-byte K chunk into shared memory in the 128-byte swizzled
+//        K-major layout (eight lanes per row, so each warp-wide load covers
+//        four whole row chunks); the sets take chunks in turn and issue a
+//        chunk's loads before waiting for its stage, so loads overlap the
+//        MMAs;
+//   4-7  epilogue: every group of offsets, add the TMEM accumulator into a
 //        TMEM running total; after the tile's last offset write the total
 //        (FP32) to chat.  The two-level sum keeps the FP32 rounding of the
 //        ~189 k products per target at the level the FP32 path reaches;
@@ -35,17 +36,23 @@ namespace kifmm {
 
 namespace {
 
-constexpr int kThreads = 448;
-#ifndef KIFMM_TC_GROUP
-#define KIFMM_TC_GROUP 1
-#endif
-// Offsets summed in one TMEM accumulator before it is added to the total.
-constexpr int kGroup = KIFMM_TC_GROUP;
+// Gather sets of 128 threads (warps 0-3, then 10-13, 14-17, ...).  A set
+// holds a whole 32 KB K chunk (hi and lo) in registers, 64 per thread; a
+// third set would push the shared register count below what the roles need.
+constexpr int kSets = 2;
+constexpr int kThreads = 32 * (10 + 4 * (kSets - 1));
+// Offsets summed in one TMEM accumulator before it is added to the running
+// total: the tensor core's FP32 accumulation over long sums loses accuracy
+// (all ~189 offsets of a tile in one accumulator: 2.4e-5 relative error
+// with BF16x3), so sums are kept short.  BF16x3 uses 4 (its error, 5.5e-6
+// against the direct sum, is set by the BF16 split itself); TF32x3 uses 1,
+// which its 1e-6 bar needs (4 gave 1.5e-6 against the oracle).
+inline int group_for(bool tf32) { return tf32 ? 1 : 4; }
 constexpr uint64_t kWaitLimit = 2000000000ull;  // 2 s per wait
 
 struct TcArgs {
     DevM2L m;
-    int nrhs, kpad, nch, stages, row_chunks, nitems, nbuf;
+    int nrhs, kpad, nch, stages, row_chunks, nitems, nbuf, group;
     uint32_t tmem_cols;
     const uint4 *qh_hi, *qh_lo;   // rows of kpad elements (16-byte pieces)
     int zero_row;                 // index of an all-zero qhat row
@@ -122,13 +129,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp < 4 || warp >= 10) {
         // ------------------------------------------------ X_t row gatherers
-        // Two sets of 128 threads take alternate K chunks, so two chunks'
-        // loads are in flight while the MMAs consume a third.  Within a set,
-        // eight lanes share a row (one 16-byte piece each), so one warp-wide
-        // load reads four whole 128-byte row chunks; a thread covers the
-        // rows (4 wi + i) * 4 + sub, i < 8, of its warp wi.
-        const int set = warp < 4 ? 0 : 1;
-        const int wi = set == 0 ? warp : warp - 10;        // warp within the set
+        // kSets sets of 128 threads take K chunks in turn, so kSets chunks'
+        // loads are in flight while the MMAs consume earlier stages.  Within
+        // a set, eight lanes share a row (one 16-byte piece each), so one
+        // warp-wide load reads four whole 128-byte row chunks; a thread
+        // covers the rows (4 wi + i) * 4 + sub, i < 8, of its warp wi.
+        const int set = warp < 4 ? 0 : 1 + (warp - 10) / 4;
+        const int wi = warp < 4 ? warp : (warp - 10) % 4;   // warp within the set
         const int piece = lane & 7, sub = lane >> 3;
         uint32_t j = 0;
         bool ok = true;
@@ -150,7 +157,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     qoff[i] = (uint32_t)qrow * (uint32_t)row16 + (uint32_t)piece;
                 }
                 for (int c = 0; c < a.nch && ok; ++c, ++j) {
-                    if ((int)(j & 1) != set) continue;
+                    if ((int)(j % kSets) != set) continue;
                     const int s = j % S;
                     const int valid = min(F::kc, kp - c * F::kc);   // elements in this chunk
                     const bool mine = piece * 16 < valid * F::esize; // this lane's piece exists
@@ -194,7 +201,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int slot = g / a.nrhs, rhs = g - slot * a.nrhs;
             const int tgt = a.m.tile_target[(size_t)tile * kTileRows + slot];
             const int ne = a.m.tile_entry_ptr[tile + 1] - a.m.tile_entry_ptr[tile];
-            const int ngroups = (ne + kGroup - 1) / kGroup;
+            const int ngroups = (ne + a.group - 1) / a.group;
             for (int grp = 0; grp < ngroups; ++grp, ++gi) {
                 const int buf = gi % nbuf;
                 const uint32_t acc_col = (uint32_t)(buf * kp);
@@ -274,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x) {
                 const int tile = item / a.row_chunks;
                 const int e0 = a.m.tile_entry_ptr[tile], e1 = a.m.tile_entry_ptr[tile + 1];
-                for (int eg = e0; eg < e1 && ok; eg += kGroup, ++gi) {
+                for (int eg = e0; eg < e1 && ok; eg += a.group, ++gi) {
                     const int buf = gi % nbuf;
                     const uint32_t acc_col = (uint32_t)(buf * kp);
                     ok = tc::mbar_wait(&acc_empty[buf], ((gi / nbuf) & 1) ^ 1, abort_flag,
@@ -285,7 +292,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     tc::tc_fence_after();
                     uint32_t accumulate = 0;
-                    const int eend = min(e1, eg + kGroup);
+                    const int eend = min(e1, eg + a.group);
                     for (int e = eg; e < eend && ok; ++e) {
                         for (int c = 0; c < a.nch; ++c, ++j) {
                             const int s = j % S;
@@ -392,6 +399,7 @@ cudaError_t launch_m2l_tc(const DevM2L &m, const DevOps &o, const DevWork &w, in
     a.row_chunks = w.nrhs;
     a.nitems = m.ntiles * a.row_chunks;
     a.nbuf = 3 * kp <= 512 ? 2 : 1;
+    a.group = group_for(tf32);
     uint32_t cols = 32;
     while (cols < (uint32_t)((a.nbuf + 1) * kp)) cols <<= 1;
     a.tmem_cols = cols;
