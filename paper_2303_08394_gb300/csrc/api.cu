@@ -260,9 +260,11 @@ fmm_status upload_plan(fmm_plan_s *P) {
     const Operators &o = *P->ops;
     const int64_t nn = t.nodes();
     // points and nodes
-    std::vector<float4> pts(t.n);
-    for (int64_t i = 0; i < t.n; ++i)
+    std::vector<float4> pts(t.n), pts_lo(t.n);
+    for (int64_t i = 0; i < t.n; ++i) {
         pts[i] = make_float4(t.rel[4 * i], t.rel[4 * i + 1], t.rel[4 * i + 2], 0.f);
+        pts_lo[i] = make_float4(t.rel_lo[4 * i], t.rel_lo[4 * i + 1], t.rel_lo[4 * i + 2], 0.f);
+    }
     std::vector<float4> geom(nn);
     std::vector<int2> range(nn);
     std::vector<int> level(nn);
@@ -282,6 +284,8 @@ fmm_status upload_plan(fmm_plan_s *P) {
     float4 *dp;
     if ((s = P->upload(pts, &dp))) return s;
     d.pts = dp;
+    if ((s = P->upload(pts_lo, &dp))) return s;
+    d.pts_lo = dp;
     int64_t *dq, *dout;
     if ((s = P->upload(t.qidx, &dq))) return s;
     if (t.oidx == t.qidx) {

@@ -28,6 +28,7 @@ struct DevTree {
     int64_t n;
     int nnodes, depth;
     const float4 *pts;      // n: position relative to the leaf centre (root units)
+    const float4 *pts_lo;   // n: rounding residual of pts (pts + pts_lo ~ FP64)
     const int64_t *qidx;    // n: charge row of each sorted point (-1 none)
     const int64_t *oidx;    // n: potential row of each sorted point (-1 none)
     const double *node_scale;  // nodes: 1 / (4 pi root half-width) of the

@@ -46,8 +46,16 @@ constexpr int kTMax = 4;
 // minb: resident blocks per SM the register allocation must allow.
 template <int NR> struct Cfg {
     static constexpr int cap = NR == 1 ? 1024 : (NR == 2 ? 768 : 512);
-    static constexpr int minb = NR <= 2 ? 6 : 1;
+    static constexpr int minb = NR == 1 ? 5 : (NR == 2 ? 4 : 1);
 };
+
+// s = fl(a + b); err receives the exact rounding error (a + b = s + err).
+__device__ __forceinline__ float two_sum(float a, float b, float &err) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
 
 struct Kahan {
     float s = 0.f, c = 0.f;
@@ -86,12 +94,55 @@ template <> struct Charges<8> {
     }
 };
 
+// Pairs closer than this fraction of the target leaf's half-width are
+// recomputed from the position residuals (see run()).
+constexpr float kCloseFrac = 0.125f;
+
+template <int NR> struct Smem;
+
+template <bool kSelf>
+__device__ __forceinline__ void pair_terms(float4 p, float3 x, float &r2, float &inv) {
+    const float dx = p.x - x.x, dy = p.y - x.y, dz = p.z - x.z;
+    // Outside B's own points a pair is never coincident in exact arithmetic;
+    // the 1e-30 floor keeps one that rounds to r = 0 in FP32 finite.
+    r2 = fmaf(dx, dx, fmaf(dy, dy, kSelf ? dz * dz : fmaf(dz, dz, 1e-30f)));
+    inv = KIFMM_RSQRT(r2);
+    if (kSelf) inv = r2 > 0.f ? inv : 0.f;
+}
+
+// Residual of staged source k (round `base`): what its FP32 position in B's
+// frame dropped.  Recomputed from the segment table exactly as the staging
+// formed the FP32 position (only surfaces, which are never close, have none).
+template <int NR>
+__device__ float3 staged_residual(const DevTree &t, const Smem<NR> &sm, int nsegw, int f);
+
+// Close pairs.  Positions are FP32 offsets from the target leaf's centre, so
+// a pair at distance r << h (leaf half-width) computed from them alone has
+// relative error ~ eps h / r.  The main loop tracks the smallest r^2 of
+// every block of eight sources (a target with itself excluded); a block
+// whose minimum in any lane is below thr2 = (kCloseFrac h)^2 is handed to
+// fix_block(), which recomputes the FP32 term of each close pair exactly and
+// adds q (1/r_accurate - 1/r_fp32), r_accurate from the position residuals
+// (position = hi + lo to about 2^-48 h).  Such blocks are rare, so the
+// common cost is one min per pair.
+template <int NR, int T>
+__device__ __forceinline__ void fix_block(const DevTree &t, const Smem<NR> &sm, int nsegw, int base,
+                                       int j, bool self_run, const float3 (&x)[T], int t0,
+                                       int leaf_begin, int nt, float thr2, float (&part)[T][NR]);
+
 // Staged sources j = a + 2u + h (j < e; a and e multiples of 16) against
 // this lane's T targets; h is the lane's half-warp.
+// t0: index of the lane's first target among B's points (target i is
+// t0 + 16 i); B's own points are staged first, in order, so in the self run
+// a target meets itself at staged index t0 + 16 i.
 template <int NR, int T, bool kSelf>
-__device__ __forceinline__ void run(const float4 *spos, const float *sq, int a, int e, int h,
-                                    const float3 (&x)[T], float (&part)[T][NR]) {
+__device__ __forceinline__ void run(const DevTree &t, const Smem<NR> &sm, int nsegw, int base,
+                                    int a, int e, int h, const float3 (&x)[T], int t0,
+                                    int leaf_begin, int nt, float thr2, float (&part)[T][NR]) {
+    const float4 *spos = sm.u.st.spos;
+    const float *sq = sm.u.st.sq;
     for (int j = a + h; j < e; j += 16) {
+        float r2min = 3.0e38f;
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const float4 p = spos[j + 2 * u];
@@ -103,18 +154,15 @@ __device__ __forceinline__ void run(const float4 *spos, const float *sq, int a, 
             }
 #pragma unroll
             for (int i = 0; i < T; ++i) {
-                const float dx = p.x - x[i].x, dy = p.y - x[i].y, dz = p.z - x[i].z;
-                // Outside B's own points a pair is never coincident in exact
-                // arithmetic; the 1e-30 floor keeps one that rounds to r = 0
-                // in FP32 finite.
-                const float r2 =
-                    fmaf(dx, dx, fmaf(dy, dy, kSelf ? dz * dz : fmaf(dz, dz, 1e-30f)));
-                float inv = KIFMM_RSQRT(r2);
-                if (kSelf) inv = r2 > 0.f ? inv : 0.f;
+                float r2, inv;
+                pair_terms<kSelf>(p, x[i], r2, inv);
+                if (!kSelf || base + j + 2 * u != t0 + 16 * i) r2min = fminf(r2min, r2);
 #pragma unroll
                 for (int r = 0; r < NR; ++r) part[i][r] = fmaf(q[r], inv, part[i][r]);
             }
         }
+        if (__any_sync(0xffffffffu, r2min < thr2))
+            fix_block<NR, T>(t, sm, nsegw, base, j, kSelf, x, t0, leaf_begin, nt, thr2, part);
     }
 }
 
@@ -131,6 +179,76 @@ template <int NR> struct Smem {
     int seg_node[kSegCap], seg_kind[kSegCap], seg_start[kSegCap + 1];
     int warp_sum[kWarps];
 };
+
+template <int NR>
+__device__ float3 staged_residual(const DevTree &t, const Smem<NR> &sm, int nsegw, int f) {
+    int lo = 0;
+#pragma unroll
+    for (int step = kSegCap / 2; step > 0; step >>= 1) {
+        const int mid = lo + step;
+        if (mid < nsegw && sm.seg_start[mid] <= f) lo = mid;
+    }
+    if (lo >= nsegw || sm.seg_kind[lo] != 0 || f >= sm.seg_start[nsegw])
+        return make_float3(0.f, 0.f, 0.f);
+    const int i = sm.seg_node[lo] + (f - sm.seg_start[lo]);
+    const float4 so = sm.seg_off[lo];
+    const float4 p = __ldg(t.pts + i), pl = __ldg(t.pts_lo + i);
+    float ex, ey, ez;
+    two_sum(p.x, so.x, ex);
+    two_sum(p.y, so.y, ey);
+    two_sum(p.z, so.z, ez);
+    return make_float3(ex + pl.x, ey + pl.y, ez + pl.z);
+}
+
+template <int NR, int T>
+__device__ __forceinline__ void fix_block(const DevTree &t, const Smem<NR> &sm, int nsegw, int base,
+                                       int j, bool self_run, const float3 (&x)[T], int t0,
+                                       int leaf_begin, int nt, float thr2, float (&part)[T][NR]) {
+    float3 xl[T];  // the targets' residuals
+#pragma unroll
+    for (int i = 0; i < T; ++i) {
+        xl[i] = make_float3(0.f, 0.f, 0.f);
+        if (t0 + 16 * i < nt) {
+            const float4 v = __ldg(t.pts_lo + leaf_begin + t0 + 16 * i);
+            xl[i] = make_float3(v.x, v.y, v.z);
+        }
+    }
+    for (int u = 0; u < 8; ++u) {
+        const int k = j + 2 * u;
+        const float4 p = sm.u.st.spos[k];
+        float r2[T], inv[T];
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < T; ++i) {
+            if (self_run) pair_terms<true>(p, x[i], r2[i], inv[i]);
+            else pair_terms<false>(p, x[i], r2[i], inv[i]);
+            if (self_run && base + k == t0 + 16 * i) r2[i] = thr2;  // a target with itself
+            any |= r2[i] < thr2;
+        }
+        if (!any) continue;
+        float q[NR];
+        if constexpr (NR == 1) {
+            q[0] = p.w;
+        } else {
+            Charges<NR>::get(sm.u.st.sq, k, q);
+        }
+        const float3 pl = staged_residual<NR>(t, sm, nsegw, base + k);
+#pragma unroll
+        for (int i = 0; i < T; ++i) {
+            if (!(r2[i] < thr2)) continue;
+            // fl(p - x) is exact to eps |p - x|; the residuals carry what the
+            // FP32 positions dropped.  Distinct points that coincide in FP32
+            // are resolved (exact duplicates keep r2a = 0 and drop out).
+            const float dx = (p.x - x[i].x) + (pl.x - xl[i].x);
+            const float dy = (p.y - x[i].y) + (pl.y - xl[i].y);
+            const float dz = (p.z - x[i].z) + (pl.z - xl[i].z);
+            const float r2a = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float d = (r2a > 0.f ? KIFMM_RSQRT(r2a) : 0.f) - inv[i];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) part[i][r] = fmaf(q[r], d, part[i][r]);
+        }
+    }
+}
 
 template <int NR, int T>
 __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const DevWork &w, int r0,
@@ -160,9 +278,10 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
         const bool active = chunk < nchunk;
         float3 x[T];
         bool valid[T];
+        const int t0 = chunk * CH + tl;  // target i is B's point t0 + 16 i
 #pragma unroll
         for (int i = 0; i < T; ++i) {
-            const int tt = chunk * CH + tl + 16 * i;
+            const int tt = t0 + 16 * i;
             valid[i] = active && tt < nt;
             x[i] = make_float3(-kFar, -kFar, -kFar);
             if (valid[i]) {
@@ -170,6 +289,7 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
                 x[i] = make_float3(p.x, p.y, p.z);
             }
         }
+        const float thr2 = (kCloseFrac * gb.w) * (kCloseFrac * gb.w);
         Kahan acc[T][NR];
 
         for (int sw = 0; sw < nseg; sw += kSegCap) {
@@ -241,7 +361,7 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
 #pragma unroll 4
                 for (int it = 0; it < CAP / kThreads; ++it) {
                     const int k = tid + it * kThreads;
-                    if (k >= mp) break;
+                    if ((k & ~31) >= mp) break;  // whole warp past the end
                     float4 pos = make_float4(kFar, kFar, kFar, 0.f);
                     float q[NR];
 #pragma unroll
@@ -257,7 +377,8 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
                         if (kind == 0) {
                             const int i = sm.seg_node[seg] + off;
                             const float4 p = __ldg(t.pts + i);
-                            pos = make_float4(p.x + so.x, p.y + so.y, p.z + so.z, 0.f);
+                            pos = make_float4(__fadd_rn(p.x, so.x), __fadd_rn(p.y, so.y),
+                                              __fadd_rn(p.z, so.z), 0.f);
                             const float *qi = w.qs + (size_t)i * w.nrhs + r0;
 #pragma unroll
                             for (int r = 0; r < NR; ++r) q[r] = __ldg(qi + r);
@@ -272,13 +393,15 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
                             for (int r = 0; r < NR; ++r) q[r] = __ldg(d + (size_t)r * nsp);
                         }
                     }
-                    if constexpr (NR == 1) {
-                        pos.w = q[0];
-                    } else {
+                    if (k < mp) {
+                        if constexpr (NR == 1) {
+                            pos.w = q[0];
+                        } else {
 #pragma unroll
-                        for (int r = 0; r < NR; ++r) sm.u.st.sq[k * NR + r] = q[r];
+                            for (int r = 0; r < NR; ++r) sm.u.st.sq[k * NR + r] = q[r];
+                        }
+                        sm.u.st.spos[k] = pos;
                     }
-                    sm.u.st.spos[k] = pos;
                 }
                 __syncthreads();
                 if (active) {
@@ -295,8 +418,11 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
                         for (int i = 0; i < T; ++i)
 #pragma unroll
                             for (int r = 0; r < NR; ++r) part[i][r] = 0.f;
-                        if (js > j0) run<NR, T, true>(sm.u.st.spos, sm.u.st.sq, j0, js, half, x, part);
-                        run<NR, T, false>(sm.u.st.spos, sm.u.st.sq, js, j1, half, x, part);
+                        if (js > j0)
+                            run<NR, T, true>(t, sm, nsegw, base, j0, js, half, x, t0, rb.x, nt,
+                                             thr2, part);
+                        run<NR, T, false>(t, sm, nsegw, base, js, j1, half, x, t0, rb.x, nt, thr2,
+                                          part);
 #pragma unroll
                         for (int i = 0; i < T; ++i)
 #pragma unroll

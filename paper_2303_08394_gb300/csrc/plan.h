@@ -56,6 +56,9 @@ struct Tree {
     double centre[3] = {0, 0, 0}, hw = 0;   // root cube
     int depth = 0;
     std::vector<int64_t> perm;              // sorted position -> caller index
+    std::vector<float> rel_lo;              // n x 4: rounding residual of rel
+                                            // (rel + rel_lo is the FP64 value
+                                            // to about 2^-48 of the leaf size)
     std::vector<float> rel;                 // n x 4: position relative to its
                                             // leaf centre, root units, w = 0
     // nodes that hold points, ordered by level then Morton key

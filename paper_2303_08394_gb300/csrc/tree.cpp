@@ -259,13 +259,19 @@ void build_tree(const double *xyz, int64_t n, const TreeOptions &opt,
 
     // point positions relative to their leaf centre, in root units
     t.rel.assign((size_t)4 * n, 0.0f);
+    t.rel_lo.assign((size_t)4 * n, 0.0f);
     for (int32_t lf : t.leaves) {
         double c[3];
         for (int d = 0; d < 3; ++d) c[d] = t.node_centre(lf, d);
         for (int64_t s = t.begin[lf]; s < t.end[lf]; ++s) {
             int64_t i = t.perm[s];
             for (int d = 0; d < 3; ++d)
-                t.rel[4 * s + d] = (float)((xyz[3 * i + d] - t.centre[d]) / t.hw - c[d]);
+            {
+                const double v = (xyz[3 * i + d] - t.centre[d]) / t.hw - c[d];
+                const float hi = (float)v;
+                t.rel[4 * s + d] = hi;
+                t.rel_lo[4 * s + d] = (float)(v - (double)hi);
+            }
         }
     }
 }
@@ -433,6 +439,7 @@ void merge_forest(const std::vector<Tree> &parts, const std::vector<int64_t> &ro
     m.node_problem.assign(nn, 0);
     m.perm.resize(m.n);
     m.rel.resize((size_t)4 * m.n);
+    m.rel_lo.resize((size_t)4 * m.n);
     m.qidx.resize(m.n);
     m.oidx.resize(m.n);
     for (int i = 0; i < np; ++i) {
@@ -445,6 +452,7 @@ void merge_forest(const std::vector<Tree> &parts, const std::vector<int64_t> &ro
             m.oidx[pb + s] = t.oidx[s] >= 0 ? ro + t.oidx[s] : -1;
         }
         std::copy(t.rel.begin(), t.rel.end(), m.rel.begin() + 4 * pb);
+        std::copy(t.rel_lo.begin(), t.rel_lo.end(), m.rel_lo.begin() + 4 * pb);
         const auto &id = newid[i];
         for (int64_t b = 0; b < t.nodes(); ++b) {
             const int32_t q = id[b];

@@ -42,7 +42,8 @@ def gpu_eval(plan, q):
     (wl.uniform_cube, 6000, 4, 32),
     (wl.uniform_cube, 12000, 6, 48),
     (wl.sphere_surface, 8000, 5, 16),
-], ids=["cube_p4", "cube_p6", "sphere_p5"])
+    (wl.sphere_surface, 6000, 7, 32),
+], ids=["cube_p4", "cube_p6", "sphere_p5", "sphere_p7"])
 def test_tc_m2l_matches_oracle(mode, gen, n, p, ncrit):
     x, q = gen(n, 61)
     q = q[:, 0]
