@@ -20,8 +20,8 @@
 //   8    TMA loads of the S_t chunks (hi and lo) for the same K chunk;
 //   9    allocates TMEM, issues the MMAs (one thread), frees TMEM.
 // Stages of shared memory are recycled through mbarriers: producers wait
-// for `empty`, the MMA thread waits for `full_a` / `full_b` and releases the
-// stage with tcgen05.commit.  Every wait is bounded; on expiry the block
+// for `empty`, the MMA thread waits for `full` (gatherers and S_t bytes)
+// and releases the stage with tcgen05.commit.  Every wait is bounded; on expiry the block
 // records the failing role in *err, sets a block-wide abort flag, drains
 // what it issued and frees its TMEM before returning.
 #include <algorithm>
@@ -81,7 +81,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t b_bytes = (uint32_t)kp * 128;       // one split of S_t chunk
     const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)S * stage_bytes);
-    uint64_t *full_a = bars, *full_b = bars + S, *empty = bars + 2 * S;
+    // full[s]: 128 gatherer arrivals + the TMA thread's arrival with the
+    // S_t chunk's bytes, so the MMA thread waits once per stage
+    uint64_t *full = bars, *empty = bars + 2 * S;
     uint64_t *acc_full = bars + 3 * S, *acc_empty = acc_full + 2, *done = acc_full + 4;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -90,8 +92,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
-            tc::mbar_init(&full_a[s], 128);
-            tc::mbar_init(&full_b[s], 1);
+            tc::mbar_init(&full[s], 128 + 1);
             tc::mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             *reinterpret_cast<uint4 *>(tl + off) = vl[i];
                         }
                     tc::fence_proxy_async_smem();
-                    tc::mbar_arrive(&full_a[s]);
+                    tc::mbar_arrive(&full[s]);
                 }
             }
         }
@@ -260,24 +261,33 @@ __global__ void __launch_bounds__(kThreads, 1)
                             if (!*abort_flag) fail(2);
                             break;
                         }
-                        tc::mbar_arrive_expect_tx(&full_b[s], 2 * b_bytes);
-                        tc::tma_load_2d(b_tile(s, 0), &s_hi, &full_b[s], c * F::kc, row0);
-                        tc::tma_load_2d(b_tile(s, 1), &s_lo, &full_b[s], c * F::kc, row0);
+                        tc::mbar_arrive_expect_tx(&full[s], 2 * b_bytes);
+                        tc::tma_load_2d(b_tile(s, 0), &s_hi, &full[s], c * F::kc, row0);
+                        tc::tma_load_2d(b_tile(s, 1), &s_lo, &full[s], c * F::kc, row0);
                     }
                 }
             }
-            // on abort, let the copies already issued land before the block exits
+            // on abort, let the copies already issued land before the block
+            // exits (the phase may also lack gatherer arrivals, so this wait
+            // can run to its limit; the copies take microseconds)
             if (!ok && j > 0) {
                 const uint32_t last = j - 1;
-                tc::mbar_wait(&full_b[last % S], (last / S) & 1, never, kWaitLimit);
+                tc::mbar_wait(&full[last % S], (last / S) & 1, never, kWaitLimit);
             }
         }
     } else {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t id = tc::idesc(F::ab, 128, (uint32_t)kp);
-            uint32_t j = 0, gi = 0;
+            // The MMA thread is the critical path: tcgen05.mma issue proceeds
+            // at the tensor pipe's pace, so everything else it does per stage
+            // adds to the kernel's time.  Stage and phase advance by counting;
+            // the next stage's barrier is polled before this stage's MMAs are
+            // issued, so that poll's latency overlaps the issue.
+            uint32_t s = 0, ph = 0, gi = 0;
+            bool ready = false;
             bool ok = true;
+            const int ks_last = (kp - (a.nch - 1) * F::kc) / F::kstep;
             for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x) {
                 const int tile = item / a.row_chunks;
                 const int e0 = a.m.tile_entry_ptr[tile], e1 = a.m.tile_entry_ptr[tile + 1];
@@ -294,17 +304,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                     uint32_t accumulate = 0;
                     const int eend = min(e1, eg + a.group);
                     for (int e = eg; e < eend && ok; ++e) {
-                        for (int c = 0; c < a.nch; ++c, ++j) {
-                            const int s = j % S;
-                            const uint32_t ph = (j / S) & 1;
-                            ok = tc::mbar_wait(&full_a[s], ph, abort_flag, kWaitLimit) &&
-                                 tc::mbar_wait(&full_b[s], ph, abort_flag, kWaitLimit);
-                            if (!ok) {
-                                if (!*abort_flag) fail(4);
-                                break;
+                        for (int c = 0; c < a.nch; ++c) {
+                            if (!ready) {
+                                ok = tc::mbar_wait(&full[s], ph, abort_flag, kWaitLimit);
+                                if (!ok) {
+                                    if (!*abort_flag) fail(4);
+                                    break;
+                                }
                             }
                             tc::tc_fence_after();
-                            const int ksteps = min(F::kc, kp - c * F::kc) / F::kstep;
+                            const uint32_t s1 = s + 1 == (uint32_t)S ? 0 : s + 1;
+                            const uint32_t ph1 = s1 == 0 ? ph ^ 1 : ph;
+                            const bool ready1 = tc::mbar_try_wait(&full[s1], ph1);
+                            const int ksteps = c == a.nch - 1 ? ks_last : F::kc / F::kstep;
                             const uint32_t ah = tc::smem_u32(a_tile(s, 0)), al = tc::smem_u32(a_tile(s, 1));
                             const uint32_t bh = tc::smem_u32(b_tile(s, 0)), bl = tc::smem_u32(b_tile(s, 1));
                             for (int k = 0; k < ksteps; ++k) {
@@ -319,6 +331,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 tc::mma<kTF32>(tmem + acc_col, dal, dbh, id, 1);
                             }
                             tc::mma_commit(&empty[s]);
+                            s = s1;
+                            ph = ph1;
+                            ready = ready1;
                         }
                     }
                     if (ok) tc::mma_commit(&acc_full[buf]);

@@ -42,16 +42,22 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Bounded wait: false once `limit_ns` nanoseconds have passed without the
-// phase completing, or as soon as *abort is set.
+// Bounded wait: false once about `limit_ns` nanoseconds have passed without
+// the phase completing, or soon after *abort is set.  The abort flag and the
+// clock are looked at only every 256 polls, so a wait that ends quickly
+// costs nothing but the polls themselves.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
                                           volatile int *abort, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = globaltimer_ns();
-    while (true) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (*abort) return false;
-        if (globaltimer_ns() - t0 > limit_ns) return false;
+        if ((it & 255u) == 0) {
+            if (*abort) return false;
+            const uint64_t now = globaltimer_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > limit_ns) return false;
+        }
     }
 }
 
