@@ -80,7 +80,7 @@ struct fmm_plan_s {
     int nrhs_cap = 0;
     float *qs = nullptr, *up = nullptr, *down = nullptr, *qhat = nullptr, *chat = nullptr,
           *xchk = nullptr, *charges_stage = nullptr, *chk = nullptr, *ybuf = nullptr,
-          *yp = nullptr;
+          *yp = nullptr, *part = nullptr;
     double *pot_stage = nullptr;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaStream_t last_stream = nullptr;
@@ -127,10 +127,10 @@ struct fmm_plan_s {
     }
     void free_workspace() {
         ++ws_gen;
-        void *w[] = {qs, up, down, qhat, chat, xchk, charges_stage, pot_stage, chk, ybuf, yp};
+        void *w[] = {qs, up, down, qhat, chat, xchk, charges_stage, pot_stage, chk, ybuf, yp, part};
         for (void *a : w)
             if (a) cudaFree(a);
-        qs = up = down = qhat = chat = xchk = charges_stage = chk = ybuf = yp = nullptr;
+        qs = up = down = qhat = chat = xchk = charges_stage = chk = ybuf = yp = part = nullptr;
         pot_stage = nullptr;
         nrhs_cap = 0;
     }
@@ -495,6 +495,7 @@ fmm_status ensure_workspace(fmm_plan_s *P, int nrhs) {
     CK(alloc(&P->chk, wb.chk));
     CK(alloc(&P->ybuf, wb.ybuf));
     CK(alloc(&P->yp, wb.yp));
+    if (wb.part) CK(alloc(&P->part, wb.part));
     P->nrhs_cap = nrhs;
     return FMM_OK;
 }
@@ -527,6 +528,7 @@ fmm_status enqueue(fmm_plan_s *P, const float *charges, int nrhs, double *pot,
     b.chk = P->chk;
     b.ybuf = P->ybuf;
     b.yp = P->yp;
+    b.part = P->part;
     b.qh_hi = P->qh_hi;
     b.qh_lo = P->qh_lo;
     return kifmm::plan_enqueue(P, charges, nrhs, pot, b, st);
@@ -618,7 +620,10 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
     const int nsp = (ns + 3) & ~3, rPp = (rP + 3) & ~3, rQp = (rQ + 3) & ~3;
     auto gemm = [&](VGemm &g) -> fmm_status {
         g.nrhs = nrhs;
-        if (g.count > 0) ++launches;
+        if (g.count > 0) {
+            ++launches;
+            if (g.part && vgemm_split_floats(g.m, g.count, nrhs, g.nseg) > 0) ++launches;
+        }
         CK(launch_vgemm(g, st));
         return FMM_OK;
     };
@@ -687,6 +692,7 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
             g.scale = o.Ps_inv;
             g.dst = b.ybuf;
             g.dst_ld = rPp;
+            g.part = b.part;
             if (fmm_status e = gemm(g)) return e;
             if (fmm_status e = finish_up(P->d_m2m + a0, cnt)) return e;
         }
@@ -782,6 +788,13 @@ void kifmm::plan_workspace_bytes(const fmm_plan_s *P, int nrhs, WorkspaceBytes *
     out->chk = P->sched.p2m_nodes.size() * nrhs * ns * sizeof(float);
     out->ybuf = (size_t)P->max_level_nodes * nrhs * rmax * sizeof(float);
     out->yp = (size_t)P->max_level_internal * nrhs * 8 * P->ops->rQ * sizeof(float);
+    // split-K scratch of the M2M level products (levels depth-1 .. 2)
+    size_t part = 0;
+    for (int l = t.depth - 1; l >= 2; --l) {
+        const int cnt = P->sched.m2m_level_ptr[l + 1] - P->sched.m2m_level_ptr[l];
+        if (cnt > 0) part = std::max(part, vgemm_split_floats(P->ops->rP, cnt, nrhs, 8));
+    }
+    out->part = part * sizeof(float);
 }
 
 int kifmm::plan_device(const fmm_plan_s *P) { return P->device; }

@@ -116,7 +116,16 @@ struct VGemm {
     int add_ld;
     const int *add_idx;
     const int *add_off;
+    // Optional split-K scratch of nseg x count*nrhs x round4(m) floats: a
+    // product of several segments that would run on few blocks (one block's
+    // K loop then walks every segment in turn) is computed one segment per
+    // block instead, and the partial products are summed in segment order.
+    float *part;
 };
+// A product with a split-K scratch splits its segments when it has fewer
+// than this many blocks for one right-hand side.
+constexpr int kSplitBlocks = 4 * 152;
+size_t vgemm_split_floats(int m, int count, int nrhs, int nseg);  // 0: no split
 cudaError_t launch_vgemm(const VGemm &g, cudaStream_t s);
 
 // Upward check potentials of leaves (k_updown.cu): chk[pos*nrhs + r][j] for

@@ -55,13 +55,17 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
     const int pos_l = vload < nvec ? vload / g.nrhs : -1;
     const int rhs_l = vload < nvec ? vload - pos_l * g.nrhs : 0;
 
+    // split-K: block z computes segment z alone
+    const bool split = g.part != nullptr;
+    const int s_first = split ? (int)blockIdx.z : 0;
+    const int s_end = split ? s_first + 1 : g.nseg;
     int total_chunks = 0;
-    for (int s = 0; s < g.nseg; ++s) total_chunks += (g.seg[s].n + BK - 1) / BK;
+    for (int s = s_first; s < s_end; ++s) total_chunks += (g.seg[s].n + BK - 1) / BK;
 
     // copy chunk `c` (flattened over the segments) into stage `st`
     auto issue = [&](int c) {
         if (c < total_chunks) {
-            int s = 0, cc = c;
+            int s = s_first, cc = c;
             while (cc >= (g.seg[s].n + BK - 1) / BK) {
                 cc -= (g.seg[s].n + BK - 1) / BK;
                 ++s;
@@ -129,6 +133,22 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
     cp_wait_all();
 
     // epilogue
+    if (split) {
+        // partial product of segment z (scaled: the scale is per row, linear)
+        float *pz = g.part + (size_t)blockIdx.z * nvec * mp;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int v = v0 + tv + 8 * q;
+            if (v >= nvec) continue;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int i = i0 + tr * 4 + p;
+                if (i >= g.m) continue;
+                pz[(size_t)v * mp + i] = g.scale ? acc[p][q] * __ldg(g.scale + i) : acc[p][q];
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int v = v0 + tv + 8 * q;
@@ -155,17 +175,62 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
     }
 }
 
+// Sum of the nseg partial products in segment order, then the add row and
+// the scatter of the unsplit epilogue.
+__global__ void k_vreduce(VGemm g) {
+    const int nvec = g.count * g.nrhs;
+    const int mp = (g.m + 3) & ~3;
+    const int64_t total = (int64_t)nvec * g.m;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int v = (int)(t / g.m), i = (int)(t - (int64_t)v * g.m);
+        float r = 0.f;
+        for (int z = 0; z < g.nseg; ++z) r += g.part[((size_t)z * nvec + v) * mp + i];
+        const int pos = v / g.nrhs, rhs = v - pos * g.nrhs;
+        const int dnode = g.dst_idx ? g.dst_idx[pos] : g.dst_base + pos;
+        if (dnode < 0) continue;
+        if (g.add) {
+            const int an = g.add_idx ? g.add_idx[pos] : pos;
+            if (an >= 0)
+                r += g.add[((size_t)an * g.nrhs + rhs) * g.add_ld + (g.add_off ? g.add_off[pos] : 0) + i];
+        }
+        g.dst[((size_t)dnode * g.nrhs + rhs) * g.dst_ld + i] = r;
+    }
+}
+
+// The decision looks at the box count only, not at nrhs, so every column of
+// an evaluation gets the same summation order whatever nrhs it is batched in.
+bool wants_split(int m, int count, int nseg) {
+    const int64_t blocks = (((int64_t)count + BV - 1) / BV) * ((m + BM - 1) / BM);
+    return nseg > 1 && blocks < kSplitBlocks;
+}
+
 } // namespace
 
-cudaError_t launch_vgemm(const VGemm &g, cudaStream_t s) {
-    if (g.count == 0) return cudaSuccess;
-    if (g.nseg < 1 || g.nseg > kMaxSeg) return cudaErrorInvalidValue;
-    for (int k = 0; k < g.nseg; ++k)
-        if ((g.seg[k].src_ld & 3) != 0) return cudaErrorInvalidValue;  // 16-byte rows
+size_t vgemm_split_floats(int m, int count, int nrhs, int nseg) {
+    if (!wants_split(m, count, nseg)) return 0;
+    return (size_t)nseg * count * nrhs * ((m + 3) & ~3);
+}
+
+cudaError_t launch_vgemm(const VGemm &g0, cudaStream_t s) {
+    if (g0.count == 0) return cudaSuccess;
+    if (g0.nseg < 1 || g0.nseg > kMaxSeg) return cudaErrorInvalidValue;
+    for (int k = 0; k < g0.nseg; ++k)
+        if ((g0.seg[k].src_ld & 3) != 0) return cudaErrorInvalidValue;  // 16-byte rows
+    VGemm g = g0;
+    const bool split = g.part && wants_split(g.m, g.count, g.nseg);
+    if (!split) g.part = nullptr;
     const int nvec = g.count * g.nrhs;
-    const dim3 grid((nvec + BV - 1) / BV, (g.m + BM - 1) / BM);
+    const dim3 grid((nvec + BV - 1) / BV, (g.m + BM - 1) / BM, split ? g.nseg : 1);
     if (grid.y > 65535u) return cudaErrorInvalidValue;
     k_vgemm<<<grid, 128, 0, s>>>(g);
+    if (!split) return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t total = (int64_t)nvec * g.m;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_vreduce<<<blocks, 256, 0, s>>>(g);
     return cudaGetLastError();
 }
 

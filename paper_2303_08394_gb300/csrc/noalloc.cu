@@ -65,8 +65,8 @@ extern "C" fmm_status fmm_evaluate_noalloc(fmm_plan_t plan, const float *charges
 
     kifmm::WorkspaceBytes wb;
     kifmm::plan_workspace_bytes(plan, nrhs, &wb);
-    const size_t sizes[11] = {wb.qs, wb.up,  wb.down, wb.qhat, wb.chat, wb.xchk,
-                              wb.qh, wb.qh,  wb.chk,  wb.ybuf, wb.yp};
+    const size_t sizes[12] = {wb.qs, wb.up,  wb.down, wb.qhat, wb.chat, wb.xchk,
+                              wb.qh, wb.qh,  wb.chk,  wb.ybuf, wb.yp,  wb.part};
     size_t total = 0;
     for (size_t s : sizes) total += align256(s);
     if (total > kNoAllocScratchBytes)
@@ -92,8 +92,8 @@ extern "C" fmm_status fmm_evaluate_noalloc(fmm_plan_t plan, const float *charges
     // later reads within the same call, so nothing has to start at zero and
     // the previous call's contents are harmless.
     unsigned char *p = static_cast<unsigned char *>(base);
-    float *parts[11];
-    for (int i = 0; i < 11; ++i) {
+    float *parts[12];
+    for (int i = 0; i < 12; ++i) {
         parts[i] = reinterpret_cast<float *>(p);
         p += align256(sizes[i]);
     }
@@ -109,6 +109,7 @@ extern "C" fmm_status fmm_evaluate_noalloc(fmm_plan_t plan, const float *charges
     b.chk = parts[8];
     b.ybuf = parts[9];
     b.yp = parts[10];
+    b.part = wb.part ? parts[11] : nullptr;
     fmm_status s = kifmm::plan_enqueue(plan, charges, nrhs, potentials, b,
                                        static_cast<cudaStream_t>(stream));
     return s;  // on failure plan_enqueue has set the message fmm_last_error() returns

@@ -14,6 +14,7 @@ struct WorkBuffers {
           *xchk = nullptr;
     float *qh_hi = nullptr, *qh_lo = nullptr;  // tensor-core M2L operand splits
     float *chk = nullptr, *ybuf = nullptr, *yp = nullptr;  // level-product temporaries
+    float *part = nullptr;  // split-K partial products (may be null: no split)
 };
 
 // Byte sizes of those buffers for one plan and nrhs.
@@ -21,6 +22,7 @@ struct WorkspaceBytes {
     size_t qs = 0, up = 0, down = 0, qhat = 0, chat = 0, xchk = 0;
     size_t qh = 0;  // each of the two operand splits (0 for the FP32 M2L)
     size_t chk = 0, ybuf = 0, yp = 0;
+    size_t part = 0;  // split-K scratch of the M2M level products
 };
 
 void plan_workspace_bytes(const fmm_plan_s *P, int nrhs, WorkspaceBytes *out);
