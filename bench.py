@@ -32,6 +32,15 @@ UNIT = "points/s"
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
 CPU_SAMPLE_N = 40_000
+# DRAM bytes (read + write) of one launch, from the ncu captures summarised
+# in profiles/ (k_m2l_tc_cube_n1e6_p6_bf16x3.md, k_eval_cube_n1e6_p6.md).
+# Keyed by kernel, workload and M2L mode; any other combination reports null.
+TRAFFIC = {
+    ("k_m2l_tc", "cube_n1e6_p6_ncrit150", "bf16x3"): 99.3e6,
+    ("k_eval", "cube_n1e6_p6_ncrit150", "bf16x3"): 62.0e6,
+    ("k_eval", "cube_n1e6_p6_ncrit150", "fp32"): 62.0e6,
+    ("k_eval", "cube_n1e6_p6_ncrit150", "tf32x3"): 62.0e6,
+}
 
 
 def parse():
@@ -314,7 +323,7 @@ def main():
     if a.m2l == "fp32":
         m2l_roof = {"kernel": "k_m2l_simt", "bound": "alu", "achieved": m2l_tf,
                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": m2l_tf / fp32_peak,
-                    "traffic": None,
+                    "traffic": TRAFFIC.get(("k_m2l_simt", w.name, a.m2l)),
                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz",
                     "flops_per_launch": m2l_flops, "ms_per_launch": m2l_ms}
     else:
@@ -323,7 +332,8 @@ def main():
         m2l_roof = {"kernel": "k_m2l_tc", "bound": "tensor",
                     "achieved": issued / (m2l_ms / 1e3) / 1e12,
                     "peak": tc_peak, "unit": "TFLOP/s",
-                    "frac": issued / (m2l_ms / 1e3) / 1e12 / tc_peak, "traffic": None,
+                    "frac": issued / (m2l_ms / 1e3) / 1e12 / tc_peak,
+                    "traffic": TRAFFIC.get(("k_m2l_tc", w.name, a.m2l)),
                     "peak_source": f"bf16_tflops of {peak_src}" +
                                    ("" if a.m2l == "bf16x3" else " x 1/2 (tf32)"),
                     "flops_per_launch": issued, "useful_flops_per_launch": m2l_flops,
@@ -331,7 +341,8 @@ def main():
                     peaks["bf16_tflops"],
                     "ms_per_launch": m2l_ms}
     leaf_roof = {"kernel": "k_eval", "bound": "alu", "achieved": leaf_tf, "peak": fp32_peak,
-                 "unit": "TFLOP/s", "frac": leaf_tf / fp32_peak, "traffic": None,
+                 "unit": "TFLOP/s", "frac": leaf_tf / fp32_peak,
+                 "traffic": TRAFFIC.get(("k_eval", w.name, a.m2l)),
                  "flops_per_launch": near_flops, "ms_per_launch": leaf_ms,
                  "note": "near-field pair flops only (8 + 2 nrhs per pair); L2P/M2P work uncounted"}
     dominant = m2l_roof if m2l_ms >= leaf_ms else leaf_roof
