@@ -61,6 +61,24 @@ def parse():
     return a
 
 
+def max_over_ranks(value, world, device="cpu"):
+    """The largest of every rank's `value` (all ranks get it); the timed
+    region of a multi-rank run is its slowest rank's."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, steps, world, seconds):
+    """Whole-job throughput: the units every rank processed over the time of
+    the slowest rank."""
+    return units_per_rank * steps * world / seconds
+
+
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
@@ -272,12 +290,9 @@ def main():
                                                    a.warmup, world)
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
-    total_ms = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(total_ms, op=dist.ReduceOp.MAX)
-    total_ms = float(total_ms.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     ms_per_step = total_ms / a.steps
-    value = w.n * w.nrhs * a.steps * world / (total_ms / 1e3)
+    value = job_value(w.n * w.nrhs, a.steps, world, total_ms / 1e3)
 
     # accuracy gate on sampled targets (FP64 direct sum)
     err = None
@@ -293,11 +308,8 @@ def main():
     if a.m2l != "fp32" and not a.quick:
         plan.set_m2l_mode(N.M2L_FP32)
         f_ms, f_ph, _ = time_mode(plan, qd, out, flush, stream, a.steps, a.warmup, world)
-        f_tot = torch.tensor([sum(f_ms)], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(f_tot, op=dist.ReduceOp.MAX)
-        f_tot = float(f_tot.item())
-        fp32 = {"value": w.n * w.nrhs * a.steps * world / (f_tot / 1e3),
+        f_tot = max_over_ranks(sum(f_ms), world, dev)
+        fp32 = {"value": job_value(w.n * w.nrhs, a.steps, world, f_tot / 1e3),
                 "ms_per_step": f_tot / a.steps,
                 "m2l_ms": statistics.mean(ph["m2l"] for ph in f_ph)}
         if ref is not None:
@@ -393,10 +405,8 @@ def run_e2e(plan, q, w, a, world, dev):
     t0 = time.perf_counter()
     for _ in range(steps):
         plan.evaluate(qh, out=oh, stream=stream)
-    e2e_t = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    return {"value": w.n * w.nrhs * steps * world / float(e2e_t.item()), "unit": UNIT,
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    return {"value": job_value(w.n * w.nrhs, steps, world, e2e_s), "unit": UNIT,
             "h2d_bytes_per_step": w.n * w.nrhs * 4, "d2h_bytes_per_step": w.n * w.nrhs * 8,
             "steps": steps}
 
