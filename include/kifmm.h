@@ -122,6 +122,17 @@ fmm_status fmm_plan_create_batch_ex(const double *const *sources,
 /* Evaluation-time options that may change after creation. */
 enum {
     FMM_OPT_M2L_MODE = 1, /* value: an fmm_m2l_mode */
+    FMM_OPT_AUTOTUNE = 3, /* value 1 (default): the first evaluation of each
+                             nrhs times every tile shape of each level
+                             product (the batched matrix products of the
+                             upward and downward passes) and keeps the
+                             fastest; later evaluations use those.  The
+                             shapes give bit-identical results.  0: the
+                             default shape everywhere. */
+    FMM_OPT_GEMM_SHAPE = 4,/* value -1 (default): shapes as the autotuner
+                             (or its default) chooses; 0, 1, 2: that shape
+                             (64x32, 32x64, 128x16 rows x vectors) for every
+                             level product. */
     FMM_OPT_GRAPH = 2     /* value 1 (default): fmm_evaluate captures its
                              kernels into a CUDA graph on the first call for
                              a given (charges, potentials, nrhs, M2L mode)
@@ -241,7 +252,10 @@ enum {
                                 point, -1 for a target only */
     FMM_ARRAY_OUTPUT_ROW = 18,/* int64 [points]: potential row of each sorted
                                 point, -1 for a source only */
-    FMM_ARRAY_NODE_PROBLEM = 19 /* int32 [nodes]: problem of each box */
+    FMM_ARRAY_NODE_PROBLEM = 19,/* int32 [nodes]: problem of each box */
+    FMM_ARRAY_GEMM_SHAPES = 20 /* int32 [level products]: the tile shape the
+                                autotuner chose for each, in evaluation order
+                                (empty before the first tuned evaluation) */
 };
 /* Copy array `which` into dst (capacity `bytes`).  *needed receives the
  * size in bytes (may be NULL).  dst == NULL only queries the size. */

@@ -17,6 +17,8 @@ STATUS_NAMES = {0: "FMM_OK", 1: "FMM_ERR_INVALID_ARG", 2: "FMM_ERR_CUDA",
 M2L_FP32, M2L_BF16X3, M2L_TF32X3 = 0, 1, 2
 OPT_M2L_MODE = 1
 OPT_GRAPH = 2
+OPT_AUTOTUNE = 3
+OPT_GEMM_SHAPE = 4
 
 INFO = {"n": 0, "nodes": 1, "leaves": 2, "depth": 3, "nsurf": 4, "rank_m2l": 5,
         "rank_up": 6, "rank_down": 7, "u_pairs": 8, "v_pairs": 9, "w_pairs": 10,
@@ -28,7 +30,7 @@ ARRAYS = {"node_keys": (0, "i4"), "node_range": (1, "i8"), "leaf_flag": (2, "i4"
           "w_idx": (9, "i4"), "x_ptr": (10, "i8"), "x_idx": (11, "i4"),
           "surface": (12, "f8"), "m2l_u": (13, "f8"), "m2l_v": (14, "f8"),
           "m2l_s": (15, "f8"), "root": (16, "f8"), "charge_row": (17, "i8"),
-          "output_row": (18, "i8"), "node_problem": (19, "i4")}
+          "output_row": (18, "i8"), "node_problem": (19, "i4"), "gemm_shapes": (20, "i4")}
 
 # every symbol include/kifmm.h declares
 EXPORTS = ("fmm_options_init", "fmm_plan_create", "fmm_plan_create_ex",

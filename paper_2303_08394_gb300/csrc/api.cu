@@ -83,6 +83,7 @@ struct fmm_plan_s {
           *yp = nullptr, *part = nullptr;
     double *pot_stage = nullptr;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t tune_ev[2] = {nullptr, nullptr};
     cudaStream_t last_stream = nullptr;
     int64_t last_launches = 0;
     int num_sms = 0;
@@ -94,6 +95,15 @@ struct fmm_plan_s {
     float *qh_hi = nullptr, *qh_lo = nullptr;   // split qhat (4-byte slots)
     int qh_cap = 0;                             // nrhs the split buffers hold
     int *err_host = nullptr, *err_dev = nullptr;  // mapped pinned error word
+    // Autotuner: tile shape per level-product call site (in enqueue order),
+    // chosen by timing every shape during the first evaluation of each nrhs;
+    // forced_shape >= 0 applies one shape everywhere instead.
+    bool autotune = true;
+    int forced_shape = -1;
+    int tuned_nrhs = 0;
+    bool tuning = false;
+    std::vector<int> gemm_shape;
+    std::vector<float> gemm_ms;   // best time per site (ms) of the last tuning
     // CUDA graph of one evaluation, replayed while its key holds: the
     // caller's buffers, nrhs, the M2L mode and the workspace generation
     bool use_graph = true;
@@ -122,6 +132,8 @@ struct fmm_plan_s {
         if (err_host) cudaFreeHost(err_host);
         drop_graph();
         for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+        for (auto &e : tune_ev)
             if (e) cudaEventDestroy(e);
         cudaSetDevice(prev);
     }
@@ -467,6 +479,7 @@ fmm_status upload_plan(fmm_plan_s *P) {
 #undef UPF
     if (P->timing)
         for (auto &e : P->ev) CK(cudaEventCreate(&e));
+    for (auto &e : P->tune_ev) CK(cudaEventCreate(&e));
     CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
     CK(cudaHostAlloc((void **)&P->err_host, sizeof(int), cudaHostAllocMapped));
     *P->err_host = 0;
@@ -540,6 +553,17 @@ fmm_status enqueue(fmm_plan_s *P, const float *charges, int nrhs, double *pot,
 // the kernels are launched directly.
 fmm_status run_evaluation(fmm_plan_s *P, const float *charges, int nrhs, double *pot,
                           cudaStream_t st) {
+    if (P->autotune && P->forced_shape < 0 && P->tuned_nrhs != nrhs) {
+        // this evaluation tunes the level products (direct launches, timed
+        // one by one) and is itself the result
+        P->tuning = true;
+        fmm_status s = enqueue(P, charges, nrhs, pot, st);
+        P->tuning = false;
+        if (s != FMM_OK) return s;
+        P->tuned_nrhs = nrhs;
+        P->drop_graph();
+        return FMM_OK;
+    }
     const bool legacy = st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread;
     if (!P->use_graph || legacy) return enqueue(P, charges, nrhs, pot, st);
     const int mode = P->opts.m2l_mode;
@@ -618,13 +642,46 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
     const int ns = o.ns, rP = o.rP, rQ = o.rQ, kp = o.kpad;
     // row strides of the per-box arrays, all 16-byte aligned
     const int nsp = (ns + 3) & ~3, rPp = (rP + 3) & ~3, rQp = (rQ + 3) & ~3;
+    int site = 0;
+    if (P->tuning) {
+        P->gemm_shape.clear();
+        P->gemm_ms.clear();
+    }
     auto gemm = [&](VGemm &g) -> fmm_status {
         g.nrhs = nrhs;
+        const int my = site++;
         if (g.count > 0) {
             ++launches;
             if (g.part && vgemm_split_floats(g.m, g.count, nrhs, g.nseg) > 0) ++launches;
         }
-        CK(launch_vgemm(g, st));
+        if (P->tuning) {
+            // time every shape (second of two runs each); no product reads
+            // its own output, so the reruns are idempotent and every shape
+            // writes the same bits
+            int best = 0;
+            float best_ms = 0.f;
+            for (int sh = 0; sh < kGemmShapes && g.count > 0; ++sh) {
+                float ms = 0.f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    CK(cudaEventRecord(P->tune_ev[0], st));
+                    CK(launch_vgemm(g, st, sh));
+                    CK(cudaEventRecord(P->tune_ev[1], st));
+                    CK(cudaEventSynchronize(P->tune_ev[1]));
+                    CK(cudaEventElapsedTime(&ms, P->tune_ev[0], P->tune_ev[1]));
+                }
+                if (sh == 0 || ms < best_ms) {
+                    best = sh;
+                    best_ms = ms;
+                }
+            }
+            P->gemm_shape.push_back(best);
+            P->gemm_ms.push_back(best_ms);
+            CK(launch_vgemm(g, st, best));
+            return FMM_OK;
+        }
+        const int shape = P->forced_shape >= 0 ? P->forced_shape
+                          : my < (int)P->gemm_shape.size() ? P->gemm_shape[my] : 0;
+        CK(launch_vgemm(g, st, shape));
         return FMM_OK;
     };
     auto seg = [](const float *AT, int n, const float *src, int src_ld, const int *idx, int base) {
@@ -1015,6 +1072,19 @@ fmm_status fmm_plan_set_option(fmm_plan_t plan, int key, double value) {
         plan->opts.m2l_mode = mode;
         return FMM_OK;
     }
+    if (key == FMM_OPT_AUTOTUNE) {
+        plan->autotune = value != 0.0;
+        plan->tuned_nrhs = 0;
+        plan->drop_graph();
+        return FMM_OK;
+    }
+    if (key == FMM_OPT_GEMM_SHAPE) {
+        const int sh = (int)value;
+        if (sh < -1 || sh >= kGemmShapes) return fail(FMM_ERR_INVALID_ARG, "shape in [-1, 2]");
+        plan->forced_shape = sh;
+        plan->drop_graph();
+        return FMM_OK;
+    }
     if (key == FMM_OPT_GRAPH) {
         plan->use_graph = value != 0.0;
         if (!plan->use_graph) plan->drop_graph();
@@ -1099,7 +1169,7 @@ fmm_status fmm_plan_get_array(fmm_plan_t P, int which, void *dst, int64_t bytes,
     const void *src = nullptr;
     size_t size = 0;
     std::vector<int64_t> range;
-    std::vector<int32_t> leaf32;
+    std::vector<int32_t> leaf32, shapes;
     switch (which) {
     case FMM_ARRAY_NODE_KEYS: src = t.key.data(); size = t.key.size() * 4; break;
     case FMM_ARRAY_NODE_RANGE:
@@ -1132,6 +1202,11 @@ fmm_status fmm_plan_get_array(fmm_plan_t P, int which, void *dst, int64_t bytes,
     case FMM_ARRAY_ROOT: src = t.roots.data(); size = t.roots.size() * 8; break;
     case FMM_ARRAY_CHARGE_ROW: src = t.qidx.data(); size = t.qidx.size() * 8; break;
     case FMM_ARRAY_OUTPUT_ROW: src = t.oidx.data(); size = t.oidx.size() * 8; break;
+    case FMM_ARRAY_GEMM_SHAPES:
+        shapes.assign(P->gemm_shape.begin(), P->gemm_shape.end());
+        src = shapes.data();
+        size = shapes.size() * 4;
+        break;
     case FMM_ARRAY_NODE_PROBLEM:
         src = t.node_problem.data();
         size = t.node_problem.size() * 4;

@@ -126,7 +126,10 @@ struct VGemm {
 // than this many blocks for one right-hand side.
 constexpr int kSplitBlocks = 4 * 152;
 size_t vgemm_split_floats(int m, int count, int nrhs, int nseg);  // 0: no split
-cudaError_t launch_vgemm(const VGemm &g, cudaStream_t s);
+// Tile shapes of the level products (rows x vectors per block): 0 = 64 x 32,
+// 1 = 32 x 64, 2 = 128 x 16.  Bit-identical results; speed differs by shape.
+constexpr int kGemmShapes = 3;
+cudaError_t launch_vgemm(const VGemm &g, cudaStream_t s, int shape = 0);
 
 // Upward check potentials of leaves (k_updown.cu): chk[pos*nrhs + r][j] for
 // pos < count, rows of `ld` floats.

@@ -10,22 +10,28 @@
 // of 4 floats) with a source array whose row for vector v is chosen through
 // an index list (a child, the parent, the box itself, ...; -1 reads zeros).
 //
-// Tiling: a block computes 64 output rows x 32 vectors with 128 threads,
-// each a 4 x 4 register tile (rows 4*tr.., vectors tv + 8 q).  K advances in
-// chunks of 16; chunks are copied global -> shared with cp.async, kStages
-// chunks in flight, so the per-chunk L2 round trip is paid once per
-// kStages chunks.  Missing sources and the ragged end of K are zero-filled
-// by the copies themselves (source size below 16 bytes).  Every source and
-// operator row stride is a multiple of 4 floats, so each 16-byte copy is
-// aligned.
+// Tiling: a block of 128 threads computes BM output rows x BV vectors, each
+// thread a 4 x 4 register tile (rows 4*tr.., vectors tv + TV q).  Three
+// shapes are compiled -- 64 x 32, 32 x 64 and 128 x 16 -- and the plan's
+// autotuner picks one per call site; every shape computes each output with
+// the same K-ordered FMA chain, so the choice never changes a bit of the
+// result.  K advances in chunks of 16, copied global -> shared with
+// cp.async, kStages chunks in flight, so the per-chunk L2 round trip is paid
+// once per kStages chunks.  Missing sources and the ragged end of K are
+// zero-filled by the copies themselves (source size below 16 bytes).  Every
+// source and operator row stride is a multiple of 4 floats, so each 16-byte
+// copy is aligned.
 #include "device.cuh"
 
 namespace kifmm {
 
 namespace {
 
-constexpr int BM = 64, BV = 32, BK = 16, kStages = 4;
+constexpr int BK = 16, kStages = 4;
 constexpr int XLD = BK + 4;  // padded row of the vector tile (floats)
+// The split-K decision uses this reference shape whatever shape runs, so it
+// (and the rounding it implies) is the same for every variant.
+constexpr int kRefBM = 64, kRefBV = 32;
 
 __device__ __forceinline__ void cp16(void *dst, const void *src, int bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
@@ -39,21 +45,36 @@ __device__ __forceinline__ void cp_wait_stages() {
 }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+template <int BM>
 __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
+    constexpr int TR = BM / 4;          // row groups of 4
+    constexpr int TV = 128 / TR;        // vector lanes
+    constexpr int BV = 4 * TV;          // vectors per block
+    constexpr int XP = BV * 4;          // 16-byte pieces of one X chunk
+    constexpr int AP = BM * 4;          // 16-byte pieces of one A chunk
+    constexpr int XH = (XP + 127) / 128, AH = AP / 128;
+    static_assert(AP % 128 == 0, "whole A pieces per thread");
     __shared__ __align__(16) float As[kStages][BK][BM];     // As[.][j][i]
     __shared__ __align__(16) float Xs[kStages][BV][XLD];    // Xs[.][v][j]
     const int tid = threadIdx.x;
-    const int tr = tid >> 3, tv = tid & 7;
+    const int tr = tid / TV, tv = tid % TV;
     const int i0 = blockIdx.y * BM;
     const int v0 = blockIdx.x * BV;
     const int nvec = g.count * g.nrhs;
     const int mp = (g.m + 3) & ~3;
 
-    // the vector this thread copies (32 vectors x 4 pieces of 4 floats)
-    const int lv = tid >> 2, lq = tid & 3;
-    const int vload = v0 + lv;
-    const int pos_l = vload < nvec ? vload / g.nrhs : -1;
-    const int rhs_l = vload < nvec ? vload - pos_l * g.nrhs : 0;
+    // the X pieces this thread copies: vector lv[h], quarter lq[h]
+    int lv[XH], lq[XH], pos_l[XH], rhs_l[XH];
+#pragma unroll
+    for (int h = 0; h < XH; ++h) {
+        const int q = tid + h * 128;
+        lv[h] = q >> 2;
+        lq[h] = q & 3;
+        const int vload = v0 + lv[h];
+        const bool in = q < XP && vload < nvec;
+        pos_l[h] = in ? vload / g.nrhs : -1;
+        rhs_l[h] = in ? vload - pos_l[h] * g.nrhs : 0;
+    }
 
     // split-K: block z computes segment z alone
     const bool split = g.part != nullptr;
@@ -74,24 +95,28 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
             const int st = c % kStages;
             const int j0 = cc * BK;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int q = tid + h * 128;            // 16 rows x 16 pieces
-                const int jj = q >> 4, ii = (q & 15) * 4;
+            for (int h = 0; h < AH; ++h) {
+                const int q = tid + h * 128;            // 16 rows x BM/4 pieces
+                const int jj = q / (BM / 4), ii = (q % (BM / 4)) * 4;
                 const int j = j0 + jj, i = i0 + ii;
                 const bool in = j < sg.n && i < mp;
                 cp16(&As[st][jj][ii], in ? sg.AT + (size_t)j * mp + i : sg.AT, in ? 16 : 0);
             }
-            int bytes = 0;
-            const float *src = sg.src;
-            if (pos_l >= 0) {
-                const int node = sg.src_idx ? sg.src_idx[pos_l] : sg.src_base + pos_l;
-                const int j = j0 + lq * 4;
-                if (node >= 0 && j < sg.n) {
-                    src = sg.src + ((size_t)node * g.nrhs + rhs_l) * sg.src_ld + j;
-                    bytes = 4 * min(4, sg.n - j);
+#pragma unroll
+            for (int h = 0; h < XH; ++h) {
+                if (tid + h * 128 >= XP) continue;
+                int bytes = 0;
+                const float *src = sg.src;
+                if (pos_l[h] >= 0) {
+                    const int node = sg.src_idx ? sg.src_idx[pos_l[h]] : sg.src_base + pos_l[h];
+                    const int j = j0 + lq[h] * 4;
+                    if (node >= 0 && j < sg.n) {
+                        src = sg.src + ((size_t)node * g.nrhs + rhs_l[h]) * sg.src_ld + j;
+                        bytes = 4 * min(4, sg.n - j);
+                    }
                 }
+                cp16(&Xs[st][lv[h]][lq[h] * 4], src, bytes);
             }
-            cp16(&Xs[st][lv][lq * 4], src, bytes);
         }
         cp_commit();
     };
@@ -118,7 +143,7 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float4 t = *reinterpret_cast<const float4 *>(&Xs[st][tv + 8 * q][k4]);
+                const float4 t = *reinterpret_cast<const float4 *>(&Xs[st][tv + TV * q][k4]);
                 x[q][0] = t.x; x[q][1] = t.y; x[q][2] = t.z; x[q][3] = t.w;
             }
 #pragma unroll
@@ -138,7 +163,7 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
         float *pz = g.part + (size_t)blockIdx.z * nvec * mp;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int v = v0 + tv + 8 * q;
+            const int v = v0 + tv + TV * q;
             if (v >= nvec) continue;
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
@@ -151,7 +176,7 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const int v = v0 + tv + 8 * q;
+        const int v = v0 + tv + TV * q;
         if (v >= nvec) continue;
         const int pos = v / g.nrhs, rhs = v - pos * g.nrhs;
         const int dnode = g.dst_idx ? g.dst_idx[pos] : g.dst_base + pos;
@@ -201,8 +226,17 @@ __global__ void k_vreduce(VGemm g) {
 // The decision looks at the box count only, not at nrhs, so every column of
 // an evaluation gets the same summation order whatever nrhs it is batched in.
 bool wants_split(int m, int count, int nseg) {
-    const int64_t blocks = (((int64_t)count + BV - 1) / BV) * ((m + BM - 1) / BM);
+    const int64_t blocks = (((int64_t)count + kRefBV - 1) / kRefBV) * ((m + kRefBM - 1) / kRefBM);
     return nseg > 1 && blocks < kSplitBlocks;
+}
+
+template <int BM>
+cudaError_t launch_shape(const VGemm &g, int nvec, bool split, cudaStream_t s) {
+    constexpr int BV = 4 * (128 / (BM / 4));
+    const dim3 grid((nvec + BV - 1) / BV, (g.m + BM - 1) / BM, split ? g.nseg : 1);
+    if (grid.y > 65535u || grid.x > 2147483647u) return cudaErrorInvalidValue;
+    k_vgemm<BM><<<grid, 128, 0, s>>>(g);
+    return cudaGetLastError();
 }
 
 } // namespace
@@ -212,7 +246,7 @@ size_t vgemm_split_floats(int m, int count, int nrhs, int nseg) {
     return (size_t)nseg * count * nrhs * ((m + 3) & ~3);
 }
 
-cudaError_t launch_vgemm(const VGemm &g0, cudaStream_t s) {
+cudaError_t launch_vgemm(const VGemm &g0, cudaStream_t s, int shape) {
     if (g0.count == 0) return cudaSuccess;
     if (g0.nseg < 1 || g0.nseg > kMaxSeg) return cudaErrorInvalidValue;
     for (int k = 0; k < g0.nseg; ++k)
@@ -221,12 +255,10 @@ cudaError_t launch_vgemm(const VGemm &g0, cudaStream_t s) {
     const bool split = g.part && wants_split(g.m, g.count, g.nseg);
     if (!split) g.part = nullptr;
     const int nvec = g.count * g.nrhs;
-    const dim3 grid((nvec + BV - 1) / BV, (g.m + BM - 1) / BM, split ? g.nseg : 1);
-    if (grid.y > 65535u) return cudaErrorInvalidValue;
-    k_vgemm<<<grid, 128, 0, s>>>(g);
-    if (!split) return cudaGetLastError();
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e = shape == 1   ? launch_shape<32>(g, nvec, split, s)
+                    : shape == 2 ? launch_shape<128>(g, nvec, split, s)
+                                 : launch_shape<64>(g, nvec, split, s);
+    if (!split || e != cudaSuccess) return e;
     const int64_t total = (int64_t)nvec * g.m;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 152 * 8) blocks = 152 * 8;

@@ -138,6 +138,15 @@ class FMMPlan:
     def set_m2l_mode(self, mode: int):
         N.check(N.lib().fmm_plan_set_option(self._h, N.OPT_M2L_MODE, float(mode)))
 
+    def set_autotune(self, on: bool):
+        """Time the level products' tile shapes on the first evaluation of
+        each nrhs (default on; results are bit-identical either way)."""
+        N.check(N.lib().fmm_plan_set_option(self._h, N.OPT_AUTOTUNE, 1.0 if on else 0.0))
+
+    def set_gemm_shape(self, shape: int):
+        """Force one level-product tile shape (0, 1, 2) or -1 for automatic."""
+        N.check(N.lib().fmm_plan_set_option(self._h, N.OPT_GEMM_SHAPE, float(shape)))
+
     def set_graph(self, on: bool):
         """Capture/replay evaluations as a CUDA graph (default on; never on
         the legacy default stream)."""

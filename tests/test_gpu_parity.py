@@ -171,6 +171,25 @@ def test_graph_replay_matches_direct_launches():
     assert rel(tc.cpu().numpy(), direct) < 1e-6
 
 
+@pytest.mark.parametrize("mode", [N.M2L_FP32, N.M2L_BF16X3], ids=["fp32", "bf16x3"])
+def test_autotuned_tile_shapes_are_bit_identical(mode):
+    """The first evaluation times every tile shape of each level product and
+    keeps the fastest; every shape computes the same bits, so the tuned
+    result equals the result of any forced shape and of tuning off."""
+    x, q = wl.gaussian_mixture(20000, 49, nrhs=2)
+    plan = FMMPlan(x, 6, 40, m2l_mode=mode)
+    tuned = gpu_eval(plan, q)
+    shapes = plan.array("gemm_shapes")
+    assert len(shapes) > 0 and set(shapes.tolist()) <= {0, 1, 2}
+    np.testing.assert_array_equal(gpu_eval(plan, q), tuned)       # replay of the choice
+    for sh in (0, 1, 2):
+        plan.set_gemm_shape(sh)
+        np.testing.assert_array_equal(gpu_eval(plan, q), tuned)
+    plan.set_gemm_shape(-1)
+    plan.set_autotune(False)
+    np.testing.assert_array_equal(gpu_eval(plan, q), tuned)
+
+
 @pytest.mark.slow
 def test_million_point_workload_sampled_against_direct_sum():
     """The 10^6-point uniform workload at p=6, ncrit=150 (the benchmark's
