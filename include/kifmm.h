@@ -46,6 +46,23 @@ typedef enum {
     FMM_M2L_TF32X3 = 2  /* tcgen05 kind::tf32, hi/lo TF32 split, 3 products */
 } fmm_m2l_mode;
 
+/* Where a plan's octree, point order and U/V/W/X lists are built.  Every
+   choice gives the same arrays, bit for bit. */
+typedef enum {
+    FMM_TREE_AUTO = 0,        /* on the device for a problem of at least
+                                 65536 points (unless host_only), else
+                                 FMM_TREE_HOST */
+    FMM_TREE_HOST = 1,        /* recursive splitting and a balance worklist
+                                 on the host */
+    FMM_TREE_DEVICE = 2,      /* level-synchronous passes on the plan's CUDA
+                                 device: Morton radix sort, split sets per
+                                 level, balance from the deepest level up,
+                                 lists by per-box neighbour lookups;
+                                 positions may be host or device pointers */
+    FMM_TREE_LEVELS_HOST = 3  /* the same level-synchronous passes in host
+                                 loops (OpenMP) */
+} fmm_tree_build;
+
 /* Plan options.  fmm_options_init() fills the defaults given here. */
 typedef struct {
     double alpha_inner; /* radius of upward-equivalent / downward-check
@@ -64,7 +81,9 @@ typedef struct {
                            only; fmm_evaluate then returns
                            FMM_ERR_INVALID_ARG.  For inspection. (0) */
     int32_t device;     /* CUDA device ordinal; -1 = current device (-1) */
-    int32_t reserved[7];
+    int32_t tree_build; /* fmm_tree_build: where the octree and the lists
+                           are built (FMM_TREE_AUTO) */
+    int32_t reserved[6];
 } fmm_options;
 
 void fmm_options_init(fmm_options *opts);
@@ -217,7 +236,9 @@ enum {
     FMM_INFO_LAST_LAUNCHES = 15,/* kernels the last evaluation launched */
     FMM_INFO_POINTS = 16,     /* points in the tree (2n with distinct
                                  targets) */
-    FMM_INFO_PROBLEMS = 17    /* independent problems */
+    FMM_INFO_PROBLEMS = 17,   /* independent problems */
+    FMM_INFO_DEVICE_TREES = 18 /* problems whose octree and lists were built
+                                 on the device */
 };
 fmm_status fmm_plan_info(fmm_plan_t plan, int key, int64_t *value);
 

@@ -19,11 +19,12 @@ OPT_M2L_MODE = 1
 OPT_GRAPH = 2
 OPT_AUTOTUNE = 3
 OPT_GEMM_SHAPE = 4
+TREE_AUTO, TREE_HOST, TREE_DEVICE, TREE_LEVELS_HOST = 0, 1, 2, 3
 
 INFO = {"n": 0, "nodes": 1, "leaves": 2, "depth": 3, "nsurf": 4, "rank_m2l": 5,
         "rank_up": 6, "rank_down": 7, "u_pairs": 8, "v_pairs": 9, "w_pairs": 10,
         "x_pairs": 11, "p2p_pairs": 12, "m2l_tiles": 13, "m2l_entries": 14,
-        "last_launches": 15, "points": 16, "problems": 17}
+        "last_launches": 15, "points": 16, "problems": 17, "device_trees": 18}
 ARRAYS = {"node_keys": (0, "i4"), "node_range": (1, "i8"), "leaf_flag": (2, "i4"),
           "perm": (3, "i8"), "u_ptr": (4, "i8"), "u_idx": (5, "i4"),
           "v_ptr": (6, "i8"), "v_idx": (7, "i4"), "w_ptr": (8, "i8"),
@@ -43,7 +44,8 @@ class Options(ctypes.Structure):
                 ("rcond", ctypes.c_double), ("eps_svd", ctypes.c_double),
                 ("max_level", ctypes.c_int32), ("balance", ctypes.c_int32),
                 ("m2l_mode", ctypes.c_int32), ("host_only", ctypes.c_int32),
-                ("device", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("device", ctypes.c_int32), ("tree_build", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class FMMError(RuntimeError):

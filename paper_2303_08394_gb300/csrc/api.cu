@@ -58,6 +58,7 @@ struct fmm_plan_s {
     fmm_options opts;
     int p = 0, ncrit = 0, device = 0;
     int64_t rows = 0;             // caller rows of charges and potentials
+    int device_trees = 0;         // problems whose tree was built on the device
     Tree tree;
     M2LTable m2l;
     Schedules sched;
@@ -884,19 +885,27 @@ fmm_status host_points(const double *src, int64_t n, bool may_be_device,
     return FMM_OK;
 }
 
-// Tree, lists and point roles of one problem from host positions
-// (optional distinct targets: the tree is built on their union).
+// Problems of at least this many points build their tree on the device
+// under FMM_TREE_AUTO.
+constexpr int64_t kDeviceTreeMin = 65536;
+
+// Tree, lists and point roles of one problem (optional distinct targets:
+// the tree is built on their union).  FMM_TREE_DEVICE takes host or device
+// positions, the host builders host positions.
 void build_problem(const double *xs, const double *xt, int64_t n, const TreeOptions &to,
-                   Tree &t) {
-    if (xt) {
+                   int how, Tree &t) {
+    if (how == FMM_TREE_DEVICE || how == FMM_TREE_LEVELS_HOST) {
+        build_tree_levels(xs, xt, n, to, how == FMM_TREE_DEVICE, t);
+    } else if (xt) {
         std::vector<double> all((size_t)6 * n);
         std::copy(xs, xs + 3 * n, all.begin());
         std::copy(xt, xt + 3 * n, all.begin() + 3 * n);
         build_tree(all.data(), 2 * n, to, t);
+        build_lists(t);
     } else {
         build_tree(xs, n, to, t);
+        build_lists(t);
     }
-    build_lists(t);
     set_point_roles(t, n, xt != nullptr);
 }
 
@@ -932,6 +941,10 @@ fmm_status create_plan(const double *const *sources, const double *const *target
     if (o.m2l_mode != FMM_M2L_FP32 && o.m2l_mode != FMM_M2L_BF16X3 &&
         o.m2l_mode != FMM_M2L_TF32X3)
         return fail(FMM_ERR_INVALID_ARG, "unknown M2L mode");
+    if (o.tree_build < FMM_TREE_AUTO || o.tree_build > FMM_TREE_LEVELS_HOST)
+        return fail(FMM_ERR_INVALID_ARG, "unknown tree_build");
+    if (o.tree_build == FMM_TREE_DEVICE && o.host_only)
+        return fail(FMM_ERR_INVALID_ARG, "FMM_TREE_DEVICE needs a device (host_only is set)");
     fmm_plan_s *P = nullptr;
     try {
         P = new fmm_plan_s();
@@ -961,12 +974,26 @@ fmm_status create_plan(const double *const *sources, const double *const *target
         to.ncrit = ncrit;
         to.max_level = o.max_level;
         to.balance = o.balance != 0;
-        // host views of every problem's points (device arrays copied down)
+        // builder of every problem; host views of the points of those built
+        // on the host (device arrays copied down)
+        std::vector<int> how(nproblems);
         std::vector<std::vector<double>> buf(2 * (size_t)nproblems);
         std::vector<const double *> xs(nproblems), xt(nproblems, nullptr);
         for (int i = 0; i < nproblems; ++i) {
-            fmm_status e = host_points(sources[i], n[i], !o.host_only, buf[2 * i], &xs[i]);
-            if (e == FMM_OK && targets && targets[i] && targets[i] != sources[i])
+            const bool distinct = targets && targets[i] && targets[i] != sources[i];
+            const int64_t pts = distinct ? 2 * n[i] : n[i];
+            how[i] = o.tree_build == FMM_TREE_AUTO
+                         ? (!o.host_only && pts >= kDeviceTreeMin ? FMM_TREE_DEVICE : FMM_TREE_HOST)
+                         : o.tree_build;
+            fmm_status e = FMM_OK;
+            if (how[i] == FMM_TREE_DEVICE) {
+                xs[i] = sources[i];
+                xt[i] = distinct ? targets[i] : nullptr;
+                P->device_trees++;
+                continue;
+            }
+            e = host_points(sources[i], n[i], !o.host_only, buf[2 * i], &xs[i]);
+            if (e == FMM_OK && distinct)
                 e = host_points(targets[i], n[i], !o.host_only, buf[2 * i + 1], &xt[i]);
             if (e != FMM_OK) {
                 delete P;
@@ -974,17 +1001,21 @@ fmm_status create_plan(const double *const *sources, const double *const *target
             }
         }
         if (nproblems == 1) {
-            build_problem(xs[0], xt[0], n[0], to, P->tree);
+            build_problem(xs[0], xt[0], n[0], to, how[0], P->tree);
         } else {
             std::vector<Tree> parts(nproblems);
             std::vector<int64_t> row_off(nproblems, 0);
             for (int i = 1; i < nproblems; ++i) row_off[i] = row_off[i - 1] + n[i - 1];
             std::vector<std::string> msg(nproblems);
+            // device builds one after another, then the host builds in parallel
+            for (int i = 0; i < nproblems; ++i)
+                if (how[i] == FMM_TREE_DEVICE) build_problem(xs[i], xt[i], n[i], to, how[i], parts[i]);
             bool bad = false;
 #pragma omp parallel for schedule(dynamic, 1) reduction(|| : bad)
             for (int i = 0; i < nproblems; ++i) {
+                if (how[i] == FMM_TREE_DEVICE) continue;
                 try {
-                    build_problem(xs[i], xt[i], n[i], to, parts[i]);
+                    build_problem(xs[i], xt[i], n[i], to, how[i], parts[i]);
                 } catch (const std::exception &ex) {
                     msg[i] = std::string("problem ") + std::to_string(i) + ": " + ex.what();
                     bad = true;
@@ -1009,6 +1040,10 @@ fmm_status create_plan(const double *const *sources, const double *const *target
     } catch (const std::bad_alloc &) {
         delete P;
         return fail(FMM_ERR_OOM, "host allocation failed");
+    } catch (const CudaFailure &ex) {
+        delete P;
+        return fail(ex.code == (int)cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA,
+                    std::string("device tree build: ") + ex.what());
     } catch (const std::exception &ex) {
         delete P;
         return fail(FMM_ERR_INVALID_ARG, ex.what());
@@ -1033,6 +1068,7 @@ void fmm_options_init(fmm_options *o) {
     o->m2l_mode = FMM_M2L_FP32;
     o->host_only = 0;
     o->device = -1;
+    o->tree_build = FMM_TREE_AUTO;
 }
 
 fmm_status fmm_plan_create(const double *sources, const double *targets, int64_t n, int p,
@@ -1141,6 +1177,7 @@ fmm_status fmm_plan_info(fmm_plan_t P, int key, int64_t *value) {
     case FMM_INFO_N: *value = P->rows; break;
     case FMM_INFO_POINTS: *value = t.n; break;
     case FMM_INFO_PROBLEMS: *value = t.nproblems; break;
+    case FMM_INFO_DEVICE_TREES: *value = P->device_trees; break;
     case FMM_INFO_NODES: *value = t.nodes(); break;
     case FMM_INFO_LEAVES: *value = (int64_t)t.leaves.size(); break;
     case FMM_INFO_DEPTH: *value = t.depth; break;

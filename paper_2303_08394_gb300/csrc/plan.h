@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <memory>
+#include <stdexcept>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -97,6 +98,25 @@ struct TreeOptions {
 // Build the tree (throws std::runtime_error on bad input).
 void build_tree(const double *xyz, int64_t n, const TreeOptions &opt,
                 Tree &tree);
+// Root cube from the coordinate bounds: centred on the bounding box, the
+// half-width of its largest extent inflated by a relative 1e-6 (0.5 when
+// every point coincides).
+void root_cube(const double lo[3], const double hi[3], double centre[3], double &hw);
+
+// A CUDA call failed while building a plan on the device.
+struct CudaFailure : std::runtime_error {
+    int code;
+    CudaFailure(int c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+// The level-synchronous builder: the tree, the sorted point data and the
+// U, V, W, X lists that build_tree + build_lists give, bit for bit, from
+// whole-level passes (Morton sort, split sets per level, 2:1 balance as a
+// closed form over the levels, lists by per-node neighbour lookups).  It
+// runs on the current CUDA device (on_device; xs and xt may be host or
+// device pointers) or on the host (host pointers).  With xt the tree is
+// built on the union of the n sources and the n targets.
+void build_tree_levels(const double *xs, const double *xt, int64_t n, const TreeOptions &opt,
+                       bool on_device, Tree &tree);
 // Fill U, V, W, X lists.
 void build_lists(Tree &tree);
 // Point roles and the single root of a one-problem tree.  With

@@ -79,6 +79,16 @@ double Tree::node_centre(int64_t node, int d) const {
     return -1.0 + (2.0 * key[4 * node + 1 + d] + 1.0) * std::ldexp(1.0, -l);
 }
 
+void root_cube(const double lo[3], const double hi[3], double centre[3], double &hw) {
+    double ext = 0;
+    for (int d = 0; d < 3; ++d) {
+        centre[d] = 0.5 * (lo[d] + hi[d]);
+        ext = std::max(ext, hi[d] - lo[d]);
+    }
+    const double h = 0.5 * ext * (1.0 + 1e-6);
+    hw = h > 0 ? h : 0.5;
+}
+
 void build_tree(const double *xyz, int64_t n, const TreeOptions &opt,
                 Tree &t) {
     if (n < 1) throw std::runtime_error("n must be >= 1");
@@ -96,13 +106,7 @@ void build_tree(const double *xyz, int64_t n, const TreeOptions &opt,
             lo[d] = std::min(lo[d], v);
             hi[d] = std::max(hi[d], v);
         }
-    double ext = 0;
-    for (int d = 0; d < 3; ++d) {
-        t.centre[d] = 0.5 * (lo[d] + hi[d]);
-        ext = std::max(ext, hi[d] - lo[d]);
-    }
-    double hw = 0.5 * ext * (1.0 + 1e-6);
-    t.hw = hw > 0 ? hw : 0.5;
+    root_cube(lo, hi, t.centre, t.hw);
     double corner[3];
     for (int d = 0; d < 3; ++d) corner[d] = t.centre[d] - t.hw;
 
