@@ -2,7 +2,9 @@
 """Benchmark: Laplace KIFMM points/s on one GB300 (or N independent ones).
 
 Workload (default): 10^6 points uniform in the unit cube, charges uniform in
-[-1, 1], p = 6, ncrit = 150, adaptive octree.  One step is one full
+[-1, 1], p = 6, ncrit = 150, adaptive octree; M2L compression tolerance
+eps_svd = 5e-7 (rank k = 127, operand width 128; the error against the
+direct sum is set by p: 5.26e-6 here against 5.24e-6 at eps_svd = 1e-7, k = 143).  One step is one full
 ``fmm_evaluate`` (every operator, the M2L and P2P hot path included) with
 inputs resident in device memory, replayed as a CUDA graph on a side
 stream; L2 is flushed (256 MB write) before every timed step, outside the
@@ -34,12 +36,13 @@ NUM_SMS = 152
 CPU_SAMPLE_N = 40_000
 # DRAM bytes (read + write) of one launch, from the ncu captures summarised
 # in profiles/ (k_m2l_tc_cube_n1e6_p6_bf16x3.md, k_eval_cube_n1e6_p6.md).
-# Keyed by kernel, workload and M2L mode; any other combination reports null.
+# Keyed by kernel, workload, M2L mode and M2L operand width (kpad; the leaf
+# kernel does not depend on it: None); any other combination reports null.
 TRAFFIC = {
-    ("k_m2l_tc", "cube_n1e6_p6_ncrit150", "bf16x3"): 99.3e6,
-    ("k_eval", "cube_n1e6_p6_ncrit150", "bf16x3"): 62.0e6,
-    ("k_eval", "cube_n1e6_p6_ncrit150", "fp32"): 62.0e6,
-    ("k_eval", "cube_n1e6_p6_ncrit150", "tf32x3"): 62.0e6,
+    ("k_m2l_tc", "cube_n1e6_p6_ncrit150", "bf16x3", 128): 78.9e6,
+    ("k_eval", "cube_n1e6_p6_ncrit150", "bf16x3", None): 62.0e6,
+    ("k_eval", "cube_n1e6_p6_ncrit150", "fp32", None): 62.0e6,
+    ("k_eval", "cube_n1e6_p6_ncrit150", "tf32x3", None): 62.0e6,
 }
 
 
@@ -51,6 +54,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="cube_n1e6_p6_ncrit150")
     ap.add_argument("--m2l", default="bf16x3", choices=["fp32", "bf16x3", "tf32x3"])
+    ap.add_argument("--eps-svd", type=float, default=5e-7,
+                    help="M2L compression tolerance (rank: singular values above eps * max)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error-check", action="store_true")
     ap.add_argument("--quick", action="store_true",
@@ -236,7 +241,8 @@ def main():
     from paper_2303_08394_gb300 import workloads as wl
     w = wl.WORKLOADS[a.workload]
     config = {"workload": w.name, "n": w.n, "p": w.p, "ncrit": w.ncrit, "nrhs": w.nrhs,
-              "points": w.kind, "m2l": a.m2l, "graph": "CUDA graph replay on a side stream",
+              "points": w.kind, "m2l": a.m2l, "eps_svd": a.eps_svd,
+              "graph": "CUDA graph replay on a side stream",
               "l2_flush": "256 MB write before every step",
               "per_rank": "independent problem (seed = rank)"}
 
@@ -276,7 +282,7 @@ def main():
     modes = {"fp32": N.M2L_FP32, "bf16x3": N.M2L_BF16X3, "tf32x3": N.M2L_TF32X3}
     x, q = w.generate(rank)
     t0 = time.perf_counter()
-    plan = FMMPlan(x, w.p, w.ncrit, m2l_mode=modes[a.m2l])
+    plan = FMMPlan(x, w.p, w.ncrit, m2l_mode=modes[a.m2l], eps_svd=a.eps_svd)
     plan_s = time.perf_counter() - t0
     qd = torch.as_tensor(q.astype(np.float32), device=dev)
     out = torch.empty((w.n, w.nrhs), dtype=torch.float64, device=dev)
@@ -324,6 +330,7 @@ def main():
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s
     k = plan.info("rank_m2l")
+    kpad = (k + 15) // 16 * 16
     v_pairs = plan.info("v_pairs")
     p2p_pairs = plan.info("p2p_pairs")
     m2l_ms = statistics.mean(ph["m2l"] for ph in phases)
@@ -335,7 +342,7 @@ def main():
     if a.m2l == "fp32":
         m2l_roof = {"kernel": "k_m2l_simt", "bound": "alu", "achieved": m2l_tf,
                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": m2l_tf / fp32_peak,
-                    "traffic": TRAFFIC.get(("k_m2l_simt", w.name, a.m2l)),
+                    "traffic": TRAFFIC.get(("k_m2l_simt", w.name, a.m2l, kpad)),
                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz",
                     "flops_per_launch": m2l_flops, "ms_per_launch": m2l_ms}
     else:
@@ -345,7 +352,7 @@ def main():
                     "achieved": issued / (m2l_ms / 1e3) / 1e12,
                     "peak": tc_peak, "unit": "TFLOP/s",
                     "frac": issued / (m2l_ms / 1e3) / 1e12 / tc_peak,
-                    "traffic": TRAFFIC.get(("k_m2l_tc", w.name, a.m2l)),
+                    "traffic": TRAFFIC.get(("k_m2l_tc", w.name, a.m2l, kpad)),
                     "peak_source": f"bf16_tflops of {peak_src}" +
                                    ("" if a.m2l == "bf16x3" else " x 1/2 (tf32)"),
                     "flops_per_launch": issued, "useful_flops_per_launch": m2l_flops,
@@ -354,7 +361,7 @@ def main():
                     "ms_per_launch": m2l_ms}
     leaf_roof = {"kernel": "k_eval", "bound": "alu", "achieved": leaf_tf, "peak": fp32_peak,
                  "unit": "TFLOP/s", "frac": leaf_tf / fp32_peak,
-                 "traffic": TRAFFIC.get(("k_eval", w.name, a.m2l)),
+                 "traffic": TRAFFIC.get(("k_eval", w.name, a.m2l, None)),
                  "flops_per_launch": near_flops, "ms_per_launch": leaf_ms,
                  "note": "near-field pair flops only (8 + 2 nrhs per pair); L2P/M2P work uncounted"}
     dominant = m2l_roof if m2l_ms >= leaf_ms else leaf_roof
