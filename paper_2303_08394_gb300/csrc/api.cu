@@ -330,7 +330,22 @@ fmm_status upload_plan(fmm_plan_s *P) {
     UP32(level, level);
     UP32(t.parent, parent);
     UP32(t.child, child);
-    UP32(t.leaves, leaves);
+    {
+        // leaves grouped by the leaf pass's targets per lane (one kernel per
+        // group, so each gets the register budget and occupancy of its width)
+        std::vector<int> by_t;
+        by_t.reserve(t.leaves.size());
+        d.t_first[4] = 0;
+        for (int w = 4; w >= 1; --w) {
+            for (int32_t lf : t.leaves) {
+                const int64_t np = t.end[lf] - t.begin[lf];
+                const int tw = (int)std::min<int64_t>(4, std::max<int64_t>(1, (np + 15) / 16));
+                if (tw == w) by_t.push_back(lf);
+            }
+            d.t_first[w - 1] = (int)by_t.size();
+        }
+        UP32(by_t, leaves);
+    }
     UP32(to32(t.u_ptr), u_ptr);
     UP32(t.u_idx, u_idx);
     UP32(to32(t.w_ptr), w_ptr);
@@ -826,7 +841,11 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
     }
     if (P->timing) CK(record_phase(P->ev[3], st));
     CK(launch_eval(P->dt, P->dops, w, st));
-    launches += nrhs / 8 + ((nrhs % 8) >> 2) + ((nrhs % 4) >> 1) + (nrhs % 2);
+    {
+        int groups = 0;  // non-empty leaf width groups: one launch each per column group
+        for (int tw = 1; tw <= 4; ++tw) groups += P->dt.t_first[tw - 1] > P->dt.t_first[tw];
+        launches += (int64_t)groups * (nrhs / 8 + ((nrhs % 8) >> 2) + ((nrhs % 4) >> 1) + (nrhs % 2));
+    }
     if (P->timing) CK(record_phase(P->ev[4], st));
     P->last_launches = launches;
     return FMM_OK;

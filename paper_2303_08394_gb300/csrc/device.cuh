@@ -38,8 +38,13 @@ struct DevTree {
     const int *level;       // nodes
     const int *parent;      // nodes
     const int *child;       // nodes x 8
-    const int *leaves;      // nleaves
+    const int *leaves;      // nleaves, grouped by the leaf pass's targets per
+                            // lane T = min(4, ceil(points / 16)): the leaves
+                            // with T = 4 first, then 3, 2, 1 (plan order
+                            // within each group)
     int nleaves;
+    int t_first[5];         // leaves[t_first[T] .. t_first[T - 1]) have width T
+                            // (t_first[4] = 0, t_first[0] = nleaves)
     const int *u_ptr, *u_idx, *w_ptr, *w_idx, *x_ptr, *x_idx, *v_ptr;
     const int *x_slot;      // nodes: row block in the P2L buffer or -1
 };

@@ -13,7 +13,9 @@
 // difference of box centres, so no precision is lost at deep levels).
 //
 // Compute: a warp owns a chunk of 16 T targets, T = 1..4 chosen per leaf
-// from its size: lane l holds targets (l mod 16) + 16 i, i < T, and the two
+// from its size (the plan groups the leaves by T and each group runs as its
+// own kernel, so the narrow widths keep fewer registers and more resident
+// blocks): lane l holds targets (l mod 16) + 16 i, i < T, and the two
 // half-warps take alternate staged sources, so one shared-memory access
 // (two adjacent 16-byte words) feeds 2 T pairs per lane.  Leaves with at
 // most 16 T targets use one chunk and the four warps split the sources.
@@ -44,9 +46,11 @@ constexpr float kFar = 1.0e15f;    // position of padding sources (charge 0)
 // that the work split (and the rounding) is the same for every column.
 constexpr int kTMax = 4;
 // minb: resident blocks per SM the register allocation must allow.
-template <int NR> struct Cfg {
+// minb: resident blocks per SM the register allocation must allow; the
+// narrow widths (T <= 2, the bulk of the leaves at ncrit ~ 150) fit more.
+template <int NR, int T> struct Cfg {
     static constexpr int cap = NR == 1 ? 1024 : (NR == 2 ? 768 : 512);
-    static constexpr int minb = NR == 1 ? 5 : (NR == 2 ? 4 : 1);
+    static constexpr int minb = NR == 1 ? (T <= 2 ? 7 : 5) : (NR == 2 ? (T <= 2 ? 5 : 4) : 1);
 };
 
 // s = fl(a + b); err receives the exact rounding error (a + b = s + err).
@@ -169,8 +173,8 @@ __device__ __forceinline__ void run(const DevTree &t, const Smem<NR> &sm, int ns
 template <int NR> struct Smem {
     union {
         struct {
-            float4 spos[Cfg<NR>::cap];
-            float sq[NR > 1 ? Cfg<NR>::cap * NR : 4];
+            float4 spos[Cfg<NR, 1>::cap];
+            float sq[NR > 1 ? Cfg<NR, 1>::cap * NR : 4];
         } st;
         // partial sums of the source slices (used after the last round)
         float2 red[kWarps][kTMax * NR][16];
@@ -253,7 +257,7 @@ __device__ __forceinline__ void fix_block(const DevTree &t, const Smem<NR> &sm, 
 template <int NR, int T>
 __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const DevWork &w, int r0,
                                      Smem<NR> &sm, int b, int2 rb, int nt) {
-    constexpr int CAP = Cfg<NR>::cap;
+    constexpr int CAP = Cfg<NR, T>::cap;
     static_assert(CAP % (64 * kWarps) == 0, "rounds must hold whole runs for every slicing");
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int tl = lane & 15, half = lane >> 4;
@@ -476,26 +480,28 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
     }
 }
 
-template <int NR>
-__global__ void __launch_bounds__(kThreads, Cfg<NR>::minb) k_eval(DevTree t, DevOps o, DevWork w, int r0) {
+template <int NR, int T>
+__global__ void __launch_bounds__(kThreads, Cfg<NR, T>::minb) k_eval(DevTree t, DevOps o, DevWork w, int r0) {
     __shared__ __align__(16) Smem<NR> sm;
-    const int b = t.leaves[blockIdx.x];
+    const int b = t.leaves[t.t_first[T] + blockIdx.x];
     const int2 rb = t.range[b];
     const int nt = rb.y - rb.x;
     if (nt <= 0) return;
-    static_assert(kTMax == 4, "dispatch below covers T = 1..4");
-    const int T = min(kTMax, (nt + 15) >> 4);
-    if (T == 1) leaf<NR, 1>(t, o, w, r0, sm, b, rb, nt);
-    else if (T == 2) leaf<NR, 2>(t, o, w, r0, sm, b, rb, nt);
-    else if (T == 3) leaf<NR, 3>(t, o, w, r0, sm, b, rb, nt);
-    else leaf<NR, 4>(t, o, w, r0, sm, b, rb, nt);
+    leaf<NR, T>(t, o, w, r0, sm, b, rb, nt);
 }
 
+// one launch per non-empty width group, widest first (longest blocks
+// start first)
 template <int NR>
 cudaError_t launch_eval_nr(const DevTree &t, const DevOps &o, const DevWork &w, int r0,
                            cudaStream_t s) {
-    if (t.nleaves <= 0) return cudaSuccess;
-    k_eval<NR><<<t.nleaves, kThreads, 0, s>>>(t, o, w, r0);
+    static_assert(kTMax == 4, "width groups 1..4");
+    const int n4 = t.t_first[3] - t.t_first[4], n3 = t.t_first[2] - t.t_first[3];
+    const int n2 = t.t_first[1] - t.t_first[2], n1 = t.t_first[0] - t.t_first[1];
+    if (n4 > 0) k_eval<NR, 4><<<n4, kThreads, 0, s>>>(t, o, w, r0);
+    if (n3 > 0) k_eval<NR, 3><<<n3, kThreads, 0, s>>>(t, o, w, r0);
+    if (n2 > 0) k_eval<NR, 2><<<n2, kThreads, 0, s>>>(t, o, w, r0);
+    if (n1 > 0) k_eval<NR, 1><<<n1, kThreads, 0, s>>>(t, o, w, r0);
     return cudaGetLastError();
 }
 
