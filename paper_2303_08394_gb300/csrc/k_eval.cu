@@ -50,7 +50,7 @@ constexpr int kTMax = 4;
 // narrow widths (T <= 2, the bulk of the leaves at ncrit ~ 150) fit more.
 template <int NR, int T> struct Cfg {
     static constexpr int cap = NR == 1 ? 1024 : (NR == 2 ? 768 : 512);
-    static constexpr int minb = NR == 1 ? (T <= 2 ? 7 : 5) : (NR == 2 ? (T <= 2 ? 5 : 4) : 1);
+    static constexpr int minb = NR == 1 ? (T <= 2 ? 7 : (T == 3 ? 6 : 5)) : (NR == 2 ? (T <= 2 ? 5 : 4) : 1);
 };
 
 // s = fl(a + b); err receives the exact rounding error (a + b = s + err).
