@@ -86,6 +86,20 @@ def laplace_kernel(targets, sources):
     return out
 
 
+def laplace_gradient_kernel(targets, sources):
+    """G[i, j, :] = (s_j - t_i) / (4 pi |t_i - s_j|^3): the gradient of
+    laplace_kernel's entry with respect to the target position t_i; zero
+    where t_i == s_j."""
+    t = np.asarray(targets, dtype=np.float64).reshape(-1, 3)
+    s = np.asarray(sources, dtype=np.float64).reshape(-1, 3)
+    d = s[None, :, :] - t[:, None, :]
+    r = np.sqrt(np.einsum("ijk,ijk->ij", d, d))
+    w = np.zeros_like(r)
+    nz = r > 0.0
+    w[nz] = 1.0 / (FOUR_PI * r[nz] ** 3)
+    return d * w[:, :, None]
+
+
 def surface_grid(p: int):
     """Unit-cube surface points: grid {-1, -1+2/(p-1), ..., 1}^3 on the
     boundary of [-1, 1]^3, lexicographic in (a, b, c) with c fastest.
@@ -360,7 +374,12 @@ class KIFMM:
             self._m2l_cache[key] = m
         return m
 
-    def evaluate(self, charges):
+    def evaluate(self, charges, gradient=False):
+        """Potentials at the points; with gradient=True also their gradients
+        with respect to the target position, (n, 3) or (n, nrhs, 3): the
+        leaf step applies the target-gradient of the kernel to the same
+        sources and densities (near field over U, L2P, M2P); the upward and
+        downward passes do not change."""
         t = self.tree
         q = np.asarray(charges, dtype=np.float64)
         vec = q.ndim == 1
@@ -407,20 +426,30 @@ class KIFMM:
         # leaves: near field (U), L2P (own local density), M2P (W)
         near = np.zeros((len(t.x), nrhs))
         far = np.zeros((len(t.x), nrhs))
+        grad = np.zeros((len(t.x), nrhs, 3)) if gradient else None
+
+        def apply(tidx, xt, srcs, dens, acc):
+            acc[tidx] += laplace_kernel(xt, srcs) @ dens
+            if gradient:
+                grad[tidx] += np.einsum("ijk,jr->irk", laplace_gradient_kernel(xt, srcs), dens)
+
         for b in t.leaves:
             tidx = t.points[b]
             xt = t.x[tidx]
             for a in self.U[b]:
                 sidx = t.points[a]
-                near[tidx] += laplace_kernel(xt, t.x[sidx]) @ q[sidx]
+                apply(tidx, xt, t.x[sidx], q[sidx], near)
             if b[0] >= 2:
-                far[tidx] += laplace_kernel(xt, self._surface(b, ao)) @ down[b]
+                apply(tidx, xt, self._surface(b, ao), down[b], far)
             for a in self.W.get(b, ()):
-                far[tidx] += laplace_kernel(xt, self._surface(a, ai)) @ up[a]
+                apply(tidx, xt, self._surface(a, ai), up[a], far)
         self.up, self.down, self.down_check = up, down, down_check
         self.near, self.far = near, far
         phi = near + far
-        return phi[:, 0] if vec else phi
+        phi = phi[:, 0] if vec else phi
+        if not gradient:
+            return phi
+        return phi, (grad[:, 0, :] if vec else grad)
 
 
 def fmm(points, charges, p, ncrit, **kw):
