@@ -181,6 +181,27 @@ fmm_status fmm_evaluate(fmm_plan_t plan, const float *charges, int nrhs,
                         double *potentials, void *stream);
 
 /*
+ * Gradients of the potentials with respect to the target positions (the
+ * field is minus this), beside or instead of the potentials:
+ *
+ *     grad_j = sum_{i != j} q_i (x_i - y_j) / (4 pi |x_i - y_j|^3),
+ *
+ * the derivative of Eq. (1) in the target position.  The kernel-independent
+ * method admits it ("The Fast Multipole Method" section: any kernel the
+ * evaluation step can apply): the upward and downward passes and the M2L are
+ * those of fmm_evaluate; only the leaf step (near field over U, L2P, M2P)
+ * applies the target-gradient of the kernel, in FP32 with Kahan-compensated
+ * sums and the same close-pair correction, then FP64 output.
+ *
+ * gradients   n x nrhs x 3 row-major FP64, overwritten, caller's point order.
+ * potentials  as in fmm_evaluate, or NULL (not written).
+ * charges, stream, host/device pointers and synchronisation: as in
+ * fmm_evaluate.  NULL gradients return FMM_ERR_INVALID_ARG.
+ */
+fmm_status fmm_evaluate_gradient(fmm_plan_t plan, const float *charges, int nrhs,
+                                 double *potentials, double *gradients, void *stream);
+
+/*
  * The evaluation of fmm_evaluate without any device allocation.  The paper
  * has no counterpart: this serves callers that may not allocate device
  * memory while they evaluate -- an application whose device memory is owned

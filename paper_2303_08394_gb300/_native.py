@@ -35,7 +35,7 @@ ARRAYS = {"node_keys": (0, "i4"), "node_range": (1, "i8"), "leaf_flag": (2, "i4"
 
 # every symbol include/kifmm.h declares
 EXPORTS = ("fmm_options_init", "fmm_plan_create", "fmm_plan_create_ex",
-           "fmm_plan_create_batch", "fmm_plan_create_batch_ex", "fmm_plan_set_option", "fmm_evaluate", "fmm_evaluate_noalloc", "fmm_destroy",
+           "fmm_plan_create_batch", "fmm_plan_create_batch_ex", "fmm_plan_set_option", "fmm_evaluate", "fmm_evaluate_gradient", "fmm_evaluate_noalloc", "fmm_destroy",
            "fmm_last_error", "fmm_plan_info", "fmm_plan_get_array", "fmm_plan_phase_ms")
 
 
@@ -81,6 +81,7 @@ def lib():
     L.fmm_plan_set_option.argtypes = [vp, ctypes.c_int, ctypes.c_double]
     L.fmm_evaluate.argtypes = [vp, fp, ctypes.c_int, dp, vp]
     L.fmm_evaluate_noalloc.argtypes = [vp, fp, ctypes.c_int, dp, vp]
+    L.fmm_evaluate_gradient.argtypes = [vp, fp, ctypes.c_int, dp, dp, vp]
     L.fmm_destroy.argtypes = [vp]
     L.fmm_destroy.restype = None
     L.fmm_last_error.argtypes = []
@@ -90,7 +91,7 @@ def lib():
     L.fmm_plan_phase_ms.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     for name in ("fmm_plan_create", "fmm_plan_create_ex", "fmm_plan_create_batch",
                  "fmm_plan_create_batch_ex", "fmm_plan_set_option",
-                 "fmm_evaluate", "fmm_evaluate_noalloc", "fmm_plan_info", "fmm_plan_get_array", "fmm_plan_phase_ms"):
+                 "fmm_evaluate", "fmm_evaluate_gradient", "fmm_evaluate_noalloc", "fmm_plan_info", "fmm_plan_get_array", "fmm_plan_phase_ms"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L

@@ -82,7 +82,7 @@ struct fmm_plan_s {
     float *qs = nullptr, *up = nullptr, *down = nullptr, *qhat = nullptr, *chat = nullptr,
           *xchk = nullptr, *charges_stage = nullptr, *chk = nullptr, *ybuf = nullptr,
           *yp = nullptr, *part = nullptr;
-    double *pot_stage = nullptr;
+    double *pot_stage = nullptr, *grad_stage = nullptr;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t tune_ev[2] = {nullptr, nullptr};
     cudaStream_t last_stream = nullptr;
@@ -111,6 +111,7 @@ struct fmm_plan_s {
     cudaGraphExec_t graph_exec = nullptr;
     const void *g_charges = nullptr;
     const void *g_pot = nullptr;
+    const void *g_grad = nullptr;
     int g_nrhs = 0, g_mode = -1;
     uint64_t ws_gen = 0, g_ws_gen = 0;
     void drop_graph() {
@@ -140,11 +141,12 @@ struct fmm_plan_s {
     }
     void free_workspace() {
         ++ws_gen;
-        void *w[] = {qs, up, down, qhat, chat, xchk, charges_stage, pot_stage, chk, ybuf, yp, part};
+        void *w[] = {qs,    up,        down,       qhat, chat, xchk, charges_stage,
+                     pot_stage, grad_stage, chk, ybuf, yp,   part};
         for (void *a : w)
             if (a) cudaFree(a);
         qs = up = down = qhat = chat = xchk = charges_stage = chk = ybuf = yp = part = nullptr;
-        pot_stage = nullptr;
+        pot_stage = grad_stage = nullptr;
         nrhs_cap = 0;
     }
     template <class T> fmm_status upload(const std::vector<T> &v, T **out) {
@@ -545,7 +547,7 @@ fmm_status ensure_split(fmm_plan_s *P, int nrhs) {
     return FMM_OK;
 }
 
-fmm_status enqueue(fmm_plan_s *P, const float *charges, int nrhs, double *pot,
+fmm_status enqueue(fmm_plan_s *P, const float *charges, int nrhs, double *pot, double *grad,
                    cudaStream_t st) {
     WorkBuffers b;
     b.qs = P->qs;
@@ -560,7 +562,7 @@ fmm_status enqueue(fmm_plan_s *P, const float *charges, int nrhs, double *pot,
     b.part = P->part;
     b.qh_hi = P->qh_hi;
     b.qh_lo = P->qh_lo;
-    return kifmm::plan_enqueue(P, charges, nrhs, pot, b, st);
+    return kifmm::plan_enqueue(P, charges, nrhs, pot, grad, b, st);
 }
 
 // One evaluation on `st`: replay the plan's graph when its key holds,
@@ -568,12 +570,12 @@ fmm_status enqueue(fmm_plan_s *P, const float *charges, int nrhs, double *pot,
 // default stream cannot be captured; there (and with the graph option off)
 // the kernels are launched directly.
 fmm_status run_evaluation(fmm_plan_s *P, const float *charges, int nrhs, double *pot,
-                          cudaStream_t st) {
+                          double *grad, cudaStream_t st) {
     if (P->autotune && P->forced_shape < 0 && P->tuned_nrhs != nrhs) {
         // this evaluation tunes the level products (direct launches, timed
         // one by one) and is itself the result
         P->tuning = true;
-        fmm_status s = enqueue(P, charges, nrhs, pot, st);
+        fmm_status s = enqueue(P, charges, nrhs, pot, grad, st);
         P->tuning = false;
         if (s != FMM_OK) return s;
         P->tuned_nrhs = nrhs;
@@ -581,17 +583,17 @@ fmm_status run_evaluation(fmm_plan_s *P, const float *charges, int nrhs, double 
         return FMM_OK;
     }
     const bool legacy = st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread;
-    if (!P->use_graph || legacy) return enqueue(P, charges, nrhs, pot, st);
+    if (!P->use_graph || legacy) return enqueue(P, charges, nrhs, pot, grad, st);
     const int mode = P->opts.m2l_mode;
-    if (P->graph_exec && P->g_charges == charges && P->g_pot == pot && P->g_nrhs == nrhs &&
-        P->g_mode == mode && P->g_ws_gen == P->ws_gen) {
+    if (P->graph_exec && P->g_charges == charges && P->g_pot == pot && P->g_grad == grad &&
+        P->g_nrhs == nrhs && P->g_mode == mode && P->g_ws_gen == P->ws_gen) {
         CK(cudaGraphLaunch(P->graph_exec, st));
         return FMM_OK;
     }
     P->drop_graph();
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     const int64_t before = P->last_launches;
-    fmm_status s = enqueue(P, charges, nrhs, pot, st);
+    fmm_status s = enqueue(P, charges, nrhs, pot, grad, st);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(st, &g);
     if (s != FMM_OK) {
@@ -611,6 +613,7 @@ fmm_status run_evaluation(fmm_plan_s *P, const float *charges, int nrhs, double 
     }
     P->g_charges = charges;
     P->g_pot = pot;
+    P->g_grad = grad;
     P->g_nrhs = nrhs;
     P->g_mode = mode;
     P->g_ws_gen = P->ws_gen;
@@ -636,7 +639,7 @@ cudaError_t record_phase(cudaEvent_t ev, cudaStream_t st) {
 // Enqueue every kernel of one evaluation on `st`, using the given
 // per-evaluation buffers (sized for nrhs, see plan_workspace_bytes).
 fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, double *pot,
-                               const WorkBuffers &b, cudaStream_t st) {
+                               double *grad, const WorkBuffers &b, cudaStream_t st) {
     const Tree &t = P->tree;
     const Schedules &sc = P->sched;
     DevWork w{};
@@ -649,6 +652,7 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
     w.chat = b.chat;
     w.xchk = b.xchk;
     w.pot_user = pot;
+    w.grad_user = grad;
     if (!b.chk || !b.ybuf || !b.yp) return fail(FMM_ERR_INVALID_ARG, "workspace is incomplete");
     int64_t launches = 0;
     if (P->timing) CK(record_phase(P->ev[0], st));
@@ -844,7 +848,9 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
     {
         int groups = 0;  // non-empty leaf width groups: one launch each per column group
         for (int tw = 1; tw <= 4; ++tw) groups += P->dt.t_first[tw - 1] > P->dt.t_first[tw];
-        launches += (int64_t)groups * (nrhs / 8 + ((nrhs % 8) >> 2) + ((nrhs % 4) >> 1) + (nrhs % 2));
+        // (gradients: one column per launch)
+        launches += (int64_t)groups * (grad ? nrhs : nrhs / 8 + ((nrhs % 8) >> 2) +
+                                                      ((nrhs % 4) >> 1) + (nrhs % 2));
     }
     if (P->timing) CK(record_phase(P->ev[4], st));
     P->last_launches = launches;
@@ -1071,6 +1077,52 @@ fmm_status create_plan(const double *const *sources, const double *const *target
     return FMM_OK;
 }
 
+// fmm_evaluate / fmm_evaluate_gradient: host buffers are staged through
+// plan-owned device memory; potentials may be NULL when gradients are asked.
+fmm_status evaluate_impl(fmm_plan_s *P, const float *charges, int nrhs, double *potentials,
+                         double *gradients, void *stream) {
+    if (!P) return fail(FMM_ERR_INVALID_ARG, "plan is NULL");
+    if (P->opts.host_only) return fail(FMM_ERR_INVALID_ARG, "host-only plan cannot evaluate");
+    if (!charges) return fail(FMM_ERR_INVALID_ARG, "NULL charges or potentials");
+    if (nrhs < 1) return fail(FMM_ERR_INVALID_ARG, "nrhs must be >= 1");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(P->device));
+    if (fmm_status e = kifmm::plan_check_device_error(P)) return e;
+    const bool dq = is_device_pointer(charges);
+    const bool dp = !potentials || is_device_pointer(potentials);
+    const bool dg = !gradients || is_device_pointer(gradients);
+    fmm_status s = ensure_workspace(P, nrhs);
+    if (s != FMM_OK) return s;
+    s = ensure_split(P, nrhs);
+    if (s != FMM_OK) return s;
+    const size_t nq = (size_t)P->rows * nrhs;
+    const float *dq_ptr = charges;
+    double *dp_ptr = potentials, *dg_ptr = gradients;
+    if (!dq) {
+        if (!P->charges_stage) CK(cudaMalloc((void **)&P->charges_stage, (size_t)P->rows * P->nrhs_cap * sizeof(float)));
+        CK(cudaMemcpyAsync(P->charges_stage, charges, nq * sizeof(float), cudaMemcpyHostToDevice, st));
+        dq_ptr = P->charges_stage;
+    }
+    if (!dp) {
+        if (!P->pot_stage) CK(cudaMalloc((void **)&P->pot_stage, (size_t)P->rows * P->nrhs_cap * sizeof(double)));
+        dp_ptr = P->pot_stage;
+    }
+    if (!dg) {
+        if (!P->grad_stage) CK(cudaMalloc((void **)&P->grad_stage, (size_t)P->rows * P->nrhs_cap * 3 * sizeof(double)));
+        dg_ptr = P->grad_stage;
+    }
+    s = run_evaluation(P, dq_ptr, nrhs, dp_ptr, dg_ptr, st);
+    if (s != FMM_OK) return s;
+    P->last_stream = st;
+    if (!dp) CK(cudaMemcpyAsync(potentials, dp_ptr, nq * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (!dg) CK(cudaMemcpyAsync(gradients, dg_ptr, 3 * nq * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (!dq || !dp || !dg) {
+        CK(cudaStreamSynchronize(st));
+        return kifmm::plan_check_device_error(P);
+    }
+    return FMM_OK;
+}
+
 } // namespace
 
 extern "C" {
@@ -1150,39 +1202,14 @@ fmm_status fmm_plan_set_option(fmm_plan_t plan, int key, double value) {
 
 fmm_status fmm_evaluate(fmm_plan_t P, const float *charges, int nrhs, double *potentials,
                         void *stream) {
-    if (!P) return fail(FMM_ERR_INVALID_ARG, "plan is NULL");
-    if (P->opts.host_only) return fail(FMM_ERR_INVALID_ARG, "host-only plan cannot evaluate");
-    if (!charges || !potentials) return fail(FMM_ERR_INVALID_ARG, "NULL charges or potentials");
-    if (nrhs < 1) return fail(FMM_ERR_INVALID_ARG, "nrhs must be >= 1");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    CK(cudaSetDevice(P->device));
-    if (fmm_status e = kifmm::plan_check_device_error(P)) return e;
-    const bool dq = is_device_pointer(charges), dp = is_device_pointer(potentials);
-    fmm_status s = ensure_workspace(P, nrhs);
-    if (s != FMM_OK) return s;
-    s = ensure_split(P, nrhs);
-    if (s != FMM_OK) return s;
-    const size_t nq = (size_t)P->rows * nrhs;
-    const float *dq_ptr = charges;
-    double *dp_ptr = potentials;
-    if (!dq) {
-        if (!P->charges_stage) CK(cudaMalloc((void **)&P->charges_stage, (size_t)P->rows * P->nrhs_cap * sizeof(float)));
-        CK(cudaMemcpyAsync(P->charges_stage, charges, nq * sizeof(float), cudaMemcpyHostToDevice, st));
-        dq_ptr = P->charges_stage;
-    }
-    if (!dp) {
-        if (!P->pot_stage) CK(cudaMalloc((void **)&P->pot_stage, (size_t)P->rows * P->nrhs_cap * sizeof(double)));
-        dp_ptr = P->pot_stage;
-    }
-    s = run_evaluation(P, dq_ptr, nrhs, dp_ptr, st);
-    if (s != FMM_OK) return s;
-    P->last_stream = st;
-    if (!dp) CK(cudaMemcpyAsync(potentials, dp_ptr, nq * sizeof(double), cudaMemcpyDeviceToHost, st));
-    if (!dq || !dp) {
-        CK(cudaStreamSynchronize(st));
-        return kifmm::plan_check_device_error(P);
-    }
-    return FMM_OK;
+    if (!potentials) return fail(FMM_ERR_INVALID_ARG, "NULL charges or potentials");
+    return evaluate_impl(P, charges, nrhs, potentials, nullptr, stream);
+}
+
+fmm_status fmm_evaluate_gradient(fmm_plan_t P, const float *charges, int nrhs,
+                                 double *potentials, double *gradients, void *stream) {
+    if (!gradients) return fail(FMM_ERR_INVALID_ARG, "NULL gradients");
+    return evaluate_impl(P, charges, nrhs, potentials, gradients, stream);
 }
 
 void fmm_destroy(fmm_plan_t plan) { delete plan; }

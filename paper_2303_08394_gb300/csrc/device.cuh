@@ -89,7 +89,10 @@ struct DevWork {
     float *up, *down;           // nodes x nrhs x ns
     float *qhat, *chat;         // nodes x nrhs x kpad
     float *xchk;                // x nodes x nrhs x ns
-    double *pot_user;           // rows x nrhs, caller order
+    double *pot_user;           // rows x nrhs, caller order (may be null when
+                                // grad_user is set)
+    double *grad_user;          // rows x nrhs x 3, caller order: gradient of the
+                                // potential at each target (null: potentials only)
 };
 
 // Batched operator x gathered-vector products (k_vgemm.cu):

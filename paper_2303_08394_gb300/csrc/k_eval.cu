@@ -32,6 +32,11 @@
 // are sources only are not written).  Runs are assigned from the
 // source order alone, so every right-hand side gets bit-identical
 // arithmetic whatever NR it is batched in.
+//
+// Gradient variant (kGrad, one charge column per launch): each pair also
+// adds q (y - x) / r^3 (y the source, x the target), the target-gradient of
+// q / r, into three more Kahan sums; the close-pair correction covers it,
+// and it is scaled by 1 / (4 pi hw^2) (positions are in root units).
 #include "device.cuh"
 
 namespace kifmm {
@@ -46,6 +51,12 @@ constexpr float kFar = 1.0e15f;    // position of padding sources (charge 0)
 // that the work split (and the rounding) is the same for every column.
 constexpr int kTMax = 4;
 // minb: resident blocks per SM the register allocation must allow.
+// sums per target and launch: NR potentials, or potential + gradient
+template <int NR, bool kGrad> struct Sums {
+    static_assert(!kGrad || NR == 1, "gradients are evaluated one column per launch");
+    static constexpr int n = kGrad ? 4 : NR;
+};
+
 // minb: resident blocks per SM the register allocation must allow; the
 // narrow widths (T <= 2, the bulk of the leaves at ncrit ~ 150) fit more.
 template <int NR, int T> struct Cfg {
@@ -129,20 +140,22 @@ __device__ float3 staged_residual(const DevTree &t, const Smem<NR> &sm, int nseg
 // adds q (1/r_accurate - 1/r_fp32), r_accurate from the position residuals
 // (position = hi + lo to about 2^-48 h).  Such blocks are rare, so the
 // common cost is one min per pair.
-template <int NR, int T>
+template <int NR, int T, bool kGrad>
 __device__ __forceinline__ void fix_block(const DevTree &t, const Smem<NR> &sm, int nsegw, int base,
                                        int j, bool self_run, const float3 (&x)[T], int t0,
-                                       int leaf_begin, int nt, float thr2, float (&part)[T][NR]);
+                                       int leaf_begin, int nt, float thr2,
+                                       float (&part)[T][Sums<NR, kGrad>::n]);
 
 // Staged sources j = a + 2u + h (j < e; a and e multiples of 16) against
 // this lane's T targets; h is the lane's half-warp.
 // t0: index of the lane's first target among B's points (target i is
 // t0 + 16 i); B's own points are staged first, in order, so in the self run
 // a target meets itself at staged index t0 + 16 i.
-template <int NR, int T, bool kSelf>
+template <int NR, int T, bool kSelf, bool kGrad>
 __device__ __forceinline__ void run(const DevTree &t, const Smem<NR> &sm, int nsegw, int base,
                                     int a, int e, int h, const float3 (&x)[T], int t0,
-                                    int leaf_begin, int nt, float thr2, float (&part)[T][NR]) {
+                                    int leaf_begin, int nt, float thr2,
+                                    float (&part)[T][Sums<NR, kGrad>::n]) {
     const float4 *spos = sm.u.st.spos;
     const float *sq = sm.u.st.sq;
     for (int j = a + h; j < e; j += 16) {
@@ -161,12 +174,21 @@ __device__ __forceinline__ void run(const DevTree &t, const Smem<NR> &sm, int ns
                 float r2, inv;
                 pair_terms<kSelf>(p, x[i], r2, inv);
                 if (!kSelf || base + j + 2 * u != t0 + 16 * i) r2min = fminf(r2min, r2);
+                if constexpr (kGrad) {
+                    const float w3 = q[0] * (inv * inv * inv);
+                    part[i][0] = fmaf(q[0], inv, part[i][0]);
+                    part[i][1] = fmaf(w3, p.x - x[i].x, part[i][1]);
+                    part[i][2] = fmaf(w3, p.y - x[i].y, part[i][2]);
+                    part[i][3] = fmaf(w3, p.z - x[i].z, part[i][3]);
+                } else {
 #pragma unroll
-                for (int r = 0; r < NR; ++r) part[i][r] = fmaf(q[r], inv, part[i][r]);
+                    for (int r = 0; r < NR; ++r) part[i][r] = fmaf(q[r], inv, part[i][r]);
+                }
             }
         }
         if (__any_sync(0xffffffffu, r2min < thr2))
-            fix_block<NR, T>(t, sm, nsegw, base, j, kSelf, x, t0, leaf_begin, nt, thr2, part);
+            fix_block<NR, T, kGrad>(t, sm, nsegw, base, j, kSelf, x, t0, leaf_begin, nt, thr2,
+                                    part);
     }
 }
 
@@ -177,7 +199,7 @@ template <int NR> struct Smem {
             float sq[NR > 1 ? Cfg<NR, 1>::cap * NR : 4];
         } st;
         // partial sums of the source slices (used after the last round)
-        float2 red[kWarps][kTMax * NR][16];
+        float2 red[kWarps][kTMax * (NR > 4 ? NR : 4)][16];
     } u;
     float4 seg_off[kSegCap];  // centre offset, surface radius
     int seg_node[kSegCap], seg_kind[kSegCap], seg_start[kSegCap + 1];
@@ -204,10 +226,11 @@ __device__ float3 staged_residual(const DevTree &t, const Smem<NR> &sm, int nseg
     return make_float3(ex + pl.x, ey + pl.y, ez + pl.z);
 }
 
-template <int NR, int T>
+template <int NR, int T, bool kGrad>
 __device__ __forceinline__ void fix_block(const DevTree &t, const Smem<NR> &sm, int nsegw, int base,
                                        int j, bool self_run, const float3 (&x)[T], int t0,
-                                       int leaf_begin, int nt, float thr2, float (&part)[T][NR]) {
+                                       int leaf_begin, int nt, float thr2,
+                                       float (&part)[T][Sums<NR, kGrad>::n]) {
     float3 xl[T];  // the targets' residuals
 #pragma unroll
     for (int i = 0; i < T; ++i) {
@@ -247,16 +270,28 @@ __device__ __forceinline__ void fix_block(const DevTree &t, const Smem<NR> &sm, 
             const float dy = (p.y - x[i].y) + (pl.y - xl[i].y);
             const float dz = (p.z - x[i].z) + (pl.z - xl[i].z);
             const float r2a = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float d = (r2a > 0.f ? KIFMM_RSQRT(r2a) : 0.f) - inv[i];
+            const float ia = r2a > 0.f ? KIFMM_RSQRT(r2a) : 0.f;
+            const float d = ia - inv[i];
+            if constexpr (kGrad) {
+                // replace the main loop's FP32 term w3 (p - x) by the accurate one
+                part[i][0] = fmaf(q[0], d, part[i][0]);
+                const float w3 = q[0] * (inv[i] * inv[i] * inv[i]);
+                const float wa = q[0] * (ia * ia * ia);
+                part[i][1] = fmaf(wa, dx, fmaf(-w3, p.x - x[i].x, part[i][1]));
+                part[i][2] = fmaf(wa, dy, fmaf(-w3, p.y - x[i].y, part[i][2]));
+                part[i][3] = fmaf(wa, dz, fmaf(-w3, p.z - x[i].z, part[i][3]));
+            } else {
 #pragma unroll
-            for (int r = 0; r < NR; ++r) part[i][r] = fmaf(q[r], d, part[i][r]);
+                for (int r = 0; r < NR; ++r) part[i][r] = fmaf(q[r], d, part[i][r]);
+            }
         }
     }
 }
 
-template <int NR, int T>
+template <int NR, int T, bool kGrad>
 __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const DevWork &w, int r0,
                                      Smem<NR> &sm, int b, int2 rb, int nt) {
+    constexpr int NQ = Sums<NR, kGrad>::n;
     constexpr int CAP = Cfg<NR, T>::cap;
     static_assert(CAP % (64 * kWarps) == 0, "rounds must hold whole runs for every slicing");
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -294,7 +329,7 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
             }
         }
         const float thr2 = (kCloseFrac * gb.w) * (kCloseFrac * gb.w);
-        Kahan acc[T][NR];
+        Kahan acc[T][NQ];
 
         for (int sw = 0; sw < nseg; sw += kSegCap) {
             const int nsegw = min(kSegCap, nseg - sw);
@@ -417,20 +452,20 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
                     for (int j0 = 64 * split; j0 < mp; j0 += 64 * nsplit) {
                         const int j1 = min(j0 + 64, mp);
                         const int js = min(max(self_hi, j0), j1);
-                        float part[T][NR];
+                        float part[T][NQ];
 #pragma unroll
                         for (int i = 0; i < T; ++i)
 #pragma unroll
-                            for (int r = 0; r < NR; ++r) part[i][r] = 0.f;
+                            for (int r = 0; r < NQ; ++r) part[i][r] = 0.f;
                         if (js > j0)
-                            run<NR, T, true>(t, sm, nsegw, base, j0, js, half, x, t0, rb.x, nt,
-                                             thr2, part);
-                        run<NR, T, false>(t, sm, nsegw, base, js, j1, half, x, t0, rb.x, nt, thr2,
-                                          part);
+                            run<NR, T, true, kGrad>(t, sm, nsegw, base, j0, js, half, x, t0, rb.x,
+                                                    nt, thr2, part);
+                        run<NR, T, false, kGrad>(t, sm, nsegw, base, js, j1, half, x, t0, rb.x, nt,
+                                                 thr2, part);
 #pragma unroll
                         for (int i = 0; i < T; ++i)
 #pragma unroll
-                            for (int r = 0; r < NR; ++r) acc[i][r].add(part[i][r]);
+                            for (int r = 0; r < NQ; ++r) acc[i][r].add(part[i][r]);
                     }
                 }
                 __syncthreads();
@@ -441,7 +476,7 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
 #pragma unroll
         for (int i = 0; i < T; ++i)
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
+            for (int r = 0; r < NQ; ++r) {
                 const float s2 = __shfl_down_sync(0xffffffffu, acc[i][r].s, 16);
                 const float c2 = __shfl_down_sync(0xffffffffu, acc[i][r].c, 16);
                 if (half == 0) acc[i][r].merge(s2, c2);
@@ -450,8 +485,8 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
 #pragma unroll
             for (int i = 0; i < T; ++i)
 #pragma unroll
-                for (int r = 0; r < NR; ++r)
-                    sm.u.red[wid][i * NR + r][tl] = make_float2(acc[i][r].s, acc[i][r].c);
+                for (int r = 0; r < NQ; ++r)
+                    sm.u.red[wid][i * NQ + r][tl] = make_float2(acc[i][r].s, acc[i][r].c);
         }
         __syncthreads();
         if (split == 0 && active && half == 0) {
@@ -459,8 +494,8 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
 #pragma unroll
                 for (int i = 0; i < T; ++i)
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) {
-                        const float2 v = sm.u.red[s * CW + cw][i * NR + r][tl];
+                    for (int r = 0; r < NQ; ++r) {
+                        const float2 v = sm.u.red[s * CW + cw][i * NQ + r][tl];
                         acc[i][r].merge(v.x, v.y);
                     }
             }
@@ -470,44 +505,68 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
                 if (!valid[i]) continue;
                 const int64_t row = t.oidx[rb.x + chunk * CH + tl + 16 * i];
                 if (row < 0) continue;  // a source only
-                double *out = w.pot_user + (size_t)row * w.nrhs + r0;
+                if constexpr (kGrad) {
+                    if (w.pot_user)
+                        w.pot_user[(size_t)row * w.nrhs + r0] =
+                            ((double)acc[i][0].s - (double)acc[i][0].c) * scale;
+                    // d/dx of 1 / (4 pi hw r_root): 1 / (4 pi hw^2) per root-unit term
+                    const double gscale = scale * scale * (4.0 * 3.14159265358979323846);
+                    double *g = w.grad_user + ((size_t)row * w.nrhs + r0) * 3;
 #pragma unroll
-                for (int r = 0; r < NR; ++r)
-                    out[r] = ((double)acc[i][r].s - (double)acc[i][r].c) * scale;
+                    for (int k = 0; k < 3; ++k)
+                        g[k] = ((double)acc[i][1 + k].s - (double)acc[i][1 + k].c) * gscale;
+                } else {
+                    double *out = w.pot_user + (size_t)row * w.nrhs + r0;
+#pragma unroll
+                    for (int r = 0; r < NR; ++r)
+                        out[r] = ((double)acc[i][r].s - (double)acc[i][r].c) * scale;
+                }
             }
         }
         __syncthreads();
     }
 }
 
-template <int NR, int T>
-__global__ void __launch_bounds__(kThreads, Cfg<NR, T>::minb) k_eval(DevTree t, DevOps o, DevWork w, int r0) {
+template <int NR, int T, bool kGrad>
+struct Occupancy {
+    static constexpr int minb = kGrad ? (T <= 2 ? 5 : (T == 3 ? 4 : 3)) : Cfg<NR, T>::minb;
+};
+
+template <int NR, int T, bool kGrad>
+__global__ void __launch_bounds__(kThreads, (Occupancy<NR, T, kGrad>::minb))
+    k_eval(DevTree t, DevOps o, DevWork w, int r0) {
     __shared__ __align__(16) Smem<NR> sm;
     const int b = t.leaves[t.t_first[T] + blockIdx.x];
     const int2 rb = t.range[b];
     const int nt = rb.y - rb.x;
     if (nt <= 0) return;
-    leaf<NR, T>(t, o, w, r0, sm, b, rb, nt);
+    leaf<NR, T, kGrad>(t, o, w, r0, sm, b, rb, nt);
 }
 
 // one launch per non-empty width group, widest first (longest blocks
 // start first)
-template <int NR>
+template <int NR, bool kGrad = false>
 cudaError_t launch_eval_nr(const DevTree &t, const DevOps &o, const DevWork &w, int r0,
                            cudaStream_t s) {
     static_assert(kTMax == 4, "width groups 1..4");
     const int n4 = t.t_first[3] - t.t_first[4], n3 = t.t_first[2] - t.t_first[3];
     const int n2 = t.t_first[1] - t.t_first[2], n1 = t.t_first[0] - t.t_first[1];
-    if (n4 > 0) k_eval<NR, 4><<<n4, kThreads, 0, s>>>(t, o, w, r0);
-    if (n3 > 0) k_eval<NR, 3><<<n3, kThreads, 0, s>>>(t, o, w, r0);
-    if (n2 > 0) k_eval<NR, 2><<<n2, kThreads, 0, s>>>(t, o, w, r0);
-    if (n1 > 0) k_eval<NR, 1><<<n1, kThreads, 0, s>>>(t, o, w, r0);
+    if (n4 > 0) k_eval<NR, 4, kGrad><<<n4, kThreads, 0, s>>>(t, o, w, r0);
+    if (n3 > 0) k_eval<NR, 3, kGrad><<<n3, kThreads, 0, s>>>(t, o, w, r0);
+    if (n2 > 0) k_eval<NR, 2, kGrad><<<n2, kThreads, 0, s>>>(t, o, w, r0);
+    if (n1 > 0) k_eval<NR, 1, kGrad><<<n1, kThreads, 0, s>>>(t, o, w, r0);
     return cudaGetLastError();
 }
 
 } // namespace
 
 cudaError_t launch_eval(const DevTree &t, const DevOps &o, const DevWork &w, cudaStream_t s) {
+    if (w.grad_user) {
+        // potentials (if w.pot_user) and gradients, one column per launch
+        cudaError_t e = cudaSuccess;
+        for (int r0 = 0; r0 < w.nrhs && e == cudaSuccess; ++r0) e = launch_eval_nr<1, true>(t, o, w, r0, s);
+        return e;
+    }
     int r0 = 0;
     cudaError_t e = cudaSuccess;
     while (r0 < w.nrhs && e == cudaSuccess) {

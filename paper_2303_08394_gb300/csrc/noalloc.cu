@@ -110,7 +110,7 @@ extern "C" fmm_status fmm_evaluate_noalloc(fmm_plan_t plan, const float *charges
     b.ybuf = parts[9];
     b.yp = parts[10];
     b.part = wb.part ? parts[11] : nullptr;
-    fmm_status s = kifmm::plan_enqueue(plan, charges, nrhs, potentials, b,
+    fmm_status s = kifmm::plan_enqueue(plan, charges, nrhs, potentials, nullptr, b,
                                        static_cast<cudaStream_t>(stream));
     return s;  // on failure plan_enqueue has set the message fmm_last_error() returns
 }

@@ -26,8 +26,10 @@ struct WorkspaceBytes {
 };
 
 void plan_workspace_bytes(const fmm_plan_s *P, int nrhs, WorkspaceBytes *out);
+// grad (rows x nrhs x 3, may be null): also write the gradient of the
+// potential at every target; pot may then be null.
 fmm_status plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, double *pot,
-                        const WorkBuffers &b, cudaStream_t st);
+                        double *grad, const WorkBuffers &b, cudaStream_t st);
 int plan_device(const fmm_plan_s *P);
 int plan_m2l_mode(const fmm_plan_s *P);
 // FMM_ERR_TIMEOUT (once) if a device-side bounded wait expired, else FMM_OK.

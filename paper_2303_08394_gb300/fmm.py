@@ -186,6 +186,46 @@ class FMMPlan:
                                      ctypes.c_void_p(st)))
         return out[:, 0] if vec else out
 
+    def evaluate_gradient(self, charges, grad_out=None, out=None, potentials=True, stream=None):
+        """(potentials, gradients) for charges (n,) or (n, nrhs) float32: the
+        gradient of each target's potential with respect to its position,
+        (n, 3) or (n, nrhs, 3) float64 (the field is minus this).  With
+        potentials=False only the gradients are written (the first item is
+        None).  Streams and host/device handling as in evaluate()."""
+        if isinstance(charges, np.ndarray):
+            q = np.ascontiguousarray(charges, dtype=np.float32)
+            vec = q.ndim == 1
+            q = q.reshape(self.n, -1)
+            nrhs = q.shape[1]
+            if grad_out is None:
+                grad_out = np.empty((self.n, nrhs, 3), dtype=np.float64)
+            if potentials and out is None:
+                out = np.empty((self.n, nrhs), dtype=np.float64)
+            st = 0 if stream is None else int(stream)
+            N.check(N.lib().fmm_evaluate_gradient(
+                self._h, q.ctypes.data, nrhs, out.ctypes.data if potentials else None,
+                grad_out.ctypes.data, ctypes.c_void_p(st)))
+        else:
+            import torch
+            q = charges
+            if q.dtype != torch.float32:
+                raise TypeError("charges must be float32")
+            vec = q.dim() == 1
+            q = q.reshape(self.n, -1).contiguous()
+            nrhs = q.shape[1]
+            if grad_out is None:
+                grad_out = torch.empty((self.n, nrhs, 3), dtype=torch.float64, device=q.device)
+            if potentials and out is None:
+                out = torch.empty((self.n, nrhs), dtype=torch.float64, device=q.device)
+            if stream is None:
+                stream = torch.cuda.current_stream(q.device) if q.is_cuda else None
+            st = 0 if stream is None else stream.cuda_stream
+            N.check(N.lib().fmm_evaluate_gradient(
+                self._h, q.data_ptr(), nrhs, out.data_ptr() if potentials else None,
+                grad_out.data_ptr(), ctypes.c_void_p(st)))
+        phi = (out[:, 0] if vec else out) if potentials else None
+        return phi, (grad_out[:, 0, :] if vec else grad_out)
+
     # ---------------------------------------------------------------
     def info(self, key: str) -> int:
         v = ctypes.c_int64()
