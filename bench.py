@@ -205,16 +205,34 @@ def direct_sum_sampled(x, q, idx, block=4):
     return out / (4 * np.pi)
 
 
+def direct_gradient_sampled(x, q, idx, block=4):
+    """FP64 gradient of the direct sum at the sampled targets (numpy)."""
+    import numpy as np
+    out = np.zeros((len(idx), 3))
+    for s in range(0, len(idx), block):
+        t = idx[s:s + block]
+        d = x[None, :, :] - x[t][:, None, :]
+        r = np.sqrt(np.einsum("ijk,ijk->ij", d, d))
+        with np.errstate(divide="ignore"):
+            w3 = np.where(r > 0, 1.0 / r ** 3, 0.0) * q[None, :]
+        out[s:s + block] = np.einsum("ij,ijk->ik", w3, d)
+    return out / (4 * np.pi)
+
+
 # ---------------------------------------------------------------------------
-def time_mode(plan, qd, out, flush, stream, steps, warmup, world):
+def time_mode(plan, qd, out, flush, stream, steps, warmup, world, call=None):
     """Warm up, then time `steps` evaluations (CUDA events on `stream`, L2
     flushed before each step outside the events); returns per-step ms, the
-    per-phase ms of every step and the launches of one evaluation."""
+    per-phase ms of every step and the launches of one evaluation.  `call`
+    replaces the evaluation (default: potentials into `out`)."""
     import torch
     import torch.distributed as dist
+    if call is None:
+        def call():
+            plan.evaluate(qd, out=out, stream=stream)
     with torch.cuda.stream(stream):
         for _ in range(warmup):
-            plan.evaluate(qd, out=out, stream=stream)
+            call()
     torch.cuda.synchronize()
     launches = plan.info("last_launches")
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -227,7 +245,7 @@ def time_mode(plan, qd, out, flush, stream, steps, warmup, world):
         for i in range(steps):
             flush.fill_(float(i))
             starts[i].record(stream)
-            plan.evaluate(qd, out=out, stream=stream)
+            call()
             ends[i].record(stream)
             phases.append(plan.phase_ms())
     torch.cuda.synchronize()
@@ -325,6 +343,26 @@ def main():
         fp32["mixed_over_fp32"] = value / fp32["value"]
         plan.set_m2l_mode(modes[a.m2l])
 
+    # gradients of the potentials (fmm_evaluate_gradient), same protocol, the
+    # gradients only
+    gradient = None
+    if not a.quick and w.nrhs == 1:
+        gout = torch.empty((w.n, 1, 3), dtype=torch.float64, device=dev)
+        g_steps = min(a.steps, 100)
+        g_ms, g_ph, g_launch = time_mode(
+            plan, qd, out, flush, stream, g_steps, a.warmup, world,
+            call=lambda: plan.evaluate_gradient(qd, grad_out=gout, potentials=False,
+                                                stream=stream))
+        g_tot = max_over_ranks(sum(g_ms), world, dev)
+        gradient = {"value": job_value(w.n, g_steps, world, g_tot / 1e3), "unit": UNIT,
+                    "ms_per_step": g_tot / g_steps, "steps": g_steps,
+                    "phase_ms": {k: statistics.mean(ph[k] for ph in g_ph) for k in g_ph[0]},
+                    "gpu_launches": g_launch * g_steps}
+        if idx is not None:
+            got = gout.cpu().numpy()[idx, 0, :]
+            gref = direct_gradient_sampled(x, q[:, 0], idx)
+            gradient["rel_l2_err"] = float(np.linalg.norm(got - gref) / np.linalg.norm(gref))
+
     # rooflines from the library's per-phase CUDA events (each phase below is
     # one kernel launch on `stream`)
     peaks, peak_src = load_peaks()
@@ -368,6 +406,18 @@ def main():
                          "uncounted; one leaf pass = one launch per leaf width group (T = 1..4 "
                          "targets per lane), timed and counted together"}
     dominant = m2l_roof if m2l_ms >= leaf_ms else leaf_roof
+    if gradient is not None:
+        # potential + gradient: 8 (r^2, as above) + 2 (potential) + 3 (q / r^3)
+        # + 6 (three FMAs) flops per near-field pair
+        g_leaf = gradient["phase_ms"]["leaf"]
+        g_flops = 19.0 * p2p_pairs
+        g_tf = g_flops / (g_leaf / 1e3) / 1e12
+        gradient["roofline"] = {"kernel": "k_eval (gradient variant)", "bound": "alu",
+                                "achieved": g_tf, "peak": fp32_peak, "unit": "TFLOP/s",
+                                "frac": g_tf / fp32_peak, "traffic": None,
+                                "flops_per_launch": g_flops, "ms_per_launch": g_leaf,
+                                "note": "near-field pair flops only (19 per pair); one leaf "
+                                        "pass = one launch per leaf width group"}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -382,7 +432,7 @@ def main():
                 "dtype": "f32" if a.m2l == "fp32" else f"f32 (M2L {a.m2l} split on tensor cores)",
                 "data": "synthetic", "config": config,
                 "rel_l2_err": err, "error_gate_1e-5": (err is not None and err <= 1e-5),
-                "fp32": fp32,
+                "fp32": fp32, "gradient": gradient,
                 "roofline": dominant, "rooflines": {"m2l": m2l_roof, "leaf": leaf_roof},
                 "phase_ms": {k2: statistics.mean(ph[k2] for ph in phases) for k2 in phases[0]},
                 "e2e": e2e,
