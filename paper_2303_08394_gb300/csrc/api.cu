@@ -96,6 +96,11 @@ struct fmm_plan_s {
     float *qh_hi = nullptr, *qh_lo = nullptr;   // split qhat (4-byte slots)
     int qh_cap = 0;                             // nrhs the split buffers hold
     int *err_host = nullptr, *err_dev = nullptr;  // mapped pinned error word
+    // side stream of the upward pass: each level's M2L projection (qhat =
+    // Vk^T rho, needed only by the M2L) runs there while the next level's
+    // M2M proceeds; joined before the M2L
+    cudaStream_t s_side = nullptr;
+    cudaEvent_t ev_side[2] = {nullptr, nullptr};
     // Autotuner: tile shape per level-product call site (in enqueue order),
     // chosen by timing every shape during the first evaluation of each nrhs;
     // forced_shape >= 0 applies one shape everywhere instead.
@@ -133,6 +138,9 @@ struct fmm_plan_s {
         if (qh_lo) cudaFree(qh_lo);
         if (err_host) cudaFreeHost(err_host);
         drop_graph();
+        for (auto &e : ev_side)
+            if (e) cudaEventDestroy(e);
+        if (s_side) cudaStreamDestroy(s_side);
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
         for (auto &e : tune_ev)
@@ -499,6 +507,8 @@ fmm_status upload_plan(fmm_plan_s *P) {
         for (auto &e : P->ev) CK(cudaEventCreate(&e));
     for (auto &e : P->tune_ev) CK(cudaEventCreate(&e));
     CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
+    CK(cudaStreamCreateWithFlags(&P->s_side, cudaStreamNonBlocking));
+    for (auto &e : P->ev_side) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     CK(cudaHostAlloc((void **)&P->err_host, sizeof(int), cudaHostAllocMapped));
     *P->err_host = 0;
     CK(cudaHostGetDevicePointer((void **)&P->err_dev, P->err_host, 0));
@@ -667,7 +677,7 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
         P->gemm_shape.clear();
         P->gemm_ms.clear();
     }
-    auto gemm = [&](VGemm &g) -> fmm_status {
+    auto gemm = [&](VGemm &g, cudaStream_t gs) -> fmm_status {
         g.nrhs = nrhs;
         const int my = site++;
         if (g.count > 0) {
@@ -683,9 +693,9 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
             for (int sh = 0; sh < kGemmShapes && g.count > 0; ++sh) {
                 float ms = 0.f;
                 for (int rep = 0; rep < 2; ++rep) {
-                    CK(cudaEventRecord(P->tune_ev[0], st));
-                    CK(launch_vgemm(g, st, sh));
-                    CK(cudaEventRecord(P->tune_ev[1], st));
+                    CK(cudaEventRecord(P->tune_ev[0], gs));
+                    CK(launch_vgemm(g, gs, sh));
+                    CK(cudaEventRecord(P->tune_ev[1], gs));
                     CK(cudaEventSynchronize(P->tune_ev[1]));
                     CK(cudaEventElapsedTime(&ms, P->tune_ev[0], P->tune_ev[1]));
                 }
@@ -696,12 +706,12 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
             }
             P->gemm_shape.push_back(best);
             P->gemm_ms.push_back(best_ms);
-            CK(launch_vgemm(g, st, best));
+            CK(launch_vgemm(g, gs, best));
             return FMM_OK;
         }
         const int shape = P->forced_shape >= 0 ? P->forced_shape
                           : my < (int)P->gemm_shape.size() ? P->gemm_shape[my] : 0;
-        CK(launch_vgemm(g, st, shape));
+        CK(launch_vgemm(g, gs, shape));
         return FMM_OK;
     };
     auto seg = [](const float *AT, int n, const float *src, int src_ld, const int *idx, int base) {
@@ -714,6 +724,9 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
         s.src_base = base;
         return s;
     };
+    // side stream for the projections (not while tuning: timed one by one)
+    const bool side = P->s_side && !P->tuning;
+    bool side_used = false;
     // rho = Pv y (y already divided by Ps), written to up[node]; then the
     // M2L projection qhat[node] = Vk^T rho
     auto finish_up = [&](const int *nodes, int count) -> fmm_status {
@@ -725,7 +738,7 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
         g.dst = b.up;
         g.dst_ld = nsp;
         g.dst_idx = nodes;
-        if (fmm_status e = gemm(g)) return e;
+        if (fmm_status e = gemm(g, st)) return e;
         VGemm h{};
         h.m = kp;
         h.count = count;
@@ -734,7 +747,13 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
         h.dst = b.qhat;
         h.dst_ld = kp;
         h.dst_idx = nodes;
-        return gemm(h);
+        if (!side) return gemm(h, st);
+        // reads this level's rho, writes its qhat rows: nothing the rest of
+        // the upward pass touches
+        CK(cudaEventRecord(P->ev_side[0], st));
+        CK(cudaStreamWaitEvent(P->s_side, P->ev_side[0], 0));
+        side_used = true;
+        return gemm(h, P->s_side);
     };
     if (t.depth >= 2) {
         // P2M: check potentials, y = Pu^T chk / Ps, rho, qhat
@@ -750,7 +769,7 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
             g.scale = o.Ps_inv;
             g.dst = b.ybuf;
             g.dst_ld = rPp;
-            if (fmm_status e = gemm(g)) return e;
+            if (fmm_status e = gemm(g, st)) return e;
             if (fmm_status e = finish_up(P->d_p2m, np)) return e;
         }
         // M2M, bottom-up: y = sum_sigma M2M_sigma up[child_sigma] / Ps
@@ -770,9 +789,13 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
             g.dst = b.ybuf;
             g.dst_ld = rPp;
             g.part = b.part;
-            if (fmm_status e = gemm(g)) return e;
+            if (fmm_status e = gemm(g, st)) return e;
             if (fmm_status e = finish_up(P->d_m2m + a0, cnt)) return e;
         }
+    }
+    if (side_used) {
+        CK(cudaEventRecord(P->ev_side[1], P->s_side));
+        CK(cudaStreamWaitEvent(st, P->ev_side[1], 0));
     }
     if (P->timing) CK(record_phase(P->ev[1], st));
     if (t.depth >= 2 && P->dm.ntiles > 0) {
@@ -809,7 +832,7 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
                 g.seg[0] = seg(o.L2L, ns, b.down, nsp, P->d_m2m + a0, 0);
                 g.dst = b.yp;
                 g.dst_ld = 8 * rQ;
-                if (fmm_status e = gemm(g)) return e;
+                if (fmm_status e = gemm(g, st)) return e;
             }
             // y = ((Qu^T Uk) chat + Qu^T xchk) / Qs + L2L part
             VGemm g{};
@@ -830,7 +853,7 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
             }
             g.dst = b.ybuf;
             g.dst_ld = rQp;
-            if (fmm_status e = gemm(g)) return e;
+            if (fmm_status e = gemm(g, st)) return e;
             // rho = Qv y -> down[node]
             VGemm h{};
             h.m = ns;
@@ -840,7 +863,7 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
             h.dst = b.down;
             h.dst_ld = nsp;
             h.dst_base = b0;
-            if (fmm_status e = gemm(h)) return e;
+            if (fmm_status e = gemm(h, st)) return e;
         }
     }
     if (P->timing) CK(record_phase(P->ev[3], st));
