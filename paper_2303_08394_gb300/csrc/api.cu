@@ -814,7 +814,8 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
     }
     if (P->timing) CK(record_phase(P->ev[2], st));
     if (t.depth >= 2) {
-        if (!sc.x_nodes.empty()) ++launches;
+        if (!sc.x_nodes.empty())  // one launch per charge-column group of 8, 4, 2, 1
+            launches += nrhs / 8 + ((nrhs % 8) >> 2) + ((nrhs % 4) >> 1) + (nrhs % 2);
         CK(launch_p2l(P->dt, o, w, P->d_xnodes, (int)sc.x_nodes.size(), st));
         const int total = (int)sc.m2m_nodes.size();
         (void)total;

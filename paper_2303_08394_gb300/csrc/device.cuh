@@ -165,8 +165,6 @@ cudaError_t launch_m2l_tc(const DevM2L &m, const DevOps &o, const DevWork &w, in
                           bool tf32, const CUtensorMap &s_hi, const CUtensorMap &s_lo,
                           void *qh_hi, void *qh_lo, int *err, int num_sms, cudaStream_t st);
 
-// Right-hand sides handled per block by the point-evaluation kernels.
-constexpr int kMaxRhs = 16;
 // Nodes per down-pass chunk (chunks never mix child positions).
 constexpr int kDownChunk = 32;
 

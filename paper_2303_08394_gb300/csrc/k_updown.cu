@@ -50,56 +50,70 @@ __global__ void __launch_bounds__(128) k_p2m_check(DevTree t, DevOps o, DevWork 
 }
 
 // P2L: downward check potential of box B (radius ai, normalised by h_B)
-// from the points of every leaf in X(B).
-__global__ void __launch_bounds__(128) k_p2l(DevTree t, DevOps o, DevWork w, const int *nodes,
-                                             int nr) {
-    __shared__ float4 spos[128];
-    __shared__ float sq[kMaxRhs][128];
+// from the points of every leaf in X(B), for NR right-hand sides from r0.
+// One block per box and one thread per check point (the block is ns rounded
+// up to a warp); the X leaves' points are staged in shared memory in chunks
+// of the block size, shifted into B's frame (charges in the w slot when NR
+// is 1).  Each check point sums its sources in order.  No pair coincides:
+// an X(B) leaf does not touch B, so it lies at least one B-width from it,
+// and the check surface reaches only 0.05 h_B beyond B.
+template <int NR>
+__global__ void __launch_bounds__(512) k_p2l(DevTree t, DevOps o, DevWork w, const int *nodes,
+                                             int r0) {
+    extern __shared__ float4 p2l_smem[];
+    float4 *spos = p2l_smem;                                     // blockDim
+    float *sq = reinterpret_cast<float *>(spos + blockDim.x);    // blockDim x NR (NR > 1)
     const int b = nodes[blockIdx.x];
-    const int r0 = blockIdx.y * nr;
-    const int nrr = min(nr, w.nrhs - r0);
     const float4 gb = t.geom[b];
     const float inv_h = 1.f / gb.w;
     const int ns = o.ns, nsp = (o.ns + 3) & ~3;
     const int slot = t.x_slot[b];
-    for (int j0 = 0; j0 < ns; j0 += blockDim.x) {
-        const int j = j0 + threadIdx.x;
-        const float4 s = o.surf[min(j, ns - 1)];
-        const float cx = o.ai * s.x, cy = o.ai * s.y, cz = o.ai * s.z;
-        float acc[kMaxRhs];
+    const int j = threadIdx.x;
+    const float4 s = o.surf[min(j, ns - 1)];
+    const float cx = o.ai * s.x, cy = o.ai * s.y, cz = o.ai * s.z;
+    float acc[NR];
 #pragma unroll
-        for (int r = 0; r < kMaxRhs; ++r) acc[r] = 0.f;
-        for (int e = t.x_ptr[b]; e < t.x_ptr[b + 1]; ++e) {
-            const int a = t.x_idx[e];
-            const float4 ga = t.geom[a];
-            const float sx = (ga.x - gb.x) * inv_h, sy = (ga.y - gb.y) * inv_h,
-                        sz = (ga.z - gb.z) * inv_h;
-            const int2 rg = t.range[a];
-            for (int i0 = rg.x; i0 < rg.y; i0 += blockDim.x) {
-                __syncthreads();
-                const int i = i0 + threadIdx.x;
-                if (i < rg.y) {
-                    const float4 p = t.pts[i];
-                    spos[threadIdx.x] = make_float4(p.x * inv_h + sx, p.y * inv_h + sy,
-                                                    p.z * inv_h + sz, 0.f);
-                    for (int r = 0; r < nrr; ++r)
-                        sq[r][threadIdx.x] = w.qs[(size_t)i * w.nrhs + r0 + r];
+    for (int r = 0; r < NR; ++r) acc[r] = 0.f;
+    for (int e = t.x_ptr[b]; e < t.x_ptr[b + 1]; ++e) {
+        const int a = t.x_idx[e];
+        const float4 ga = t.geom[a];
+        const float sx = (ga.x - gb.x) * inv_h, sy = (ga.y - gb.y) * inv_h,
+                    sz = (ga.z - gb.z) * inv_h;
+        const int2 rg = t.range[a];
+        for (int i0 = rg.x; i0 < rg.y; i0 += blockDim.x) {
+            __syncthreads();
+            const int i = i0 + threadIdx.x;
+            if (i < rg.y) {
+                const float4 p = t.pts[i];
+                float4 v = make_float4(p.x * inv_h + sx, p.y * inv_h + sy, p.z * inv_h + sz, 0.f);
+                const float *qi = w.qs + (size_t)i * w.nrhs + r0;
+                if constexpr (NR == 1) {
+                    v.w = qi[0];
+                } else {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) sq[threadIdx.x * NR + r] = qi[r];
                 }
-                __syncthreads();
-                const int cnt = min((int)blockDim.x, rg.y - i0);
-                for (int c = 0; c < cnt; ++c) {
-                    const float dx = cx - spos[c].x, dy = cy - spos[c].y, dz = cz - spos[c].z;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    const float inv = r2 > 0.f ? KIFMM_RSQRT(r2) : 0.f;
+                spos[threadIdx.x] = v;
+            }
+            __syncthreads();
+            const int cnt = min((int)blockDim.x, rg.y - i0);
+            for (int c = 0; c < cnt; ++c) {
+                const float4 v = spos[c];
+                const float dx = cx - v.x, dy = cy - v.y, dz = cz - v.z;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                const float inv = KIFMM_RSQRT(r2);
+                if constexpr (NR == 1) {
+                    acc[0] = fmaf(v.w, inv, acc[0]);
+                } else {
 #pragma unroll
-                    for (int r = 0; r < kMaxRhs; ++r)
-                        if (r < nrr) acc[r] = fmaf(sq[r][c], inv, acc[r]);
+                    for (int r = 0; r < NR; ++r) acc[r] = fmaf(sq[c * NR + r], inv, acc[r]);
                 }
             }
         }
-        if (j < ns)
-            for (int r = 0; r < nrr; ++r)
-                w.xchk[((size_t)slot * w.nrhs + r0 + r) * nsp + j] = acc[r];
+    }
+    if (j < ns) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) w.xchk[((size_t)slot * w.nrhs + r0 + r) * nsp + j] = acc[r];
     }
 }
 
@@ -112,8 +126,6 @@ __global__ void k_gather_charges(DevTree t, DevWork w) {
         w.qs[idx] = c >= 0 ? w.charges_user[c * w.nrhs + r] : 0.f;
     }
 }
-
-inline int rhs_chunk(int nrhs) { return nrhs < kMaxRhs ? nrhs : kMaxRhs; }
 
 } // namespace
 
@@ -152,10 +164,21 @@ cudaError_t launch_p2m_check(const DevTree &t, const DevOps &o, const DevWork &w
 cudaError_t launch_p2l(const DevTree &t, const DevOps &o, const DevWork &w, const int *nodes,
                        int count, cudaStream_t s) {
     if (count == 0) return cudaSuccess;
-    const int nr = rhs_chunk(w.nrhs);
-    const dim3 grid(count, (w.nrhs + nr - 1) / nr);
-    k_p2l<<<grid, 128, 0, s>>>(t, o, w, nodes, nr);
-    return cudaGetLastError();
+    const int threads = (o.ns + 31) & ~31;
+    if (threads > 512) return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    for (int r0 = 0; r0 < w.nrhs && e == cudaSuccess;) {
+        const int left = w.nrhs - r0;
+        const int nr = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        const size_t smem = (size_t)threads * 16 + (nr > 1 ? (size_t)threads * nr * 4 : 0);
+        if (nr == 8) k_p2l<8><<<count, threads, smem, s>>>(t, o, w, nodes, r0);
+        else if (nr == 4) k_p2l<4><<<count, threads, smem, s>>>(t, o, w, nodes, r0);
+        else if (nr == 2) k_p2l<2><<<count, threads, smem, s>>>(t, o, w, nodes, r0);
+        else k_p2l<1><<<count, threads, smem, s>>>(t, o, w, nodes, r0);
+        e = cudaGetLastError();
+        r0 += nr;
+    }
+    return e;
 }
 
 } // namespace kifmm
