@@ -42,6 +42,8 @@ TRAFFIC = {
     ("k_m2l_tc", "cube_n1e6_p6_ncrit150", "bf16x3", 128): 78.9e6,
     # the leaf pass: its four width-group launches together
     ("k_eval", "cube_n1e6_p6_ncrit150", "bf16x3", None): 90.6e6,
+    # the gradient variant (profiles/k_eval_gradient_cube_n1e6_p6.md)
+    ("k_eval_grad", "cube_n1e6_p6_ncrit150", "bf16x3", None): 117.1e6,
     ("k_eval", "cube_n1e6_p6_ncrit150", "fp32", None): 90.6e6,
     ("k_eval", "cube_n1e6_p6_ncrit150", "tf32x3", None): 90.6e6,
 }
@@ -414,7 +416,8 @@ def main():
         g_tf = g_flops / (g_leaf / 1e3) / 1e12
         gradient["roofline"] = {"kernel": "k_eval (gradient variant)", "bound": "alu",
                                 "achieved": g_tf, "peak": fp32_peak, "unit": "TFLOP/s",
-                                "frac": g_tf / fp32_peak, "traffic": None,
+                                "frac": g_tf / fp32_peak,
+                                "traffic": TRAFFIC.get(("k_eval_grad", w.name, a.m2l, None)),
                                 "flops_per_launch": g_flops, "ms_per_launch": g_leaf,
                                 "note": "near-field pair flops only (19 per pair); one leaf "
                                         "pass = one launch per leaf width group"}
