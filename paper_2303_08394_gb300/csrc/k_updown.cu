@@ -14,38 +14,65 @@ namespace kifmm {
 
 namespace {
 
-// Upward check potential of leaf `pos` at check point j for NR right-hand
-// sides from r0: thread per (leaf, j); the leaf's points are read as
-// warp-wide broadcasts.
+// Upward check potential of leaf nodes[pos] at its ns check points for NR
+// right-hand sides from r0: one block per leaf, one thread per check point
+// (the block is ns rounded up to a warp).  The leaf's points are staged in
+// shared memory, scaled to leaf units (an exact power-of-two scaling), with
+// the charge in the w slot when NR is 1; each check point sums them in
+// order.
 template <int NR>
-__global__ void __launch_bounds__(128) k_p2m_check(DevTree t, DevOps o, DevWork w,
+__global__ void __launch_bounds__(512) k_p2m_check(DevTree t, DevOps o, DevWork w,
                                                    const int *nodes, int count, float *chk,
                                                    int ld, int r0) {
+    extern __shared__ float4 p2m_smem[];
+    float4 *spos = p2m_smem;                                     // blockDim
+    float *sq = reinterpret_cast<float *>(spos + blockDim.x);    // blockDim x NR (NR > 1)
     const int ns = o.ns;
-    const int64_t total = (int64_t)count * ns;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int pos = (int)(idx / ns), j = (int)(idx - (int64_t)pos * ns);
+    const int j = threadIdx.x;
+    const float4 s = o.surf[min(j, ns - 1)];
+    const float cx = o.ao * s.x, cy = o.ao * s.y, cz = o.ao * s.z;
+    for (int pos = blockIdx.x; pos < count; pos += gridDim.x) {
         const int node = nodes[pos];
         const float inv_h = 1.f / t.geom[node].w;
         const int2 rg = t.range[node];
-        const float4 s = o.surf[j];
-        const float cx = o.ao * s.x, cy = o.ao * s.y, cz = o.ao * s.z;
         float acc[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) acc[r] = 0.f;
+        for (int i0 = rg.x; i0 < rg.y; i0 += blockDim.x) {
+            __syncthreads();
+            const int i = i0 + threadIdx.x;
+            if (i < rg.y) {
+                const float4 p = __ldg(t.pts + i);
+                float4 v = make_float4(p.x * inv_h, p.y * inv_h, p.z * inv_h, 0.f);
+                const float *qi = w.qs + (size_t)i * w.nrhs + r0;
+                if constexpr (NR == 1) {
+                    v.w = __ldg(qi);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) sq[threadIdx.x * NR + r] = __ldg(qi + r);
+                }
+                spos[threadIdx.x] = v;
+            }
+            __syncthreads();
+            const int cnt = min((int)blockDim.x, rg.y - i0);
 #pragma unroll 4
-        for (int i = rg.x; i < rg.y; ++i) {
-            const float4 p = __ldg(t.pts + i);
-            const float dx = cx - p.x * inv_h, dy = cy - p.y * inv_h, dz = cz - p.z * inv_h;
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            const float inv = r2 > 0.f ? KIFMM_RSQRT(r2) : 0.f;
-            const float *q = w.qs + (size_t)i * w.nrhs + r0;
+            for (int c = 0; c < cnt; ++c) {
+                const float4 v = spos[c];
+                const float dx = cx - v.x, dy = cy - v.y, dz = cz - v.z;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                const float inv = r2 > 0.f ? KIFMM_RSQRT(r2) : 0.f;
+                if constexpr (NR == 1) {
+                    acc[0] = fmaf(v.w, inv, acc[0]);
+                } else {
 #pragma unroll
-            for (int r = 0; r < NR; ++r) acc[r] = fmaf(__ldg(q + r), inv, acc[r]);
+                    for (int r = 0; r < NR; ++r) acc[r] = fmaf(sq[c * NR + r], inv, acc[r]);
+                }
+            }
         }
+        if (j < ns) {
 #pragma unroll
-        for (int r = 0; r < NR; ++r) chk[((size_t)pos * w.nrhs + r0 + r) * ld + j] = acc[r];
+            for (int r = 0; r < NR; ++r) chk[((size_t)pos * w.nrhs + r0 + r) * ld + j] = acc[r];
+        }
     }
 }
 
@@ -141,9 +168,11 @@ cudaError_t launch_gather_charges(const DevTree &t, const DevWork &w, cudaStream
 template <int NR>
 cudaError_t p2m_check_nr(const DevTree &t, const DevOps &o, const DevWork &w, const int *nodes,
                          int count, float *chk, int ld, int r0, cudaStream_t s) {
-    const int64_t total = (int64_t)count * o.ns;
-    const int blocks = (int)std::min<int64_t>((total + 127) / 128, 152 * 32);
-    k_p2m_check<NR><<<blocks, 128, 0, s>>>(t, o, w, nodes, count, chk, ld, r0);
+    const int threads = (o.ns + 31) & ~31;
+    if (threads > 512) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)threads * 16 + (NR > 1 ? (size_t)threads * NR * 4 : 0);
+    const int blocks = count < 152 * 64 ? count : 152 * 64;
+    k_p2m_check<NR><<<blocks, threads, smem, s>>>(t, o, w, nodes, count, chk, ld, r0);
     return cudaGetLastError();
 }
 
