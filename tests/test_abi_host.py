@@ -244,3 +244,22 @@ def test_single_point_and_duplicates():
     x = np.zeros((40, 3))
     P = FMMPlan(x, 4, 8, host_only=1, max_level=5)
     assert P.info("depth") == 5
+
+
+def test_gradient_entry_point_arguments():
+    """fmm_evaluate_gradient refuses NULL gradients and host-only plans with
+    status codes (no GPU needed)."""
+    x, q = wl.uniform_cube(200, 4)
+    P = FMMPlan(x, 4, 32, host_only=1)
+    L = N.lib()
+    qf = np.ascontiguousarray(q[:, 0], dtype=np.float32)
+    g = np.zeros((len(x), 1, 3))
+    phi = np.zeros((len(x), 1))
+    assert L.fmm_evaluate_gradient(P._h, qf.ctypes.data, 1, phi.ctypes.data, None,
+                                   None) == N.FMM_ERR_INVALID_ARG
+    assert "gradients" in N.lib().fmm_last_error().decode()
+    assert L.fmm_evaluate_gradient(P._h, qf.ctypes.data, 1, None, g.ctypes.data,
+                                   None) == N.FMM_ERR_INVALID_ARG
+    assert "host-only" in N.lib().fmm_last_error().decode()
+    assert L.fmm_evaluate_gradient(None, qf.ctypes.data, 1, None, g.ctypes.data,
+                                   None) == N.FMM_ERR_INVALID_ARG
