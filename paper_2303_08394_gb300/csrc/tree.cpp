@@ -514,8 +514,11 @@ void merge_forest(const std::vector<Tree> &parts, const std::vector<int64_t> &ro
 
 void build_m2l_table(const Tree &t, M2LTable &m) {
     m = M2LTable();
-    m.tile_entry_ptr.push_back(0);
-    for (int l = 2; l <= t.depth; ++l) {
+    // targets of every (level, parity class) in node order; tiles of
+    // kTileRows consecutive targets of one class
+    std::vector<std::vector<int32_t>> lists;
+    std::vector<int> list_level;
+    for (int l = 2; l <= t.depth; ++l)
         for (int cls = 0; cls < 8; ++cls) {
             std::vector<int32_t> targets;
             for (int32_t b = t.level_ptr[l]; b < t.level_ptr[l + 1]; ++b) {
@@ -523,31 +526,56 @@ void build_m2l_table(const Tree &t, M2LTable &m) {
                         ((t.key[4 * b + 3] & 1) << 2);
                 if (c == cls && t.v_ptr[b + 1] > t.v_ptr[b]) targets.push_back(b);
             }
-            for (size_t s = 0; s < targets.size(); s += kTileRows) {
-                size_t cnt = std::min<size_t>(kTileRows, targets.size() - s);
-                m.tile_level.push_back(l);
-                size_t tbase = m.tile_target.size();
-                m.tile_target.resize(tbase + kTileRows, -1);
-                std::vector<int32_t> src((size_t)kNumOffsets * kTileRows, -1);
-                std::vector<char> used(kNumOffsets, 0);
-                for (size_t r = 0; r < cnt; ++r) {
-                    int32_t b = targets[s + r];
-                    m.tile_target[tbase + r] = b;
-                    for (int64_t e = t.v_ptr[b]; e < t.v_ptr[b + 1]; ++e) {
-                        int o = t.v_off[e];
-                        src[(size_t)o * kTileRows + r] = t.v_idx[e];
-                        used[o] = 1;
-                    }
+            lists.push_back(std::move(targets));
+            list_level.push_back(l);
+        }
+    std::vector<std::pair<int, size_t>> tiles;  // (list, first target)
+    for (size_t i = 0; i < lists.size(); ++i)
+        for (size_t s0 = 0; s0 < lists[i].size(); s0 += kTileRows) tiles.push_back({(int)i, s0});
+    const int64_t nt = (int64_t)tiles.size();
+    // every tile independently: the offsets its targets use and, per offset,
+    // the source of each row; then concatenated in tile order
+    std::vector<std::vector<int32_t>> t_off(nt), t_src(nt);
+    m.tile_level.resize(nt);
+    m.tile_target.assign((size_t)nt * kTileRows, -1);
+#pragma omp parallel
+    {
+        std::vector<int32_t> src((size_t)kNumOffsets * kTileRows, -1);
+        std::vector<char> used(kNumOffsets, 0);
+#pragma omp for schedule(dynamic, 8)
+        for (int64_t i = 0; i < nt; ++i) {
+            const std::vector<int32_t> &targets = lists[tiles[i].first];
+            const size_t s0 = tiles[i].second;
+            const size_t cnt = std::min<size_t>(kTileRows, targets.size() - s0);
+            m.tile_level[i] = list_level[tiles[i].first];
+            for (size_t r = 0; r < cnt; ++r) {
+                const int32_t b = targets[s0 + r];
+                m.tile_target[(size_t)i * kTileRows + r] = b;
+                for (int64_t e = t.v_ptr[b]; e < t.v_ptr[b + 1]; ++e) {
+                    const int o = t.v_off[e];
+                    src[(size_t)o * kTileRows + r] = t.v_idx[e];
+                    used[o] = 1;
                 }
-                for (int o = 0; o < kNumOffsets; ++o) {
-                    if (!used[o]) continue;
-                    m.entry_offset.push_back(o);
-                    m.entry_src.insert(m.entry_src.end(), src.begin() + (size_t)o * kTileRows,
-                                       src.begin() + (size_t)(o + 1) * kTileRows);
-                }
-                m.tile_entry_ptr.push_back((int32_t)m.entry_offset.size());
+            }
+            for (int o = 0; o < kNumOffsets; ++o) {
+                if (!used[o]) continue;
+                t_off[i].push_back(o);
+                int32_t *row = src.data() + (size_t)o * kTileRows;
+                t_src[i].insert(t_src[i].end(), row, row + kTileRows);
+                std::fill(row, row + kTileRows, -1);
+                used[o] = 0;
             }
         }
+    }
+    size_t ne = 0;
+    for (int64_t i = 0; i < nt; ++i) ne += t_off[i].size();
+    m.entry_offset.reserve(ne);
+    m.entry_src.reserve(ne * kTileRows);
+    m.tile_entry_ptr.push_back(0);
+    for (int64_t i = 0; i < nt; ++i) {
+        m.entry_offset.insert(m.entry_offset.end(), t_off[i].begin(), t_off[i].end());
+        m.entry_src.insert(m.entry_src.end(), t_src[i].begin(), t_src[i].end());
+        m.tile_entry_ptr.push_back((int32_t)m.entry_offset.size());
     }
 }
 
