@@ -295,9 +295,25 @@ enum {
     FMM_ARRAY_OUTPUT_ROW = 18,/* int64 [points]: potential row of each sorted
                                 point, -1 for a source only */
     FMM_ARRAY_NODE_PROBLEM = 19,/* int32 [nodes]: problem of each box */
-    FMM_ARRAY_GEMM_SHAPES = 20 /* int32 [level products]: the tile shape the
+    FMM_ARRAY_GEMM_SHAPES = 20,/* int32 [level products]: the tile shape the
                                 autotuner chose for each, in evaluation order
                                 (empty before the first tuned evaluation) */
+    /* The M2L work table ("M2L" of "Computational structure of FMM
+     * operators": every target box B sums the translated densities of its
+     * V list).  Targets with a non-empty V list are grouped per level and
+     * per parity class (ix&1, iy&1, iz&1), in plan order, into tiles of 128
+     * rows; an entry is one (tile, offset t) pair with the V-list source of
+     * every row that has one at offset t. */
+    FMM_ARRAY_M2L_TILE_LEVEL = 21,    /* int32 [tiles]: level of the tile */
+    FMM_ARRAY_M2L_TILE_TARGET = 22,   /* int32 [tiles][128]: target box of
+                                         each row, -1 past the last */
+    FMM_ARRAY_M2L_TILE_ENTRY_PTR = 23,/* int32 [tiles+1]: CSR offsets of the
+                                         tiles' entries */
+    FMM_ARRAY_M2L_ENTRY_OFFSET = 24,  /* int32 [entries]: offset index t in
+                                         the order of FMM_ARRAY_M2L_S,
+                                         increasing within a tile */
+    FMM_ARRAY_M2L_ENTRY_SRC = 25      /* int32 [entries][128]: source box of
+                                         each row at that offset, -1 none */
 };
 /* Copy array `which` into dst (capacity `bytes`).  *needed receives the
  * size in bytes (may be NULL).  dst == NULL only queries the size. */

@@ -31,7 +31,10 @@ ARRAYS = {"node_keys": (0, "i4"), "node_range": (1, "i8"), "leaf_flag": (2, "i4"
           "w_idx": (9, "i4"), "x_ptr": (10, "i8"), "x_idx": (11, "i4"),
           "surface": (12, "f8"), "m2l_u": (13, "f8"), "m2l_v": (14, "f8"),
           "m2l_s": (15, "f8"), "root": (16, "f8"), "charge_row": (17, "i8"),
-          "output_row": (18, "i8"), "node_problem": (19, "i4"), "gemm_shapes": (20, "i4")}
+          "output_row": (18, "i8"), "node_problem": (19, "i4"), "gemm_shapes": (20, "i4"),
+          "m2l_tile_level": (21, "i4"), "m2l_tile_target": (22, "i4"),
+          "m2l_tile_entry_ptr": (23, "i4"), "m2l_entry_offset": (24, "i4"),
+          "m2l_entry_src": (25, "i4")}
 
 # every symbol include/kifmm.h declares
 EXPORTS = ("fmm_options_init", "fmm_plan_create", "fmm_plan_create_ex",

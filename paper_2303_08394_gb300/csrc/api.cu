@@ -1318,6 +1318,26 @@ fmm_status fmm_plan_get_array(fmm_plan_t P, int which, void *dst, int64_t bytes,
         src = t.node_problem.data();
         size = t.node_problem.size() * 4;
         break;
+    case FMM_ARRAY_M2L_TILE_LEVEL:
+        src = P->m2l.tile_level.data();
+        size = P->m2l.tile_level.size() * 4;
+        break;
+    case FMM_ARRAY_M2L_TILE_TARGET:
+        src = P->m2l.tile_target.data();
+        size = P->m2l.tile_target.size() * 4;
+        break;
+    case FMM_ARRAY_M2L_TILE_ENTRY_PTR:
+        src = P->m2l.tile_entry_ptr.data();
+        size = P->m2l.tile_entry_ptr.size() * 4;
+        break;
+    case FMM_ARRAY_M2L_ENTRY_OFFSET:
+        src = P->m2l.entry_offset.data();
+        size = P->m2l.entry_offset.size() * 4;
+        break;
+    case FMM_ARRAY_M2L_ENTRY_SRC:
+        src = P->m2l.entry_src.data();
+        size = P->m2l.entry_src.size() * 4;
+        break;
     default: return fail(FMM_ERR_INVALID_ARG, "unknown array");
     }
     if (needed) *needed = (int64_t)size;

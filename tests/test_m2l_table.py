@@ -1,0 +1,120 @@
+"""The M2L work table of a plan against the plan's V lists (host-only plans).
+
+The tensor-core and SIMT M2L kernels read nothing about the V lists but this
+table, so every (target, source) V pair must appear in it exactly once, at
+the offset index whose S_t translates from that source to that target
+(S_t in lexicographic (tx, ty, tz) order over {-3..3}^3 minus {-1..1}^3), and
+nothing else may.  The V lists themselves are checked against the oracle's
+list definitions in test_abi_host.py and test_tree_levels.py.
+"""
+import numpy as np
+import pytest
+
+from paper_2303_08394_gb300 import FMMPlan, _native as N
+from paper_2303_08394_gb300 import workloads as wl
+
+ROWS = 128
+OFFSETS = np.array([(a, b, c) for a in range(-3, 4) for b in range(-3, 4) for c in range(-3, 4)
+                    if max(abs(a), abs(b), abs(c)) > 1], dtype=np.int64)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2303_08394_gb300 import build
+    build.build()
+
+
+def check_table(P):
+    keys = P.array("node_keys").reshape(-1, 4).astype(np.int64)
+    prob = P.array("node_problem")
+    vptr, vidx = P.array("v_ptr"), P.array("v_idx").astype(np.int64)
+    lvl = P.array("m2l_tile_level")
+    tgt = P.array("m2l_tile_target").reshape(-1, ROWS).astype(np.int64)
+    eptr = P.array("m2l_tile_entry_ptr").astype(np.int64)
+    eoff = P.array("m2l_entry_offset").astype(np.int64)
+    esrc = P.array("m2l_entry_src").reshape(-1, ROWS).astype(np.int64)
+    nt, ne = len(lvl), len(eoff)
+    assert nt == P.info("m2l_tiles") and ne == P.info("m2l_entries")
+    assert tgt.shape == (nt, ROWS) and len(eptr) == nt + 1 and esrc.shape == (ne, ROWS)
+    assert eptr[0] == 0 and eptr[-1] == ne and np.all(np.diff(eptr) >= 1)
+
+    # rows: filled from the first, one level and one parity class per tile
+    filled = tgt >= 0
+    cnt = filled.sum(1)
+    assert np.all(cnt >= 1)
+    assert np.array_equal(filled, np.arange(ROWS)[None, :] < cnt[:, None])
+    assert np.all(lvl >= 2)
+    tile_of_row = np.repeat(np.arange(nt), cnt)
+    rows = tgt[filled]
+    assert np.array_equal(keys[rows, 0], lvl[tile_of_row])
+    cls = (keys[rows, 1] & 1) | ((keys[rows, 2] & 1) << 1) | ((keys[rows, 3] & 1) << 2)
+    first = np.concatenate([[0], np.cumsum(cnt)[:-1]])
+    assert np.array_equal(cls, np.repeat(cls[first], cnt))
+
+    # every box with a V list is the target of exactly one row, no other box
+    vlen = np.diff(vptr)
+    assert len(rows) == len(np.unique(rows))
+    assert np.array_equal(np.sort(rows), np.flatnonzero(vlen > 0))
+    # tiles follow (level, class) and, inside one, plan order
+    order = np.lexsort((rows, cls, keys[rows, 0]))
+    assert np.array_equal(order, np.arange(len(rows)))
+
+    # entries: offsets increasing inside a tile, at most 189 per tile (one
+    # parity class reaches 6^3 - 3^3 offsets), each used by some row
+    tile_of_entry = np.repeat(np.arange(nt), np.diff(eptr))
+    assert np.all((eoff >= 0) & (eoff < 316))
+    same = tile_of_entry[1:] == tile_of_entry[:-1]
+    assert np.all(eoff[1:][same] > eoff[:-1][same])
+    assert np.diff(eptr).max() <= 189
+    assert np.all((esrc >= 0).any(1))
+    assert not np.any((esrc >= 0) & ~filled[tile_of_entry])
+
+    # each (target, source, offset) of the table is a V pair at that offset
+    e, r = np.nonzero(esrc >= 0)
+    b, a = tgt[tile_of_entry[e], r], esrc[e, r]
+    assert np.array_equal(keys[a, 0], keys[b, 0])
+    assert np.array_equal(prob[a], prob[b])
+    np.testing.assert_array_equal(keys[a, 1:] - keys[b, 1:], OFFSETS[eoff[e]])
+    # ... and the table holds every V pair exactly once
+    owner = np.repeat(np.arange(len(vlen)), vlen)
+    nb = len(keys)
+    want = np.sort(owner * nb + vidx)
+    got = np.sort(b * nb + a)
+    assert len(got) == P.info("v_pairs")
+    np.testing.assert_array_equal(got, want)
+
+
+CASES = [("cube", 10_000, 64, 1), ("cube", 60_000, 40, 1), ("sphere", 40_000, 32, 1),
+         ("sphere", 40_000, 32, 0), ("gauss", 50_000, 24, 1), ("gauss", 50_000, 24, 0)]
+GEN = {"cube": wl.uniform_cube, "sphere": wl.sphere_surface, "gauss": wl.gaussian_mixture}
+
+
+@pytest.mark.parametrize("kind,n,ncrit,balance", CASES)
+def test_m2l_table_holds_the_v_lists(kind, n, ncrit, balance):
+    x, _ = GEN[kind](n, 7)
+    P = FMMPlan(x, 4, ncrit, host_only=1, balance=balance)
+    check_table(P)
+
+
+def test_m2l_table_distinct_targets():
+    x, _ = wl.gaussian_mixture(20_000, 8)
+    y, _ = wl.uniform_cube(20_000, 9)
+    check_table(FMMPlan(x, 4, 32, targets=y, host_only=1))
+
+
+def test_m2l_table_of_a_forest():
+    pts = [wl.uniform_cube(n, 20 + i)[0] for i, n in enumerate((3000, 40, 9000, 700))]
+    check_table(FMMPlan.batch(pts, 4, 32, host_only=1))
+
+
+def test_m2l_table_of_the_level_builder():
+    x, _ = wl.sphere_surface(30_000, 10)
+    check_table(FMMPlan(x, 4, 32, host_only=1, tree_build=N.TREE_LEVELS_HOST))
+
+
+def test_m2l_table_empty_below_level_two():
+    # one leaf: no box at level >= 2, so no tile
+    x, _ = wl.uniform_cube(20, 11)
+    P = FMMPlan(x, 4, 64, host_only=1)
+    assert P.info("m2l_tiles") == 0 and P.info("m2l_entries") == 0
+    assert len(P.array("m2l_tile_entry_ptr")) == 1
