@@ -152,13 +152,24 @@ enum {
                              (or its default) chooses; 0, 1, 2: that shape
                              (64x32, 32x64, 128x16 rows x vectors) for every
                              level product. */
-    FMM_OPT_GRAPH = 2     /* value 1 (default): fmm_evaluate captures its
+    FMM_OPT_GRAPH = 2,    /* value 1 (default): fmm_evaluate captures its
                              kernels into a CUDA graph on the first call for
                              a given (charges, potentials, nrhs, M2L mode)
                              and replays the graph on later calls with the
                              same ones; 0: launch the kernels directly.  The
                              legacy default stream (NULL) always launches
                              directly, since it cannot be captured. */
+    FMM_OPT_TEST_M2L_STALL = 5 /* failure-detection test hook, value 0
+                             (default) or 1.  With 1, block 0 of every
+                             tensor-core M2L launch first waits on a barrier
+                             that nothing completes; the wait gives up after
+                             0.1 s, the block sets the plan's error word and
+                             abandons its tiles (the other blocks finish), so
+                             the evaluation's results are invalid and the
+                             next call that checks the word (the same call
+                             with host buffers, else the next evaluation)
+                             returns FMM_ERR_TIMEOUT, roles mask 32.  The
+                             plan stays usable.  No effect in FP32 mode. */
 };
 fmm_status fmm_plan_set_option(fmm_plan_t plan, int key, double value);
 

@@ -19,6 +19,7 @@ OPT_M2L_MODE = 1
 OPT_GRAPH = 2
 OPT_AUTOTUNE = 3
 OPT_GEMM_SHAPE = 4
+OPT_TEST_M2L_STALL = 5
 TREE_AUTO, TREE_HOST, TREE_DEVICE, TREE_LEVELS_HOST = 0, 1, 2, 3
 
 INFO = {"n": 0, "nodes": 1, "leaves": 2, "depth": 3, "nsurf": 4, "rank_m2l": 5,

@@ -96,6 +96,7 @@ struct fmm_plan_s {
     float *qh_hi = nullptr, *qh_lo = nullptr;   // split qhat (4-byte slots)
     int qh_cap = 0;                             // nrhs the split buffers hold
     int *err_host = nullptr, *err_dev = nullptr;  // mapped pinned error word
+    int test_m2l_stall = 0;                     // FMM_OPT_TEST_M2L_STALL
     // side stream of the upward pass: each level's M2L projection (qhat =
     // Vk^T rho, needed only by the M2L) runs there while the next level's
     // M2M proceeds; joined before the M2L
@@ -808,7 +809,8 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
             if (!P->tc_ready[idx] || !b.qh_hi || !b.qh_lo)
                 return fail(FMM_ERR_INVALID_ARG, "tensor-core M2L buffers are not prepared");
             CK(launch_m2l_tc(P->dm, P->dops, w, (int)t.nodes(), idx == 1, P->tmap[idx][0],
-                             P->tmap[idx][1], b.qh_hi, b.qh_lo, P->err_dev, P->num_sms, st));
+                             P->tmap[idx][1], b.qh_hi, b.qh_lo, P->err_dev,
+                             P->test_m2l_stall != 0, P->num_sms, st));
             launches += 2;
         }
     }
@@ -1213,6 +1215,12 @@ fmm_status fmm_plan_set_option(fmm_plan_t plan, int key, double value) {
         const int sh = (int)value;
         if (sh < -1 || sh >= kGemmShapes) return fail(FMM_ERR_INVALID_ARG, "shape in [-1, 2]");
         plan->forced_shape = sh;
+        plan->drop_graph();
+        return FMM_OK;
+    }
+    if (key == FMM_OPT_TEST_M2L_STALL) {
+        if (value != 0.0 && value != 1.0) return fail(FMM_ERR_INVALID_ARG, "value 0 or 1");
+        plan->test_m2l_stall = (int)value;
         plan->drop_graph();
         return FMM_OK;
     }

@@ -163,7 +163,8 @@ size_t m2l_tc_smem(int kpad, int *stages);
 cudaError_t configure_m2l_tc(int kpad, bool tf32);
 cudaError_t launch_m2l_tc(const DevM2L &m, const DevOps &o, const DevWork &w, int nnodes,
                           bool tf32, const CUtensorMap &s_hi, const CUtensorMap &s_lo,
-                          void *qh_hi, void *qh_lo, int *err, int num_sms, cudaStream_t st);
+                          void *qh_hi, void *qh_lo, int *err, bool test_stall, int num_sms,
+                          cudaStream_t st);
 
 // Nodes per down-pass chunk (chunks never mix child positions).
 constexpr int kDownChunk = 32;

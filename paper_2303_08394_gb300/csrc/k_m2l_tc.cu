@@ -19,6 +19,8 @@
 //        ~189 k products per target at the level the FP32 path reaches;
 //   8    TMA loads of the S_t chunks (hi and lo) for the same K chunk;
 //   9    allocates TMEM, issues the MMAs (one thread), frees TMEM.
+// Roles in the error word: 0 gatherers, 1 epilogue, 2 TMA, 3 and 4 MMA
+// thread (accumulator, stage), 5 the test hook's stall.
 // Stages of shared memory are recycled through mbarriers: producers wait
 // for `empty`, the MMA thread waits for `full` (gatherers and S_t bytes)
 // and releases the stage with tcgen05.commit.  Every wait is bounded; on expiry the block
@@ -49,6 +51,11 @@ constexpr int kThreads = 32 * (10 + 4 * (kSets - 1));
 // which its 1e-6 bar needs (4 gave 1.5e-6 against the oracle).
 inline int group_for(bool tf32) { return tf32 ? 1 : 4; }
 constexpr uint64_t kWaitLimit = 2000000000ull;  // 2 s per wait
+// Test hook: with TcArgs::test_stall set, block 0's MMA thread first waits
+// on `done`, which nothing completes before the thread's own final commit,
+// with this shorter limit, so that its expiry (role 5) comes first and the
+// block leaves through the same abort path as a real expired wait.
+constexpr uint64_t kTestStallLimit = 100000000ull;  // 0.1 s
 
 struct TcArgs {
     DevM2L m;
@@ -58,6 +65,7 @@ struct TcArgs {
     int zero_row;                 // index of an all-zero qhat row
     float *chat;
     int *err;                     // device-visible error word (0 = ok)
+    int test_stall;               // failure-detection test hook (see below)
 };
 
 template <bool kTF32> struct Fmt {
@@ -288,6 +296,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ready = false;
             bool ok = true;
             const int ks_last = (kp - (a.nch - 1) * F::kc) / F::kstep;
+            if (a.test_stall && blockIdx.x == 0) {
+                ok = tc::mbar_wait(done, 0, abort_flag, kTestStallLimit);
+                if (!ok && !*abort_flag) fail(5);
+            }
             for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x) {
                 const int tile = item / a.row_chunks;
                 const int e0 = a.m.tile_entry_ptr[tile], e1 = a.m.tile_entry_ptr[tile + 1];
@@ -388,7 +400,8 @@ size_t m2l_tc_smem(int kpad, int *stages) {
 
 cudaError_t launch_m2l_tc(const DevM2L &m, const DevOps &o, const DevWork &w, int nnodes,
                           bool tf32, const CUtensorMap &s_hi, const CUtensorMap &s_lo,
-                          void *qh_hi, void *qh_lo, int *err, int num_sms, cudaStream_t st) {
+                          void *qh_hi, void *qh_lo, int *err, bool test_stall, int num_sms,
+                          cudaStream_t st) {
     if (m.ntiles == 0) return cudaSuccess;
     const int kp = o.kpad;
     const int64_t nrows = (int64_t)nnodes * w.nrhs;
@@ -423,6 +436,7 @@ cudaError_t launch_m2l_tc(const DevM2L &m, const DevOps &o, const DevWork &w, in
     a.zero_row = (int)nrows;
     a.chat = w.chat;
     a.err = err;
+    a.test_stall = test_stall ? 1 : 0;
     const size_t sm = m2l_tc_smem(kp, &a.stages);
     const int grid = std::min(a.nitems, num_sms);
     if (tf32)

@@ -263,3 +263,15 @@ def test_gradient_entry_point_arguments():
     assert "host-only" in N.lib().fmm_last_error().decode()
     assert L.fmm_evaluate_gradient(None, qf.ctypes.data, 1, None, g.ctypes.data,
                                    None) == N.FMM_ERR_INVALID_ARG
+
+
+def test_failure_hook_option_values():
+    """FMM_OPT_TEST_M2L_STALL takes 0 or 1 and nothing else (no GPU needed;
+    the stall itself is exercised in test_gpu_failure.py)."""
+    x, _ = wl.uniform_cube(200, 5)
+    P = FMMPlan(x, 4, 32, host_only=1)
+    L = N.lib()
+    assert L.fmm_plan_set_option(P._h, N.OPT_TEST_M2L_STALL, 1.0) == N.FMM_OK
+    assert L.fmm_plan_set_option(P._h, N.OPT_TEST_M2L_STALL, 0.0) == N.FMM_OK
+    assert L.fmm_plan_set_option(P._h, N.OPT_TEST_M2L_STALL, 2.0) == N.FMM_ERR_INVALID_ARG
+    assert "0 or 1" in L.fmm_last_error().decode()
