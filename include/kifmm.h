@@ -89,6 +89,27 @@ typedef struct {
 void fmm_options_init(fmm_options *opts);
 
 /*
+ * On-disk cache of the FP64 operator precomputation (surfaces, factored
+ * pseudo-inverses, M2M/L2L, the compressed M2L factors), which depends only
+ * on (p, alpha_inner, alpha_outer, rcond, eps_svd) and takes seconds at
+ * p >= 6.  The paper likewise computes its operators once and loads them
+ * from files ("Parallelization strategies for FMM operators").
+ *
+ * dir      an existing directory, or NULL / "" to turn the cache off (the
+ *          default).  Process-wide; affects plans created afterwards.
+ *
+ * With a directory set, a plan whose operators are not yet in this
+ * process's memory reads them from dir (one file per key, named
+ * kifmm_ops_v<format>_p<p>_<hash of the radii and cutoffs>.bin) and, when
+ * the file is missing or fails a check (key compared bit for bit, sizes,
+ * checksum), computes them and writes the file through a temporary file
+ * renamed into place.  Operators read from a file are bit-identical to the
+ * ones written.  Failing to write is not an error.  Returns
+ * FMM_ERR_INVALID_ARG if dir is not an existing directory.
+ */
+fmm_status fmm_set_operator_cache(const char *dir);
+
+/*
  * Build a plan: octree, interaction lists, FP64 operator precomputation and
  * the device copies the evaluation needs.
  *
@@ -269,6 +290,9 @@ enum {
     FMM_INFO_POINTS = 16,     /* points in the tree (2n with distinct
                                  targets) */
     FMM_INFO_PROBLEMS = 17,   /* independent problems */
+    FMM_INFO_OPERATOR_SOURCE = 19, /* where the plan's operators came
+                                 from: 0 computed, 1 this process's memory,
+                                 2 the operator cache file */
     FMM_INFO_DEVICE_TREES = 18 /* problems whose octree and lists were built
                                  on the device */
 };

@@ -25,7 +25,7 @@ TREE_AUTO, TREE_HOST, TREE_DEVICE, TREE_LEVELS_HOST = 0, 1, 2, 3
 INFO = {"n": 0, "nodes": 1, "leaves": 2, "depth": 3, "nsurf": 4, "rank_m2l": 5,
         "rank_up": 6, "rank_down": 7, "u_pairs": 8, "v_pairs": 9, "w_pairs": 10,
         "x_pairs": 11, "p2p_pairs": 12, "m2l_tiles": 13, "m2l_entries": 14,
-        "last_launches": 15, "points": 16, "problems": 17, "device_trees": 18}
+        "last_launches": 15, "points": 16, "problems": 17, "device_trees": 18, "operator_source": 19}
 ARRAYS = {"node_keys": (0, "i4"), "node_range": (1, "i8"), "leaf_flag": (2, "i4"),
           "perm": (3, "i8"), "u_ptr": (4, "i8"), "u_idx": (5, "i4"),
           "v_ptr": (6, "i8"), "v_idx": (7, "i4"), "w_ptr": (8, "i8"),
@@ -39,7 +39,7 @@ ARRAYS = {"node_keys": (0, "i4"), "node_range": (1, "i8"), "leaf_flag": (2, "i4"
 
 # every symbol include/kifmm.h declares
 EXPORTS = ("fmm_options_init", "fmm_plan_create", "fmm_plan_create_ex",
-           "fmm_plan_create_batch", "fmm_plan_create_batch_ex", "fmm_plan_set_option", "fmm_evaluate", "fmm_evaluate_gradient", "fmm_evaluate_noalloc", "fmm_destroy",
+           "fmm_plan_create_batch", "fmm_plan_create_batch_ex", "fmm_set_operator_cache", "fmm_plan_set_option", "fmm_evaluate", "fmm_evaluate_gradient", "fmm_evaluate_noalloc", "fmm_destroy",
            "fmm_last_error", "fmm_plan_info", "fmm_plan_get_array", "fmm_plan_phase_ms")
 
 
@@ -83,6 +83,7 @@ def lib():
                                            ctypes.c_int, ctypes.c_int, ctypes.POINTER(Options),
                                            ctypes.POINTER(vp)]
     L.fmm_plan_set_option.argtypes = [vp, ctypes.c_int, ctypes.c_double]
+    L.fmm_set_operator_cache.argtypes = [ctypes.c_char_p]
     L.fmm_evaluate.argtypes = [vp, fp, ctypes.c_int, dp, vp]
     L.fmm_evaluate_noalloc.argtypes = [vp, fp, ctypes.c_int, dp, vp]
     L.fmm_evaluate_gradient.argtypes = [vp, fp, ctypes.c_int, dp, dp, vp]

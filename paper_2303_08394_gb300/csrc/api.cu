@@ -63,6 +63,7 @@ struct fmm_plan_s {
     M2LTable m2l;
     Schedules sched;
     std::shared_ptr<const Operators> ops;
+    int ops_source = kOpsComputed;   // FMM_INFO_OPERATOR_SOURCE
     int kpad = 0;
     bool timing = false;
     std::vector<void *> allocs;   // plan-lifetime device memory
@@ -1079,7 +1080,8 @@ fmm_status create_plan(const double *const *sources, const double *const *target
         }
         build_m2l_table(P->tree, P->m2l);
         build_schedules(P->tree, kDownChunk, P->sched);
-        P->ops = get_operators(p, o.alpha_inner, o.alpha_outer, o.rcond, o.eps_svd);
+        P->ops = get_operators(p, o.alpha_inner, o.alpha_outer, o.rcond, o.eps_svd,
+                               &P->ops_source);
         P->kpad = (P->ops->k + 15) / 16 * 16;
         if (!o.host_only) {
             fmm_status s = upload_plan(P);
@@ -1246,6 +1248,12 @@ fmm_status fmm_evaluate_gradient(fmm_plan_t P, const float *charges, int nrhs,
 
 void fmm_destroy(fmm_plan_t plan) { delete plan; }
 
+fmm_status fmm_set_operator_cache(const char *dir) {
+    if (!set_operator_cache_dir(dir))
+        return fail(FMM_ERR_INVALID_ARG, std::string("not an existing directory: ") + dir);
+    return FMM_OK;
+}
+
 const char *fmm_last_error(void) { return g_error.c_str(); }
 
 fmm_status fmm_plan_info(fmm_plan_t P, int key, int64_t *value) {
@@ -1256,6 +1264,7 @@ fmm_status fmm_plan_info(fmm_plan_t P, int key, int64_t *value) {
     case FMM_INFO_POINTS: *value = t.n; break;
     case FMM_INFO_PROBLEMS: *value = t.nproblems; break;
     case FMM_INFO_DEVICE_TREES: *value = P->device_trees; break;
+    case FMM_INFO_OPERATOR_SOURCE: *value = P->ops_source; break;
     case FMM_INFO_NODES: *value = t.nodes(); break;
     case FMM_INFO_LEAVES: *value = (int64_t)t.leaves.size(); break;
     case FMM_INFO_DEPTH: *value = t.depth; break;

@@ -11,10 +11,17 @@
 // 1/s, then V in FP32; an explicitly formed A^+ would carry eps * cond(A)
 // of rounding in every direction (cond ~ 1e9 at p = 6), while the factored
 // form keeps the rounding in the directions the next operator damps.
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <atomic>
 #include <cmath>
+#include <cstdio>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <stdexcept>
+#include <string>
 #include <tuple>
 
 #include "linalg.h"
@@ -186,8 +193,200 @@ std::shared_ptr<Operators> compute(int p, double ai, double ao, double rcond,
 
 } // namespace
 
-std::shared_ptr<const Operators> get_operators(int p, double ai, double ao,
-                                               double rcond, double eps_svd) {
+// ------------------------------------------------------------ file cache
+// The precomputation depends only on (p, ai, ao, rcond, eps_svd), so it is
+// done once and kept, as the paper keeps its precomputed operators in files
+// ("Parallelization strategies for FMM operators": operators are computed
+// once and reused).  A cache file holds, little-endian:
+//   "KIFMMOPS", u32 format, u32 byte-order mark 0x01020304,
+//   i32 p, f64 ai, ao, rcond, eps_svd (the key, compared bit for bit),
+//   i32 ns, rP, rQ, k, then each array as i64 count + f64 values, in the
+//   order of the Operators members, and last an FNV-1a 64 checksum of
+//   every byte before it.
+// A file that fails any check (magic, format, byte order, key, sizes,
+// checksum, length) is ignored and replaced; writes go to a temporary file
+// renamed into place, so readers see a whole file or none.  The cache is
+// best effort: a directory that cannot be written only costs the write.
+
+namespace {
+
+std::mutex g_dir_mu;
+std::string g_dir;   // empty: no file cache
+
+constexpr char kMagic[8] = {'K', 'I', 'F', 'M', 'M', 'O', 'P', 'S'};
+constexpr uint32_t kFormat = 1;
+constexpr uint32_t kByteOrder = 0x01020304u;
+
+uint64_t fnv1a(const unsigned char *p, size_t n) {
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+struct Out {
+    std::vector<unsigned char> b;
+    void raw(const void *p, size_t n) {
+        const unsigned char *c = static_cast<const unsigned char *>(p);
+        b.insert(b.end(), c, c + n);
+    }
+    template <class T> void val(T v) { raw(&v, sizeof v); }
+    void vec(const std::vector<double> &v) {
+        val<int64_t>((int64_t)v.size());
+        raw(v.data(), v.size() * sizeof(double));
+    }
+};
+
+struct In {
+    const unsigned char *p;
+    size_t n, at = 0;
+    bool ok = true;
+    bool raw(void *dst, size_t k) {
+        if (!ok || k > n - at) return ok = false;
+        std::memcpy(dst, p + at, k);
+        at += k;
+        return true;
+    }
+    template <class T> T val() {
+        T v{};
+        raw(&v, sizeof v);
+        return v;
+    }
+    void vec(std::vector<double> &v, size_t want) {
+        const int64_t c = val<int64_t>();
+        if (!ok || c < 0 || (size_t)c != want) {
+            ok = false;
+            return;
+        }
+        v.resize(want);
+        raw(v.data(), want * sizeof(double));
+    }
+};
+
+std::string cache_file(const std::string &dir, int p, double ai, double ao, double rcond,
+                       double eps_svd) {
+    const double key[4] = {ai, ao, rcond, eps_svd};
+    char name[96];
+    std::snprintf(name, sizeof name, "kifmm_ops_v%u_p%d_%016llx.bin", kFormat, p,
+                  (unsigned long long)fnv1a(reinterpret_cast<const unsigned char *>(key),
+                                            sizeof key));
+    return dir + "/" + name;
+}
+
+std::vector<unsigned char> serialise(const Operators &o) {
+    Out w;
+    w.raw(kMagic, sizeof kMagic);
+    w.val<uint32_t>(kFormat);
+    w.val<uint32_t>(kByteOrder);
+    w.val<int32_t>(o.p);
+    w.val<double>(o.ai);
+    w.val<double>(o.ao);
+    w.val<double>(o.rcond);
+    w.val<double>(o.eps_svd);
+    w.val<int32_t>(o.ns);
+    w.val<int32_t>(o.rP);
+    w.val<int32_t>(o.rQ);
+    w.val<int32_t>(o.k);
+    for (const std::vector<double> *v : {&o.surf, &o.Pu, &o.Ps, &o.Pv, &o.Qu, &o.Qs, &o.Qv,
+                                         &o.M2M, &o.L2L, &o.Uk, &o.Vk, &o.S, &o.QUk,
+                                         &o.sigmaH, &o.sigmaW})
+        w.vec(*v);
+    w.val<uint64_t>(fnv1a(w.b.data(), w.b.size()));
+    return std::move(w.b);
+}
+
+bool same_bits(double a, double b) { return std::memcmp(&a, &b, sizeof a) == 0; }
+
+// The operators in `bytes` if they are a whole, intact file for this key.
+std::shared_ptr<Operators> deserialise(const std::vector<unsigned char> &bytes, int p, double ai,
+                                       double ao, double rcond, double eps_svd) {
+    if (bytes.size() < sizeof(uint64_t)) return nullptr;
+    const size_t body = bytes.size() - sizeof(uint64_t);
+    uint64_t sum;
+    std::memcpy(&sum, bytes.data() + body, sizeof sum);
+    if (sum != fnv1a(bytes.data(), body)) return nullptr;
+    In r{bytes.data(), body};
+    char magic[8];
+    r.raw(magic, sizeof magic);
+    if (!r.ok || std::memcmp(magic, kMagic, sizeof magic) != 0) return nullptr;
+    if (r.val<uint32_t>() != kFormat || r.val<uint32_t>() != kByteOrder) return nullptr;
+    auto o = std::make_shared<Operators>();
+    o->p = r.val<int32_t>();
+    o->ai = r.val<double>();
+    o->ao = r.val<double>();
+    o->rcond = r.val<double>();
+    o->eps_svd = r.val<double>();
+    if (!r.ok || o->p != p || !same_bits(o->ai, ai) || !same_bits(o->ao, ao) ||
+        !same_bits(o->rcond, rcond) || !same_bits(o->eps_svd, eps_svd))
+        return nullptr;
+    o->ns = r.val<int32_t>();
+    o->rP = r.val<int32_t>();
+    o->rQ = r.val<int32_t>();
+    o->k = r.val<int32_t>();
+    const int ns = o->ns;
+    if (!r.ok || ns != 6 * (p - 1) * (p - 1) + 2 || o->rP < 1 || o->rP > ns || o->rQ < 1 ||
+        o->rQ > ns || o->k < 1 || o->k > ns)
+        return nullptr;
+    const size_t n = (size_t)ns, rP = (size_t)o->rP, rQ = (size_t)o->rQ, k = (size_t)o->k;
+    const size_t sig = eps_svd > 0 ? n : 0;
+    r.vec(o->surf, 3 * n);
+    r.vec(o->Pu, n * rP);
+    r.vec(o->Ps, rP);
+    r.vec(o->Pv, n * rP);
+    r.vec(o->Qu, n * rQ);
+    r.vec(o->Qs, rQ);
+    r.vec(o->Qv, n * rQ);
+    r.vec(o->M2M, 8 * rP * n);
+    r.vec(o->L2L, 8 * rQ * n);
+    r.vec(o->Uk, n * k);
+    r.vec(o->Vk, n * k);
+    r.vec(o->S, (size_t)kNumOffsets * k * k);
+    r.vec(o->QUk, rQ * k);
+    r.vec(o->sigmaH, sig);
+    r.vec(o->sigmaW, sig);
+    if (!r.ok || r.at != body) return nullptr;
+    return o;
+}
+
+std::vector<unsigned char> read_file(const std::string &path) {
+    std::vector<unsigned char> b;
+    FILE *f = std::fopen(path.c_str(), "rb");
+    if (!f) return b;
+    unsigned char chunk[1 << 16];
+    size_t got;
+    while ((got = std::fread(chunk, 1, sizeof chunk, f)) > 0) b.insert(b.end(), chunk, chunk + got);
+    std::fclose(f);
+    return b;
+}
+
+void write_file_atomic(const std::string &path, const std::vector<unsigned char> &b) {
+    static std::atomic<unsigned> counter{0};
+    const std::string tmp = path + ".tmp." + std::to_string((long long)getpid()) + "." +
+                            std::to_string(counter++);
+    FILE *f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return;
+    const bool ok = std::fwrite(b.data(), 1, b.size(), f) == b.size();
+    if (std::fclose(f) != 0 || !ok || std::rename(tmp.c_str(), path.c_str()) != 0)
+        std::remove(tmp.c_str());
+}
+
+} // namespace
+
+bool set_operator_cache_dir(const char *dir) {
+    std::string d = dir ? dir : "";
+    if (!d.empty()) {
+        struct stat st;
+        if (stat(d.c_str(), &st) != 0 || !S_ISDIR(st.st_mode)) return false;
+    }
+    std::lock_guard<std::mutex> g(g_dir_mu);
+    g_dir = d;
+    return true;
+}
+
+std::shared_ptr<const Operators> get_operators(int p, double ai, double ao, double rcond,
+                                               double eps_svd, int *source) {
     static std::mutex mu;
     static std::map<std::tuple<int, double, double, double, double>,
                     std::shared_ptr<const Operators>> cache;
@@ -195,9 +394,31 @@ std::shared_ptr<const Operators> get_operators(int p, double ai, double ao,
     {
         std::lock_guard<std::mutex> g(mu);
         auto it = cache.find(key);
-        if (it != cache.end()) return it->second;
+        if (it != cache.end()) {
+            if (source) *source = kOpsFromMemory;
+            return it->second;
+        }
     }
-    auto op = compute(p, ai, ao, rcond, eps_svd);
+    std::string dir;
+    {
+        std::lock_guard<std::mutex> g(g_dir_mu);
+        dir = g_dir;
+    }
+    std::shared_ptr<Operators> op;
+    int from = kOpsComputed;
+    if (!dir.empty()) {
+        const std::string path = cache_file(dir, p, ai, ao, rcond, eps_svd);
+        op = deserialise(read_file(path), p, ai, ao, rcond, eps_svd);
+        if (op) {
+            from = kOpsFromFile;
+        } else {
+            op = compute(p, ai, ao, rcond, eps_svd);
+            write_file_atomic(path, serialise(*op));
+        }
+    } else {
+        op = compute(p, ai, ao, rcond, eps_svd);
+    }
+    if (source) *source = from;
     std::lock_guard<std::mutex> g(mu);
     cache[key] = op;
     return op;

@@ -48,8 +48,16 @@ struct Operators {
     std::vector<double> sigmaH, sigmaW;// singular values of the stacks
 };
 
+// Operators for (p, radii, cutoffs): from this process's memory, else from
+// the file cache directory when one is set, else computed (and then written
+// there).  *source (may be NULL) receives which.
+enum { kOpsComputed = 0, kOpsFromMemory = 1, kOpsFromFile = 2 };
 std::shared_ptr<const Operators> get_operators(int p, double ai, double ao,
-                                               double rcond, double eps_svd);
+                                               double rcond, double eps_svd,
+                                               int *source = nullptr);
+// Directory of the operator file cache; NULL or "" turns it off.  False if
+// `dir` is not an existing directory.
+bool set_operator_cache_dir(const char *dir);
 
 // Octree over the (sorted) points plus interaction lists and schedules.
 struct Tree {

@@ -6,6 +6,7 @@ libkifmm.so's CUDA kernels.
 from __future__ import annotations
 
 import ctypes
+import os
 
 import numpy as np
 
@@ -41,6 +42,15 @@ def _options(options):
             raise TypeError(f"unknown option {k}")
         setattr(opts, k, v)
     return opts
+
+
+def set_operator_cache(directory):
+    """Keep the FP64 operator precomputation in files under ``directory``
+    (an existing directory; None turns the cache off, the default).  Plans
+    created afterwards in this process read their operators from there, or
+    compute and write them; see fmm_set_operator_cache in kifmm.h."""
+    d = None if directory is None else os.fsencode(directory)
+    N.check(N.lib().fmm_set_operator_cache(d))
 
 
 class FMMPlan:
