@@ -961,6 +961,23 @@ void build_problem(const double *xs, const double *xt, int64_t n, const TreeOpti
     set_point_roles(t, n, xt != nullptr);
 }
 
+// Host fault-injection hook for the table check's tests (environment
+// variable FMM_TEST_CORRUPT_TABLE=<table>): one out-of-range value is put
+// into the named table before the check runs, so a test can see the check
+// refuse the plan before anything reaches the device.  Unset in normal use.
+void corrupt_table_for_test(fmm_plan_s *P, const std::string &name) {
+    Tree &t = P->tree;
+    const int32_t nn = (int32_t)t.nodes();
+    if (name == "u_idx" && !t.u_idx.empty()) t.u_idx[t.u_idx.size() / 2] = nn;
+    else if (name == "v_ptr" && t.v_ptr.size() > 2) t.v_ptr[1] = t.v_ptr.back() + 1;
+    else if (name == "entry_src" && !P->m2l.entry_src.empty()) P->m2l.entry_src.back() = nn;
+    else if (name == "tile_target" && !P->m2l.tile_target.empty()) P->m2l.tile_target[0] = -2;
+    else if (name == "qidx" && !t.qidx.empty()) t.qidx[0] = P->rows;
+    else if (name == "down_chunk" && !P->sched.down_chunk.empty()) P->sched.down_chunk[1] = 1 << 30;
+    else if (name == "begin" && !t.begin.empty()) t.begin[0] = t.n + 1;
+    else if (name == "child" && !t.child.empty()) t.child[0] = nn + 7;
+}
+
 fmm_status create_plan(const double *const *sources, const double *const *targets,
                        const int64_t *n, int nproblems, int p, int ncrit,
                        const fmm_options *opts, fmm_plan_t *out) {
@@ -1080,6 +1097,13 @@ fmm_status create_plan(const double *const *sources, const double *const *target
         }
         build_m2l_table(P->tree, P->m2l);
         build_schedules(P->tree, kDownChunk, P->sched);
+        if (const char *hook = std::getenv("FMM_TEST_CORRUPT_TABLE"))
+            corrupt_table_for_test(P, hook);
+        const std::string bad = check_tables(P->tree, P->sched, P->m2l, P->rows);
+        if (!bad.empty()) {
+            delete P;
+            return fail(FMM_ERR_UNSUPPORTED, "plan tables failed their check: " + bad);
+        }
         P->ops = get_operators(p, o.alpha_inner, o.alpha_outer, o.rcond, o.eps_svd,
                                &P->ops_source);
         P->kpad = (P->ops->k + 15) / 16 * 16;

@@ -168,6 +168,13 @@ struct Schedules {
 };
 void build_schedules(const Tree &tree, int chunk, Schedules &s);
 
+// Check every index table the kernels read before any of it reaches the
+// device: CSR offsets non-decreasing and ending at their index count, every
+// node, point, row, offset and schedule index inside its array, and every
+// value the upload narrows to 32 bits representable.  Empty when the plan
+// is sound, else a message naming the first table that is not.
+std::string check_tables(const Tree &t, const Schedules &s, const M2LTable &m, int64_t rows);
+
 } // namespace kifmm
 
 // Host-side plan (the opaque fmm_plan_t).

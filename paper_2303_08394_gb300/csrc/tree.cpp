@@ -622,4 +622,108 @@ void build_schedules(const Tree &t, int chunk, Schedules &s) {
         }
 }
 
+namespace {
+
+// Index of the first element of v outside [lo, hi), or -1.
+template <class T> int64_t first_outside(const std::vector<T> &v, int64_t lo, int64_t hi) {
+    int64_t bad = INT64_MAX;
+#pragma omp parallel for reduction(min : bad) schedule(static)
+    for (int64_t i = 0; i < (int64_t)v.size(); ++i)
+        if ((int64_t)v[i] < lo || (int64_t)v[i] >= hi) bad = std::min(bad, i);
+    return bad == INT64_MAX ? -1 : bad;
+}
+
+std::string outside(const char *name, int64_t i, int64_t lo, int64_t hi) {
+    return std::string(name) + "[" + std::to_string(i) + "] outside [" + std::to_string(lo) +
+           ", " + std::to_string(hi) + ")";
+}
+
+// CSR offsets: size rows + 1, start 0, non-decreasing, end at nidx, and
+// (uploaded as int32) at most INT32_MAX.
+template <class T>
+std::string check_csr(const char *name, const std::vector<T> &ptr, int64_t rows, int64_t nidx) {
+    if ((int64_t)ptr.size() != rows + 1) return std::string(name) + ": wrong size";
+    if (ptr[0] != 0 || (int64_t)ptr[rows] != nidx)
+        return std::string(name) + ": does not span its index array";
+    if (nidx > INT32_MAX) return std::string(name) + ": too many entries for 32-bit offsets";
+    for (int64_t i = 0; i < rows; ++i)
+        if (ptr[i + 1] < ptr[i]) return std::string(name) + ": decreasing at " + std::to_string(i);
+    return "";
+}
+
+} // namespace
+
+std::string check_tables(const Tree &t, const Schedules &s, const M2LTable &m, int64_t rows) {
+    const int64_t nn = t.nodes(), n = t.n;
+    std::string e;
+    int64_t i;
+#define CHECK(expr) \
+    if (!(e = (expr)).empty()) return e;
+#define RANGE(vec, lo, hi) \
+    if ((i = first_outside(vec, lo, hi)) >= 0) return outside(#vec, i, lo, hi);
+    if (n > INT32_MAX || nn > INT32_MAX / 8) return "tree too large for 32-bit indices";
+    if ((int64_t)t.begin.size() != nn || (int64_t)t.end.size() != nn ||
+        (int64_t)t.child.size() != 8 * nn || (int64_t)t.key.size() != 4 * nn ||
+        (int64_t)t.leaf.size() != nn || (int64_t)t.node_problem.size() != nn ||
+        (int64_t)t.qidx.size() != n || (int64_t)t.oidx.size() != n ||
+        (int64_t)t.rel.size() != 4 * n || (int64_t)t.rel_lo.size() != 4 * n)
+        return "tree arrays of inconsistent sizes";
+    RANGE(t.begin, 0, n + 1);
+    RANGE(t.end, 0, n + 1);
+    for (int64_t b = 0; b < nn; ++b)
+        if (t.begin[b] > t.end[b]) return "node " + std::to_string(b) + ": begin > end";
+    RANGE(t.parent, -1, nn);
+    RANGE(t.child, -1, nn);
+    RANGE(t.leaves, 0, nn);
+    RANGE(t.node_problem, 0, t.nproblems);
+    if ((int64_t)t.roots.size() != 4 * (int64_t)t.nproblems) return "roots: wrong size";
+    RANGE(t.qidx, -1, rows);
+    RANGE(t.oidx, -1, rows);
+    if ((int64_t)t.level_ptr.size() != t.depth + 2 || t.level_ptr[0] != 0 ||
+        t.level_ptr[t.depth + 1] != nn)
+        return "level_ptr does not span the nodes";
+    CHECK(check_csr("u_ptr", t.u_ptr, nn, (int64_t)t.u_idx.size()));
+    CHECK(check_csr("v_ptr", t.v_ptr, nn, (int64_t)t.v_idx.size()));
+    CHECK(check_csr("w_ptr", t.w_ptr, nn, (int64_t)t.w_idx.size()));
+    CHECK(check_csr("x_ptr", t.x_ptr, nn, (int64_t)t.x_idx.size()));
+    RANGE(t.u_idx, 0, nn);
+    RANGE(t.v_idx, 0, nn);
+    RANGE(t.w_idx, 0, nn);
+    RANGE(t.x_idx, 0, nn);
+    if (t.v_off.size() != t.v_idx.size()) return "v_off: wrong size";
+    RANGE(t.v_off, 0, kNumOffsets);
+    // schedules
+    RANGE(s.p2m_nodes, 0, nn);
+    RANGE(s.m2m_nodes, 0, nn);
+    RANGE(s.down_nodes, 0, nn);
+    RANGE(s.x_nodes, 0, nn);
+    if ((int64_t)s.x_slot.size() != nn) return "x_slot: wrong size";
+    RANGE(s.x_slot, -1, (int64_t)s.x_nodes.size());
+    CHECK(check_csr("m2m_level_ptr", s.m2m_level_ptr, t.depth + 1, (int64_t)s.m2m_nodes.size()));
+    CHECK(check_csr("down_level_ptr", s.down_level_ptr, t.depth + 1,
+                    (int64_t)s.down_nodes.size()));
+    if (s.down_chunk.size() % 4 != 0) return "down_chunk: not whole chunks";
+    CHECK(check_csr("down_chunk_level_ptr", s.down_chunk_level_ptr, t.depth + 1,
+                    (int64_t)s.down_chunk.size() / 4));
+    for (size_t c = 0; c < s.down_chunk.size(); c += 4) {
+        const int64_t start = s.down_chunk[c], cnt = s.down_chunk[c + 1];
+        if (start < 0 || cnt < 1 || start + cnt > (int64_t)s.down_nodes.size() ||
+            s.down_chunk[c + 2] < 0 || s.down_chunk[c + 2] > 7 || s.down_chunk[c + 3] < 0 ||
+            s.down_chunk[c + 3] > t.depth)
+            return "down_chunk " + std::to_string(c / 4) + ": out of range";
+    }
+    // M2L work table
+    const int64_t nt = (int64_t)m.tile_level.size();
+    if ((int64_t)m.tile_target.size() != nt * kTileRows) return "tile_target: wrong size";
+    CHECK(check_csr("tile_entry_ptr", m.tile_entry_ptr, nt, (int64_t)m.entry_offset.size()));
+    if (m.entry_src.size() != m.entry_offset.size() * kTileRows) return "entry_src: wrong size";
+    RANGE(m.tile_level, 2, t.depth + 1);
+    RANGE(m.tile_target, -1, nn);
+    RANGE(m.entry_offset, 0, kNumOffsets);
+    RANGE(m.entry_src, -1, nn);
+#undef RANGE
+#undef CHECK
+    return "";
+}
+
 } // namespace kifmm
