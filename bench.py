@@ -39,7 +39,8 @@ CPU_SAMPLE_N = 40_000
 # Keyed by kernel, workload, M2L mode and M2L operand width (kpad; the leaf
 # kernel does not depend on it: None); any other combination reports null.
 TRAFFIC = {
-    ("k_m2l_tc", "cube_n1e6_p6_ncrit150", "bf16x3", 128): 78.9e6,
+    # dram read + write of one launch (profiles/k_m2l_tc_cube_n1e6_p6_bf16x3.md)
+    ("k_m2l_tc", "cube_n1e6_p6_ncrit150", "bf16x3", 128): 77.2e6,
     # the leaf pass: its four width-group launches together
     ("k_eval", "cube_n1e6_p6_ncrit150", "bf16x3", None): 90.6e6,
     # the gradient variant (profiles/k_eval_gradient_cube_n1e6_p6.md)
