@@ -355,6 +355,31 @@ enum {
 fmm_status fmm_plan_get_array(fmm_plan_t plan, int which, void *dst,
                               int64_t bytes, int64_t *needed);
 
+/* Per-box results of the passes of the last fmm_evaluate (or
+ * fmm_evaluate_gradient) on this plan, for per-operator tests: FP32
+ * [nodes][nrhs][ld] in plan node order (FMM_ARRAY_NODE_KEYS), nrhs of that
+ * evaluation.  Unit-box convention: in box B's coordinates y' = (y - c_B) / h_B
+ * (h_B its half-width) the arrays stand for the potential
+ *     phi(y) = sum_j rho_j / |y' - a s_j|  /  (4 pi h_B)
+ * (h_B and y in the caller's length unit, s the unit surface
+ * FMM_ARRAY_SURFACE):
+ *   FMM_WORK_UP    upward equivalent densities rho, a = alpha_inner
+ *                  ("Upward pass": P2M at leaves, M2M above), boxes of
+ *                  level >= 2; ld = nsurf rounded up to 4;
+ *   FMM_WORK_DOWN  downward equivalent densities, a = alpha_outer (after
+ *                  M2L, P2L and L2L), boxes of level >= 2; ld as UP;
+ *   FMM_WORK_QHAT  compressed multipoles Vk^T rho_up; ld = k rounded up to 16;
+ *   FMM_WORK_CHAT  the M2L's output: Uk * chat is the check potential of the
+ *                  box's V list on its downward check surface (y' =
+ *                  alpha_inner s), boxes with a non-empty V list; ld as QHAT.
+ * Rows of boxes a pass does not write hold unspecified values.  Waits for the
+ * last evaluation's stream, then copies; FMM_ERR_INVALID_ARG before the
+ * first evaluation, for a host-only plan or a short dst.  (Evaluations by
+ * fmm_evaluate_noalloc use other memory and are not seen here.) */
+enum { FMM_WORK_UP = 0, FMM_WORK_DOWN = 1, FMM_WORK_QHAT = 2, FMM_WORK_CHAT = 3 };
+fmm_status fmm_plan_get_workspace(fmm_plan_t plan, int which, void *dst, int64_t bytes,
+                                  int64_t *needed);
+
 /* Milliseconds each phase of the last evaluation took, measured with CUDA
  * events on the evaluation stream when timing is on (FMM_TIMING=1 in the
  * environment at plan creation).  phase: 0 upward, 1 M2L, 2 downward,

@@ -327,8 +327,9 @@ class KIFMM:
     ``evaluate(charges)`` returns potentials in the caller's point order and
     keeps every operator's output in attributes for per-operator tests:
     ``up`` (upward equivalent densities), ``down`` (downward equivalent
-    densities), ``down_check`` (downward check potentials), ``near`` and
-    ``far`` (potentials split by source).
+    densities), ``down_check`` (downward check potentials), ``m2l_check``
+    (the V-list part of each downward check potential, the M2L's output),
+    ``near`` and ``far`` (potentials split by source).
     """
 
     def __init__(self, points, p: int, ncrit: int, alpha_inner=1.05,
@@ -406,12 +407,14 @@ class KIFMM:
                         check += laplace_kernel(uc, self._surface(ch, ai)) @ up[ch]
                 up[b] = self.uc2e[l] @ check
         # downward pass from level 2: M2L (V), P2L (X), L2L (parent)
-        down, down_check = {}, {}
+        down, down_check, m2l_check = {}, {}, {}
         for l in range(2, t.depth + 1):
             for b in sorted(k for k in t.nonempty if k[0] == l):
                 check = np.zeros((ne, nrhs))
                 for a in self.V.get(b, ()):
                     check += self._m2l_matrix(b, a) @ up[a]
+                if b in self.V:
+                    m2l_check[b] = check.copy()
                 if b in self.X:
                     dc = self._surface(b, ai)
                     for a in self.X[b]:
@@ -444,6 +447,7 @@ class KIFMM:
             for a in self.W.get(b, ()):
                 apply(tidx, xt, self._surface(a, ai), up[a], far)
         self.up, self.down, self.down_check = up, down, down_check
+        self.m2l_check = m2l_check
         self.near, self.far = near, far
         phi = near + far
         phi = phi[:, 0] if vec else phi

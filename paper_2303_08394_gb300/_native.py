@@ -40,7 +40,7 @@ ARRAYS = {"node_keys": (0, "i4"), "node_range": (1, "i8"), "leaf_flag": (2, "i4"
 # every symbol include/kifmm.h declares
 EXPORTS = ("fmm_options_init", "fmm_plan_create", "fmm_plan_create_ex",
            "fmm_plan_create_batch", "fmm_plan_create_batch_ex", "fmm_set_operator_cache", "fmm_plan_set_option", "fmm_evaluate", "fmm_evaluate_gradient", "fmm_evaluate_noalloc", "fmm_destroy",
-           "fmm_last_error", "fmm_plan_info", "fmm_plan_get_array", "fmm_plan_phase_ms")
+           "fmm_last_error", "fmm_plan_info", "fmm_plan_get_array", "fmm_plan_get_workspace", "fmm_plan_phase_ms")
 
 
 class Options(ctypes.Structure):
@@ -93,6 +93,7 @@ def lib():
     L.fmm_last_error.restype = ctypes.c_char_p
     L.fmm_plan_info.argtypes = [vp, ctypes.c_int, ctypes.POINTER(i64)]
     L.fmm_plan_get_array.argtypes = [vp, ctypes.c_int, vp, i64, ctypes.POINTER(i64)]
+    L.fmm_plan_get_workspace.argtypes = [vp, ctypes.c_int, vp, i64, ctypes.POINTER(i64)]
     L.fmm_plan_phase_ms.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     for name in ("fmm_plan_create", "fmm_plan_create_ex", "fmm_plan_create_batch",
                  "fmm_plan_create_batch_ex", "fmm_plan_set_option",

@@ -87,6 +87,7 @@ struct fmm_plan_s {
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t tune_ev[2] = {nullptr, nullptr};
     cudaStream_t last_stream = nullptr;
+    int last_nrhs = 0;               // nrhs of the last fmm_evaluate(_gradient)
     int64_t last_launches = 0;
     int num_sms = 0;
     // tensor-core M2L: split S_t arrays and their TMA maps, per mode
@@ -1166,6 +1167,7 @@ fmm_status evaluate_impl(fmm_plan_s *P, const float *charges, int nrhs, double *
     s = run_evaluation(P, dq_ptr, nrhs, dp_ptr, dg_ptr, st);
     if (s != FMM_OK) return s;
     P->last_stream = st;
+    P->last_nrhs = nrhs;
     if (!dp) CK(cudaMemcpyAsync(potentials, dp_ptr, nq * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (!dg) CK(cudaMemcpyAsync(gradients, dg_ptr, 3 * nq * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (!dq || !dp || !dg) {
@@ -1385,6 +1387,33 @@ fmm_status fmm_plan_get_array(fmm_plan_t P, int which, void *dst, int64_t bytes,
     if (!dst) return FMM_OK;
     if (bytes < (int64_t)size) return fail(FMM_ERR_INVALID_ARG, "destination too small");
     if (size) std::memcpy(dst, src, size);
+    return FMM_OK;
+}
+
+fmm_status fmm_plan_get_workspace(fmm_plan_t P, int which, void *dst, int64_t bytes,
+                                  int64_t *needed) {
+    if (!P) return fail(FMM_ERR_INVALID_ARG, "plan is NULL");
+    if (P->opts.host_only || P->last_nrhs < 1)
+        return fail(FMM_ERR_INVALID_ARG, "no evaluation on this plan yet");
+    const size_t nn = (size_t)P->tree.nodes(), nr = (size_t)P->last_nrhs;
+    const size_t nsp = (size_t)((P->ops->ns + 3) & ~3), kp = (size_t)P->kpad;
+    const float *src = nullptr;
+    size_t ld = 0;
+    switch (which) {
+    case FMM_WORK_UP: src = P->up; ld = nsp; break;
+    case FMM_WORK_DOWN: src = P->down; ld = nsp; break;
+    case FMM_WORK_QHAT: src = P->qhat; ld = kp; break;
+    case FMM_WORK_CHAT: src = P->chat; ld = kp; break;
+    default: return fail(FMM_ERR_INVALID_ARG, "unknown workspace array");
+    }
+    const size_t size = nn * nr * ld * sizeof(float);
+    if (needed) *needed = (int64_t)size;
+    if (!dst) return FMM_OK;
+    if (bytes < (int64_t)size) return fail(FMM_ERR_INVALID_ARG, "destination too small");
+    if (!src) return fail(FMM_ERR_INVALID_ARG, "no workspace");
+    CK(cudaSetDevice(P->device));
+    CK(cudaStreamSynchronize(P->last_stream));
+    if (size) CK(cudaMemcpy(dst, src, size, cudaMemcpyDeviceToHost));
     return FMM_OK;
 }
 

@@ -251,6 +251,23 @@ class FMMPlan:
                                            ctypes.byref(need)))
         return out
 
+    def workspace(self, name: str) -> np.ndarray:
+        """Per-box results of the last evaluation's passes, float32
+        (nodes, nrhs, ld): "up", "down", "qhat" or "chat" (conventions in
+        fmm_plan_get_workspace, kifmm.h)."""
+        which = {"up": 0, "down": 1, "qhat": 2, "chat": 3}[name]
+        need = ctypes.c_int64()
+        N.check(N.lib().fmm_plan_get_workspace(self._h, which, None, 0, ctypes.byref(need)))
+        out = np.empty(need.value // 4, dtype=np.float32)
+        N.check(N.lib().fmm_plan_get_workspace(self._h, which, out.ctypes.data, need.value,
+                                               ctypes.byref(need)))
+        return out.reshape(self.info("nodes"), -1, self._ws_ld(name))
+
+    def _ws_ld(self, name):
+        if name in ("up", "down"):
+            return (self.info("nsurf") + 3) // 4 * 4
+        return (self.info("rank_m2l") + 15) // 16 * 16
+
     def phase_ms(self):
         """Per-phase milliseconds of the last evaluation (needs FMM_TIMING=1)."""
         out = []

@@ -275,3 +275,15 @@ def test_failure_hook_option_values():
     assert L.fmm_plan_set_option(P._h, N.OPT_TEST_M2L_STALL, 0.0) == N.FMM_OK
     assert L.fmm_plan_set_option(P._h, N.OPT_TEST_M2L_STALL, 2.0) == N.FMM_ERR_INVALID_ARG
     assert "0 or 1" in L.fmm_last_error().decode()
+
+
+def test_workspace_export_needs_an_evaluation():
+    """fmm_plan_get_workspace refuses host-only plans, plans never evaluated
+    and unknown arrays (no GPU needed)."""
+    x, _ = wl.uniform_cube(200, 6)
+    P = FMMPlan(x, 4, 32, host_only=1)
+    need = ctypes.c_int64()
+    L = N.lib()
+    assert L.fmm_plan_get_workspace(P._h, 0, None, 0, ctypes.byref(need)) == N.FMM_ERR_INVALID_ARG
+    assert "no evaluation" in L.fmm_last_error().decode()
+    assert L.fmm_plan_get_workspace(None, 0, None, 0, None) == N.FMM_ERR_INVALID_ARG

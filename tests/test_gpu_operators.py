@@ -1,0 +1,107 @@
+"""Each pass of the GPU evaluation against the FP64 oracle's output of the
+same operator, box by box ("Computational structure of FMM operators": the
+operators are kept apart so they can be tested one by one).
+
+The library keeps its densities in unit-box form: in box B's coordinates
+y' = (y - c_B) / h_B they generate sum_j rho_j / |y' - a s_j| / (4 pi h_B).
+The oracle's pseudo-inverses are those of the same matrices scaled by
+1/(4 pi h_B), so in exact arithmetic the two densities are equal.  They are
+compared through the potentials they generate on their check surfaces,
+since a density itself carries the rounding of the FP32 pipeline amplified
+along the pseudo-inverse's weakest directions, which the potentials damp:
+
+* up    (P2M at leaves, M2M above): K(a_out s, a_in s) rho_up, every box of
+  level >= 2;
+* chat  (the M2L, rows A0-A2 of the hot path up to the projection out):
+  Uk chat / (4 pi h_B) against the oracle's V-list check potential, every box
+  with a V list;
+* down  (M2L, P2L and L2L through the downward pseudo-inverse):
+  K(a_in s, a_out s) rho_down, every box of level >= 2.
+
+Errors are relative L2 over all boxes of a level.
+"""
+import numpy as np
+import pytest
+
+from oracle import kifmm as ok
+from paper_2303_08394_gb300 import FMMPlan, _native as N
+from paper_2303_08394_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+AI, AO = 1.05, 2.95
+# a wrong operator (transposed, mis-signed, wrong offset or level) is off by
+# O(1); the bars sit about 3x above each mode's rounding as measured on a
+# GB300 (worst level: FP32 1.5e-6, TF32x3 1.4e-6, BF16x3 6.2e-6; BF16x3
+# splits every M2L operand to 16 significant bits)
+BAR = {N.M2L_FP32: 5e-6, N.M2L_TF32X3: 5e-6, N.M2L_BF16X3: 2e-5}
+CASES = {"cube_n1e4_p4": (wl.uniform_cube, 10_000, 4, 64, 1),
+         "gauss_n6000_p5": (wl.gaussian_mixture, 6_000, 5, 24, 2)}
+_oracle = {}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2303_08394_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def unit_kernel(t, s):
+    d = np.linalg.norm(t[:, None, :] - s[None, :, :], axis=2)
+    return 1.0 / d
+
+
+def oracle_run(case):
+    if case not in _oracle:
+        gen, n, p, ncrit, nrhs = CASES[case]
+        x, q = gen(n, 90, nrhs=nrhs)
+        K = ok.KIFMM(x, p, ncrit)
+        K.evaluate(q)
+        _oracle[case] = (x, q, K)
+    return _oracle[case]
+
+
+@pytest.mark.parametrize("mode", [N.M2L_FP32, N.M2L_TF32X3, N.M2L_BF16X3],
+                         ids=["fp32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_each_pass_matches_the_oracle(case, mode):
+    _, _, p, ncrit, nrhs = CASES[case]
+    x, q, K = oracle_run(case)
+    plan = FMMPlan(x, p, ncrit, m2l_mode=mode)
+    qd = torch.as_tensor(q.astype(np.float32), device="cuda")
+    plan.evaluate(qd)
+    torch.cuda.synchronize()
+    ns, k = plan.info("nsurf"), plan.info("rank_m2l")
+    s = plan.array("surface").reshape(ns, 3)
+    Uk = plan.array("m2l_u").reshape(ns, k)
+    hw_root = plan.array("root")[3]
+    keys = [tuple(int(v) for v in r) for r in plan.array("node_keys").reshape(-1, 4)]
+    up, down = plan.workspace("up"), plan.workspace("down")
+    chat = plan.workspace("chat")
+    assert up.shape[:2] == (len(keys), nrhs) and chat.shape[2] >= k
+    assert {b for b in keys if b in K.m2l_check} == set(K.m2l_check)
+    k_up, k_dn = unit_kernel(AO * s, AI * s), unit_kernel(AI * s, AO * s)
+
+    acc = {}   # (pass, level) -> [sum |gpu - oracle|^2, sum |oracle|^2]
+
+    def add(name, level, got, ref):
+        e = acc.setdefault((name, level), [0.0, 0.0])
+        e[0] += float(np.sum((got - ref) ** 2))
+        e[1] += float(np.sum(ref ** 2))
+
+    for i, b in enumerate(keys):
+        if b[0] < 2:
+            continue
+        add("up", b[0], k_up @ up[i, :, :ns].T.astype(np.float64), k_up @ K.up[b])
+        add("down", b[0], k_dn @ down[i, :, :ns].T.astype(np.float64), k_dn @ K.down[b])
+        if b in K.m2l_check:
+            h = hw_root / 2.0 ** b[0]
+            got = Uk @ chat[i, :, :k].T.astype(np.float64) / (4.0 * np.pi * h)
+            add("m2l", b[0], got, K.m2l_check[b])
+    errs = {key: float(np.sqrt(e / r)) for key, (e, r) in acc.items()}
+    print(case, mode, {f"{a}@L{l}": f"{v:.2e}" for (a, l), v in sorted(errs.items())})
+    assert {a for a, _ in errs} == {"up", "down", "m2l"}
+    worst = max(errs.values())
+    assert worst <= BAR[mode], errs
