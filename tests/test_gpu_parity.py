@@ -203,3 +203,27 @@ def test_million_point_workload_sampled_against_direct_sum():
     # the zero-distance self pair is skipped, so these are Eq. (1) potentials
     ref = direct_sum(x, q[:, 0], targets=x[idx])
     assert rel(phi[idx], ref) <= 1e-5
+
+
+@pytest.mark.parametrize("p,n,ncrit", [(2, 3000, 16), (10, 1500, 32)], ids=["p2", "p10"])
+def test_extreme_orders_every_mode(p, n, ncrit):
+    """The smallest and largest expansion orders the ABI accepts: p = 2 (the
+    eight corners of the cube, M2L rank 8, one 16-wide tensor-core K step)
+    and p = 10 (488 surface points: the widest P2M and P2L blocks and the
+    largest M2L rank), in every M2L mode, against the oracle and the direct
+    sum with the bars above."""
+    x, q = wl.uniform_cube(n, 70)
+    q = q[:, 0]
+    ora = KIFMM(x, p, ncrit).evaluate(q)
+    ref = direct_sum(x, q)
+    e_ora = rel(ora, ref)
+    plan = FMMPlan(x, p, ncrit)
+    errs = {}
+    for mode, name in ((N.M2L_FP32, "fp32"), (N.M2L_TF32X3, "tf32x3"), (N.M2L_BF16X3, "bf16x3")):
+        plan.set_m2l_mode(mode)
+        phi = gpu_eval(plan, q)[:, 0]
+        errs[name] = (rel(phi, ora), rel(phi, ref))
+    print(p, "k", plan.info("rank_m2l"), "oracle vs direct", e_ora, errs)
+    assert errs["fp32"][0] <= 1e-6 and errs["tf32x3"][0] <= 1e-6, (e_ora, errs)
+    assert errs["bf16x3"][0] <= 1e-5, (e_ora, errs)
+    assert errs["fp32"][1] <= 1.5 * e_ora + FP32_FLOOR, (e_ora, errs)
