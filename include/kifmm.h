@@ -347,8 +347,24 @@ enum {
     FMM_ARRAY_M2L_ENTRY_OFFSET = 24,  /* int32 [entries]: offset index t in
                                          the order of FMM_ARRAY_M2L_S,
                                          increasing within a tile */
-    FMM_ARRAY_M2L_ENTRY_SRC = 25      /* int32 [entries][128]: source box of
+    FMM_ARRAY_M2L_ENTRY_SRC = 25,     /* int32 [entries][128]: source box of
                                          each row at that offset, -1 none */
+    /* FP64 operators of the unit box (half-width 1, kernel 1/r; "Upward
+     * pass" and "Downward pass" of the paper's operator list), row-major;
+     * rP = FMM_INFO_RANK_UP, rQ = FMM_INFO_RANK_DOWN, k = FMM_INFO_RANK_M2L,
+     * s the unit surface, c_sigma = ((sigma&1) - 1/2, (sigma>>1&1) - 1/2,
+     * (sigma>>2&1) - 1/2) the centre of child sigma. */
+    FMM_ARRAY_OP_PU = 26,  /* double [nsurf][rP]: K(a_out s, a_in s) = */
+    FMM_ARRAY_OP_PS = 27,  /* double [rP]:          Pu diag(Ps) Pv^T,   */
+    FMM_ARRAY_OP_PV = 28,  /* double [nsurf][rP]:   truncated SVD       */
+    FMM_ARRAY_OP_QU = 29,  /* double [nsurf][rQ]: K(a_in s, a_out s) = */
+    FMM_ARRAY_OP_QS = 30,  /* double [rQ]:          Qu diag(Qs) Qv^T    */
+    FMM_ARRAY_OP_QV = 31,  /* double [nsurf][rQ] */
+    FMM_ARRAY_OP_M2M = 32, /* double [8][rP][nsurf]: Pu^T K(a_out s,
+                              c_sigma + a_in s / 2) */
+    FMM_ARRAY_OP_L2L = 33, /* double [8][rQ][nsurf]: Qu^T K(c_sigma +
+                              a_in s / 2, a_out s) / 2 */
+    FMM_ARRAY_OP_QUK = 34  /* double [rQ][k]: Qu^T Uk */
 };
 /* Copy array `which` into dst (capacity `bytes`).  *needed receives the
  * size in bytes (may be NULL).  dst == NULL only queries the size. */

@@ -35,7 +35,9 @@ ARRAYS = {"node_keys": (0, "i4"), "node_range": (1, "i8"), "leaf_flag": (2, "i4"
           "output_row": (18, "i8"), "node_problem": (19, "i4"), "gemm_shapes": (20, "i4"),
           "m2l_tile_level": (21, "i4"), "m2l_tile_target": (22, "i4"),
           "m2l_tile_entry_ptr": (23, "i4"), "m2l_entry_offset": (24, "i4"),
-          "m2l_entry_src": (25, "i4")}
+          "m2l_entry_src": (25, "i4"), "op_pu": (26, "f8"), "op_ps": (27, "f8"),
+          "op_pv": (28, "f8"), "op_qu": (29, "f8"), "op_qs": (30, "f8"), "op_qv": (31, "f8"),
+          "op_m2m": (32, "f8"), "op_l2l": (33, "f8"), "op_quk": (34, "f8")}
 
 # every symbol include/kifmm.h declares
 EXPORTS = ("fmm_options_init", "fmm_plan_create", "fmm_plan_create_ex",

@@ -1361,6 +1361,15 @@ fmm_status fmm_plan_get_array(fmm_plan_t P, int which, void *dst, int64_t bytes,
         src = t.node_problem.data();
         size = t.node_problem.size() * 4;
         break;
+    case FMM_ARRAY_OP_PU: src = o.Pu.data(); size = o.Pu.size() * 8; break;
+    case FMM_ARRAY_OP_PS: src = o.Ps.data(); size = o.Ps.size() * 8; break;
+    case FMM_ARRAY_OP_PV: src = o.Pv.data(); size = o.Pv.size() * 8; break;
+    case FMM_ARRAY_OP_QU: src = o.Qu.data(); size = o.Qu.size() * 8; break;
+    case FMM_ARRAY_OP_QS: src = o.Qs.data(); size = o.Qs.size() * 8; break;
+    case FMM_ARRAY_OP_QV: src = o.Qv.data(); size = o.Qv.size() * 8; break;
+    case FMM_ARRAY_OP_M2M: src = o.M2M.data(); size = o.M2M.size() * 8; break;
+    case FMM_ARRAY_OP_L2L: src = o.L2L.data(); size = o.L2L.size() * 8; break;
+    case FMM_ARRAY_OP_QUK: src = o.QUk.data(); size = o.QUk.size() * 8; break;
     case FMM_ARRAY_M2L_TILE_LEVEL:
         src = P->m2l.tile_level.data();
         size = P->m2l.tile_level.size() * 4;
