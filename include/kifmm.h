@@ -92,8 +92,10 @@ void fmm_options_init(fmm_options *opts);
  * On-disk cache of the FP64 operator precomputation (surfaces, factored
  * pseudo-inverses, M2M/L2L, the compressed M2L factors), which depends only
  * on (p, alpha_inner, alpha_outer, rcond, eps_svd) and takes seconds at
- * p >= 6.  The paper likewise computes its operators once and loads them
- * from files ("Parallelization strategies for FMM operators").
+ * p >= 6.  The paper likewise precomputes the M2M and L2L matrices once
+ * ("Parallelization strategies for FMM operators") and keeps trees and
+ * precomputed quantities in a database ("Data-oriented design of
+ * PyExaFMM").
  *
  * dir      an existing directory, or NULL / "" to turn the cache off (the
  *          default).  Process-wide; affects plans created afterwards.
@@ -349,8 +351,9 @@ enum {
                                          increasing within a tile */
     FMM_ARRAY_M2L_ENTRY_SRC = 25,     /* int32 [entries][128]: source box of
                                          each row at that offset, -1 none */
-    /* FP64 operators of the unit box (half-width 1, kernel 1/r; "Upward
-     * pass" and "Downward pass" of the paper's operator list), row-major;
+    /* FP64 operators of the unit box (half-width 1, kernel 1/r): the
+     * matrices behind P2M, M2M, L2L and M2L ("Computational structure of
+     * FMM operators": bottom-up M2M, top-down M2L and L2L), row-major;
      * rP = FMM_INFO_RANK_UP, rQ = FMM_INFO_RANK_DOWN, k = FMM_INFO_RANK_M2L,
      * s the unit surface, c_sigma = ((sigma&1) - 1/2, (sigma>>1&1) - 1/2,
      * (sigma>>2&1) - 1/2) the centre of child sigma. */
@@ -380,7 +383,8 @@ fmm_status fmm_plan_get_array(fmm_plan_t plan, int which, void *dst,
  * (h_B and y in the caller's length unit, s the unit surface
  * FMM_ARRAY_SURFACE):
  *   FMM_WORK_UP    upward equivalent densities rho, a = alpha_inner
- *                  ("Upward pass": P2M at leaves, M2M above), boxes of
+ *                  (P2M at leaves, M2M above: "Computational structure
+ *                  of FMM operators"), boxes of
  *                  level >= 2; ld = nsurf rounded up to 4;
  *   FMM_WORK_DOWN  downward equivalent densities, a = alpha_outer (after
  *                  M2L, P2L and L2L), boxes of level >= 2; ld as UP;

@@ -195,9 +195,10 @@ std::shared_ptr<Operators> compute(int p, double ai, double ao, double rcond,
 
 // ------------------------------------------------------------ file cache
 // The precomputation depends only on (p, ai, ao, rcond, eps_svd), so it is
-// done once and kept, as the paper keeps its precomputed operators in files
-// ("Parallelization strategies for FMM operators": operators are computed
-// once and reused).  A cache file holds, little-endian:
+// done once and kept: the paper precomputes the M2M and L2L matrices
+// ("Parallelization strategies for FMM operators") and keeps its
+// precomputed quantities in a database ("Data-oriented design of
+// PyExaFMM").  A cache file holds, little-endian:
 //   "KIFMMOPS", u32 format, u32 byte-order mark 0x01020304,
 //   i32 p, f64 ai, ao, rcond, eps_svd (the key, compared bit for bit),
 //   i32 ns, rP, rQ, k, then each array as i64 count + f64 values, in the
