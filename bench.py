@@ -34,6 +34,16 @@ UNIT = "points/s"
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
 CPU_SAMPLE_N = 40_000
+# --impl reference: the whole run (warm-up + timed steps) is held to about
+# this many seconds by shrinking each step's sample as the step count grows
+# (the oracle evaluates about 1e4 points/s on one host core at p = 6), with
+# at least REF_MIN_N points so the sample still has a level-2 M2L
+REF_BUDGET_S = 150.0
+REF_MIN_N = 4_000
+
+
+def reference_sample_n(reps):
+    return max(REF_MIN_N, min(CPU_SAMPLE_N, int(REF_BUDGET_S * 1e4 / max(reps, 1))))
 # DRAM bytes (read + write) of one launch, from the ncu captures summarised
 # in profiles/ (k_m2l_tc_cube_n1e6_p6_bf16x3.md, k_eval_cube_n1e6_p6.md).
 # Keyed by kernel, workload, M2L mode and M2L operand width (kpad; the leaf
@@ -272,7 +282,7 @@ def main():
         if rank != 0:
             return
         reps = a.warmup + a.steps
-        res = run_oracle(a.workload, CPU_SAMPLE_N, reps)
+        res = run_oracle(a.workload, reference_sample_n(reps), reps)
         times = res["times"][a.warmup:]
         total = sum(times)
         value = res["n"] * res["nrhs"] * len(times) / total
