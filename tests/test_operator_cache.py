@@ -131,3 +131,23 @@ def test_directory_argument_is_checked(tmp_path):
     set_operator_cache(tmp_path)
     set_operator_cache(None)
     assert N.lib().fmm_set_operator_cache(b"") == N.FMM_OK
+
+
+def test_concurrent_writers_leave_one_whole_file(tmp_path):
+    """Four processes that miss the cache at once all compute and write the
+    same key; the renames leave one whole file, which a fifth reads."""
+    d = tmp_path / "ops"
+    d.mkdir()
+    env = dict(os.environ, PYTHONPATH=ROOT, OMP_NUM_THREADS="2")
+    procs = [subprocess.Popen([sys.executable, "-c", CHILD, str(d), "5", "1e-7",
+                               str(tmp_path / f"w{i}.npz")],
+                              stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env,
+                              cwd=ROOT) for i in range(4)]
+    outs = [p.communicate(timeout=300) for p in procs]
+    assert all(p.returncode == 0 for p in procs), [e for _, e in outs]
+    assert len(cache_files(d)) == 1 and not [f for f in os.listdir(d) if ".tmp." in f]
+    info, arrays = plan_in_child(d, 5, 1e-7, tmp_path / "r.npz")
+    assert info["source"] == 2
+    with np.load(tmp_path / "w0.npz") as z:
+        for k in ARRAYS:
+            assert z[k].tobytes() == arrays[k].tobytes(), k
