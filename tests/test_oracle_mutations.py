@@ -65,3 +65,39 @@ def test_wrong_v_definition_breaks_coverage():
         bad_v[b] = out
     assert _coverage(tree, (U, V, W, X)) == 0
     assert _coverage(tree, (U, bad_v, W, X)) > 0
+
+
+def test_gradient_kernel_sign_fails(monkeypatch):
+    """A sign error in the kernel's target-gradient: the KIFMM gradient then
+    disagrees with the direct gradient (itself pinned by central
+    differences of the direct potential)."""
+    from oracle.direct import direct_gradient
+    x, q, _ = _sphere()
+    ref = direct_gradient(x, q)
+    f = kifmm.KIFMM(x, 5, 12)
+    _, good = f.evaluate(q, gradient=True)
+    assert rel(good, ref) < 3e-4
+    flipped = kifmm.laplace_gradient_kernel
+    monkeypatch.setattr(kifmm, "laplace_gradient_kernel", lambda t, s: -flipped(t, s))
+    _, bad = f.evaluate(q, gradient=True)
+    assert rel(bad, ref) > 1e-1
+
+
+def test_dropped_l2l_fails(monkeypatch):
+    """Every box's parent reported at level 1 during the evaluation: the
+    downward pass loses every L2L term below level 2."""
+    x, q, ref = _sphere()
+    f = kifmm.KIFMM(x, 5, 12)       # tree and lists built with the true parents
+    monkeypatch.setattr(kifmm, "_parent", lambda key: (1, 0, 0, 0))
+    assert rel(f.evaluate(q), ref) > 1e-3
+
+
+def test_wrong_level_width_fails(monkeypatch):
+    """Surfaces sized for the level below (half the box): the check and
+    equivalent surfaces no longer enclose what they represent."""
+    x, q, ref = _sphere()
+    f = kifmm.KIFMM(x, 5, 12)
+    true_width = kifmm.Octree.box_half_width
+    monkeypatch.setattr(kifmm.Octree, "box_half_width",
+                        lambda self, level: true_width(self, level + 1))
+    assert rel(f.evaluate(q), ref) > 1e-3
