@@ -287,3 +287,27 @@ def test_workspace_export_needs_an_evaluation():
     assert L.fmm_plan_get_workspace(P._h, 0, None, 0, ctypes.byref(need)) == N.FMM_ERR_INVALID_ARG
     assert "no evaluation" in L.fmm_last_error().decode()
     assert L.fmm_plan_get_workspace(None, 0, None, 0, None) == N.FMM_ERR_INVALID_ARG
+
+
+def test_python_constants_match_the_header():
+    """Every info key, array id, option key, workspace id, status and M2L mode
+    the header declares has the same value in the Python binding, and the
+    binding names no key the header lacks."""
+    header = open(os.path.join(ROOT, "include", "kifmm.h")).read()
+
+    def enum(prefix):
+        return {m.group(1).lower(): int(m.group(2))
+                for m in re.finditer(r"\b" + prefix + r"([A-Z0-9_]+)\s*=\s*(\d+)", header)}
+
+    assert enum("FMM_INFO_") == N.INFO
+    assert enum("FMM_ARRAY_") == {k: v[0] for k, v in N.ARRAYS.items()}
+    for name, value in enum("FMM_OPT_").items():
+        assert getattr(N, "OPT_" + name.upper()) == value, name
+    for name, value in enum("FMM_ERR_").items():
+        assert getattr(N, "FMM_ERR_" + name.upper()) == value, name
+    for name, value in enum("FMM_M2L_").items():
+        assert getattr(N, "M2L_" + name.upper()) == value, name
+    for name, value in enum("FMM_TREE_").items():
+        assert getattr(N, "TREE_" + name.upper()) == value, name
+    assert enum("FMM_WORK_") == {"up": 0, "down": 1, "qhat": 2, "chat": 3}
+    assert N.FMM_OK == 0
