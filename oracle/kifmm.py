@@ -87,7 +87,8 @@ def laplace_kernel(targets, sources):
 
 
 def laplace_gradient_kernel(targets, sources):
-    """G[i, j, :] = (s_j - t_i) / (4 pi |t_i - s_j|^3): the gradient of
+    """Eq. (1) differentiated in the target (the paper evaluates potentials only;
+    a reading for the gradient extension).  G[i, j, :] = (s_j - t_i) / (4 pi |t_i - s_j|^3): the gradient of
     laplace_kernel's entry with respect to the target position t_i; zero
     where t_i == s_j."""
     t = np.asarray(targets, dtype=np.float64).reshape(-1, 3)
@@ -118,7 +119,9 @@ def surface_grid(p: int):
 
 
 def pinv(matrix, rcond=1e-7):
-    """Pseudo-inverse through the SVD, dropping sigma < rcond * sigma_max."""
+    """Check-to-equivalent inversion ("Computational structure of FMM
+    operators": expansions from check potentials; the method is silent on
+    the cutoff, a reading).  Pseudo-inverse through the SVD, dropping sigma < rcond * sigma_max."""
     return np.linalg.pinv(matrix, rcond=rcond)
 
 
@@ -127,7 +130,8 @@ def pinv(matrix, rcond=1e-7):
 # ----------------------------------------------------------------------------
 
 def _adjacent(ka, kb):
-    """Closed boxes ka, kb (level, i, j, k) touch or overlap."""
+    """Adjacency, on which every interaction list rests ("Computational
+    structure of FMM operators").  Closed boxes ka, kb (level, i, j, k) touch or overlap."""
     la, lb = ka[0], kb[0]
     L = max(la, lb)
     sa, sb = L - la, L - lb
@@ -140,11 +144,14 @@ def _adjacent(ka, kb):
 
 
 def _parent(key):
+    """The box one level up ("The Fast Multipole Method": each box is one of
+    its parent's 8 equal parts)."""
     l, i, j, k = key
     return (l - 1, i >> 1, j >> 1, k >> 1)
 
 
 def _children(key):
+    """The 8 equal parts of a box ("The Fast Multipole Method")."""
     l, i, j, k = key
     return [(l + 1, 2 * i + cx, 2 * j + cy, 2 * k + cz)
             for cz in (0, 1) for cy in (0, 1) for cx in (0, 1)]
@@ -191,7 +198,8 @@ class Octree:
         self.depth = max(k[0] for k in self.nonempty)
 
     def _split(self, key, stack=None):
-        """Create all 8 children of ``key`` and hand them its points."""
+        """("The Fast Multipole Method": a box is subdivided into 8 equal parts
+        while it holds more than ncrit points.)  Create all 8 children of ``key`` and hand them its points."""
         l = key[0]
         idx = self.points[key]
         self.leaf[key] = False
@@ -206,7 +214,9 @@ class Octree:
                 stack.append((child, sel))
 
     def _balance(self):
-        """Refine leaves until adjacent leaves differ by at most one level.
+        """The balance condition of "Computational structure of FMM
+        operators" (neighbouring leaves at most twice as large as each other).
+        Refine leaves until adjacent leaves differ by at most one level.
         A leaf at level l violates the condition exactly when an internal box
         at level l+1 touches it."""
         changed = True
@@ -237,14 +247,18 @@ class Octree:
 
     # geometry -----------------------------------------------------------
     def box_half_width(self, level):
+        """Half-width of the boxes of a level: the root's halved once per level
+        ("The Fast Multipole Method")."""
         return self.half_width / float(1 << level)
 
     def box_centre(self, key):
+        """Centre of a box from its level and integer coordinates."""
         l = key[0]
         h = self.box_half_width(l)
         return self.corner + (2.0 * np.array(key[1:], dtype=np.float64) + 1.0) * h
 
     def is_leaf(self, key):
+        """Whether the box was left unsplit by the splitting and the balancing."""
         return self.leaf[key]
 
 
@@ -253,7 +267,9 @@ class Octree:
 # ----------------------------------------------------------------------------
 
 def _colleagues(tree, key):
-    """Non-empty boxes at the same level touching ``key`` (``key`` included)."""
+    """Non-empty boxes at the same level touching ``key`` (``key``
+    included): the same-level neighbours the lists of "Computational
+    structure of FMM operators" are built from."""
     l, i, j, k = key
     out = []
     for a, b, c in itertools.product((-1, 0, 1), repeat=3):
@@ -264,7 +280,8 @@ def _colleagues(tree, key):
 
 
 def build_lists(tree):
-    """U, V, W, X lists (dicts: box -> sorted list of boxes), as defined in
+    """The U, V, W and X lists of "Computational structure of FMM
+    operators" (the inputs of the near field, M2L, M2P and P2L).  U, V, W, X lists (dicts: box -> sorted list of boxes), as defined in
     the module docstring."""
     leaves = tree.leaves
     U, V, W, X = {}, {}, {}, {}
@@ -356,11 +373,15 @@ class KIFMM:
 
     # surfaces of a box ----------------------------------------------------
     def _surface(self, key, alpha):
+        """Check or equivalent surface of a box ("Computational structure of
+        FMM operators": 6(p-1)^2 + 2 points): the unit surface scaled by
+        alpha times the half-width and moved to the box centre."""
         h = self.tree.box_half_width(key[0])
         return self.tree.box_centre(key) + alpha * h * self.surf
 
     def _m2l_matrix(self, b, a):
-        """K(DC_b, UE_a).  It depends only on the level and the integer offset
+        """The M2L's kernel evaluation between surfaces ("Computational
+        structure of FMM operators": M2L over V).  K(DC_b, UE_a).  It depends only on the level and the integer offset
         a - b, so it is computed once per (level, offset) from that offset
         (a memo, not a change of the arithmetic)."""
         l = b[0]
@@ -376,7 +397,10 @@ class KIFMM:
         return m
 
     def evaluate(self, charges, gradient=False):
-        """Potentials at the points; with gradient=True also their gradients
+        """The operators in the order of "The Fast Multipole Method" (bottom-up,
+        then top-down) and "Computational structure of FMM operators" (M2L and
+        L2L from level 2 down, then near field, L2P and M2P at the leaves).
+        Potentials at the points; with gradient=True also their gradients
         with respect to the target position, (n, 3) or (n, nrhs, 3): the
         leaf step applies the target-gradient of the kernel to the same
         sources and densities (near field over U, L2P, M2P); the upward and
