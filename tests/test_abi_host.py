@@ -311,3 +311,47 @@ def test_python_constants_match_the_header():
         assert getattr(N, "TREE_" + name.upper()) == value, name
     assert enum("FMM_WORK_") == {"up": 0, "down": 1, "qhat": 2, "chat": 3}
     assert N.FMM_OK == 0
+
+
+@pytest.mark.parametrize("label,kw,fragment", [
+    ("+inf", {"inf": np.inf}, "non-finite"), ("-inf", {"inf": -np.inf}, "non-finite"),
+    ("nan target", {"nan_target": True}, "non-finite"),
+    ("p = 11", {"p": 11}, "p must be in [2, 10]"),
+    ("max_level 17", {"max_level": 17}, "max_level"), ("max_level -1", {"max_level": -1}, "max_level"),
+    ("radii swapped", {"alpha_inner": 2.95, "alpha_outer": 1.05}, "alpha_inner"),
+    ("alpha_inner <= 1", {"alpha_inner": 0.5}, "alpha_inner"),
+    ("rcond < 0", {"rcond": -1.0}, "rcond"), ("eps_svd < 0", {"eps_svd": -1.0}, "eps_svd"),
+    ("eps_svd nan", {"eps_svd": float("nan")}, "eps_svd"),
+])
+def test_invalid_plan_arguments_are_refused_with_a_message(label, kw, fragment):
+    x, _ = wl.uniform_cube(50, 3)
+    kw = dict(kw)
+    p = kw.pop("p", 4)
+    targets = None
+    if "inf" in kw:
+        x = x.copy()
+        x[2, 0] = kw.pop("inf")
+    if kw.pop("nan_target", False):
+        targets = x.copy()
+        targets[1, 2] = np.nan
+    with pytest.raises(N.FMMError) as e:
+        FMMPlan(x, p, 8, targets=targets, host_only=1, **kw)
+    assert e.value.status == N.FMM_ERR_INVALID_ARG
+    assert fragment in str(e.value), (label, str(e.value))
+
+
+def test_null_and_negative_arguments():
+    x, _ = wl.uniform_cube(50, 3)
+    pts = np.ascontiguousarray(x)
+    L = N.lib()
+    h = ctypes.c_void_p()
+    assert L.fmm_plan_create(None, None, 10, 4, 8, ctypes.byref(h)) == N.FMM_ERR_INVALID_ARG
+    assert L.fmm_plan_create(pts.ctypes.data, None, 50, 4, 8, None) == N.FMM_ERR_INVALID_ARG
+    assert L.fmm_plan_create(pts.ctypes.data, None, -5, 4, 8, ctypes.byref(h)) == N.FMM_ERR_INVALID_ARG
+    assert not h.value
+    P = FMMPlan(x, 4, 8, host_only=1)
+    assert L.fmm_plan_info(P._h, 0, None) == N.FMM_ERR_INVALID_ARG
+    assert L.fmm_plan_set_option(P._h, 99, 1.0) == N.FMM_ERR_INVALID_ARG
+    assert L.fmm_plan_set_option(P._h, N.OPT_M2L_MODE, 7.0) == N.FMM_ERR_INVALID_ARG
+    assert L.fmm_plan_set_option(P._h, N.OPT_GEMM_SHAPE, 5.0) == N.FMM_ERR_INVALID_ARG
+    FMMPlan(x, 10, 8, host_only=1)          # the largest order is accepted
