@@ -354,4 +354,3 @@ def test_null_and_negative_arguments():
     assert L.fmm_plan_set_option(P._h, 99, 1.0) == N.FMM_ERR_INVALID_ARG
     assert L.fmm_plan_set_option(P._h, N.OPT_M2L_MODE, 7.0) == N.FMM_ERR_INVALID_ARG
     assert L.fmm_plan_set_option(P._h, N.OPT_GEMM_SHAPE, 5.0) == N.FMM_ERR_INVALID_ARG
-    FMMPlan(x, 10, 8, host_only=1)          # the largest order is accepted
