@@ -1,19 +1,22 @@
 #!/usr/bin/env python
 """Benchmark: Laplace KIFMM points/s on one GB300 (or N independent ones).
 
-Workload (default): 10^6 points uniform in the unit cube, charges uniform in
-[-1, 1], p = 6, ncrit = 150, adaptive octree; M2L compression tolerance
-eps_svd = 5e-7 (rank k = 127, operand width 128; the error against the
-direct sum is set by p: 5.26e-6 here against 5.24e-6 at eps_svd = 1e-7, k = 143).  One step is one full
-``fmm_evaluate`` (every operator, the M2L and P2P hot path included) with
-inputs resident in device memory, replayed as a CUDA graph on a side
-stream; L2 is flushed (256 MB write) before every timed step, outside the
-timed events.  The headline runs the M2L in BF16x3 split precision on the
-tensor cores (mixed); the plain FP32 path is timed on the same plan with
-the same protocol and reported beside it.
+Workload (default): 4*10^6 points uniform on the unit sphere (a strongly
+adaptive octree), charges N(0, 1), p = 7, ncrit = 128; M2L compression
+tolerance eps_svd = 1e-6 (rank k = 122, operand width 128; the error against
+the direct sum is set by p).  One step is one full ``fmm_evaluate`` (every
+operator, the M2L and P2P hot path included) with inputs resident in device
+memory, replayed as a CUDA graph on a side stream; L2 is flushed (256 MB
+write) before every timed step, outside the timed events.  The headline
+runs the M2L in BF16x3 split precision on the tensor cores (mixed); the
+plain FP32 path and the TF32x3 split (FP32-like accuracy) are timed on the
+same plan with the same protocol and reported beside it, each with its
+relative L2 error against the FP64 direct sum on 1,000 sampled targets.
 
-Printed: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
-oracle on a bounded sample of the same workload instead.
+``--workload cube_n1e6_p6_ncrit150`` (and the other named workloads) runs
+another configuration.  Printed: one JSON line (rank 0).  ``--impl
+reference`` times the FP64 CPU oracle on bounded samples of the same
+workload on every host core instead.
 """
 from __future__ import annotations
 
@@ -29,54 +32,64 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "Laplace FMM points/s at rel L2 err \u22641e-5, mixed vs FP32; M2L % tensor peak"
+METRIC = "Laplace FMM points/s at rel L2 err ≤1e-5, mixed vs FP32; M2L % tensor peak"
 UNIT = "points/s"
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
-CPU_SAMPLE_N = 40_000
+DEFAULT_WORKLOAD = "sphere_n4e6_p7_ncrit128"
+# M2L compression tolerance per workload: the largest that keeps the error
+# against the direct sum where p puts it and gives an operand width of 128
+# (k = 127 at p = 6, 122 at p = 7, 124 at p = 8)
+EPS_SVD = {"cube_n1e6_p6_ncrit150": 5e-7, "cube_n1e6_p6_ncrit150_nrhs64": 5e-7,
+           "sphere_n4e6_p7_ncrit128": 1e-6, "gauss8_n1.6e7_p8_ncrit128_nrhs8": 1e-6}
+# CPU oracle samples: points per worker process (one process per host core)
+CPU_SAMPLE_N = 20_000
 # --impl reference: the whole run (warm-up + timed steps) is held to about
 # this many seconds by shrinking each step's sample as the step count grows
-# (the oracle evaluates about 1e4 points/s on one host core at p = 6), with
-# at least REF_MIN_N points so the sample still has a level-2 M2L
-REF_BUDGET_S = 150.0
+# (the oracle evaluates about 4e3-1e4 points/s per core), with at least
+# REF_MIN_N points so the sample still has a level-2 M2L
+REF_BUDGET_S = 120.0
 REF_MIN_N = 4_000
 
 
-def reference_sample_n(reps):
-    return max(REF_MIN_N, min(CPU_SAMPLE_N, int(REF_BUDGET_S * 1e4 / max(reps, 1))))
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def reference_sample_n(reps, rate=4e3):
+    return max(REF_MIN_N, min(CPU_SAMPLE_N, int(REF_BUDGET_S * rate / max(reps, 1))))
+
+
 # DRAM bytes (read + write) of one launch, from the ncu captures summarised
-# in profiles/ (k_m2l_tc_cube_n1e6_p6_bf16x3.md, k_eval_cube_n1e6_p6.md).
-# Keyed by kernel, workload, M2L mode and M2L operand width (kpad; the leaf
-# kernel does not depend on it: None); any other combination reports null.
-TRAFFIC = {
-    # dram read + write of one launch (profiles/k_m2l_tc_cube_n1e6_p6_bf16x3.md)
-    ("k_m2l_tc", "cube_n1e6_p6_ncrit150", "bf16x3", 128): 77.2e6,
-    # the leaf pass: its four width-group launches together
-    ("k_eval", "cube_n1e6_p6_ncrit150", "bf16x3", None): 90.6e6,
-    # the gradient variant (profiles/k_eval_gradient_cube_n1e6_p6.md)
-    ("k_eval_grad", "cube_n1e6_p6_ncrit150", "bf16x3", None): 117.1e6,
-    ("k_eval", "cube_n1e6_p6_ncrit150", "fp32", None): 90.6e6,
-    ("k_eval", "cube_n1e6_p6_ncrit150", "tf32x3", None): 90.6e6,
-}
+# in profiles/.  Keyed by kernel, workload, M2L mode and M2L operand width
+# (kpad; the leaf kernel does not depend on it: None); any other combination
+# reports null.
+TRAFFIC = {}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="cube_n1e6_p6_ncrit150")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--m2l", default="bf16x3", choices=["fp32", "bf16x3", "tf32x3"])
-    ap.add_argument("--eps-svd", type=float, default=5e-7,
-                    help="M2L compression tolerance (rank: singular values above eps * max)")
+    ap.add_argument("--eps-svd", type=float, default=None,
+                    help="M2L compression tolerance (rank: singular values above eps * max); "
+                         "default per workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error-check", action="store_true")
     ap.add_argument("--quick", action="store_true",
-                    help="timed steps only: no CPU baseline, error gate or e2e leg")
+                    help="timed steps only: no other legs, CPU baseline, error gate or e2e")
     a = ap.parse_args()
     if a.quick:
         a.no_cpu_baseline = a.no_error_check = True
+    if a.eps_svd is None:
+        a.eps_svd = EPS_SVD.get(a.workload, 1e-7)
     return a
 
 
@@ -113,44 +126,129 @@ def load_peaks():
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle leg (cpu_baseline and --impl reference)
+# CPU oracle legs (cpu_baseline and --impl reference).  The oracle runs as
+# it stands: one single-threaded process per host core, each evaluating its
+# own seeded sample of the workload's distribution; they start their timed
+# evaluations together (a barrier on stdin) and the throughput is the points
+# all of them evaluated over the wall time until the last one finished.
 # ---------------------------------------------------------------------------
-_ORACLE_STEP = r"""
+_ORACLE_WORKER = r"""
 import json, sys, time
 sys.path.insert(0, {root!r})
 from oracle.kifmm import KIFMM
 from paper_2303_08394_gb300 import workloads as wl
 w = wl.WORKLOADS[{workload!r}]
 gen = {{"cube": wl.uniform_cube, "sphere": wl.sphere_surface, "gauss": wl.gaussian_mixture}}[w.kind]
-x, q = gen({n}, 0, w.nrhs)
+x, q = gen({n}, {seed}, w.nrhs)
 f = KIFMM(x, w.p, w.ncrit)
-times = []
-for i in range({reps}):
-    t0 = time.perf_counter()
-    f.evaluate(q)
-    times.append(time.perf_counter() - t0)
-print(json.dumps({{"times": times, "n": {n}, "nrhs": w.nrhs}}))
+out = {{"n": {n}, "nrhs": w.nrhs, "depth": f.tree.depth, "warm": [], "timed": []}}
+for phase, reps in (("warm", {warm}), ("timed", {reps})):
+    print("ready", flush=True)
+    sys.stdin.readline()
+    for i in range(reps):
+        t0 = time.perf_counter()
+        f.evaluate(q)
+        out[phase].append(time.perf_counter() - t0)
+print(json.dumps(out), flush=True)
 """
 
 
-def run_oracle(workload, n, reps):
+def run_oracle_workers(workload, n, warm, reps, workers):
+    """`workers` concurrent oracle processes (seeds 0..workers-1), `warm`
+    untimed then `reps` timed evaluations each; returns (wall seconds of the
+    timed evaluations, per-worker results)."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
-    code = _ORACLE_STEP.format(root=ROOT, workload=workload, n=n, reps=reps)
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
-    if r.returncode:
-        raise RuntimeError("oracle run failed:\n" + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+    procs = []
+    for s in range(workers):
+        code = _ORACLE_WORKER.format(root=ROOT, workload=workload, n=n, seed=s, warm=warm,
+                                     reps=reps)
+        procs.append(subprocess.Popen([sys.executable, "-c", code], stdin=subprocess.PIPE,
+                                      stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                      text=True, env=env))
+
+    def barrier():
+        for p in procs:
+            line = p.stdout.readline()
+            if line.strip() != "ready":
+                err = p.stderr.read()
+                for q in procs:
+                    q.kill()
+                raise RuntimeError("oracle worker failed:\n" + (line + err)[-2000:])
+        t = time.perf_counter()
+        for p in procs:
+            p.stdin.write("go\n")
+            p.stdin.flush()
+        return t
+
+    barrier()            # setup done: warm-up evaluations
+    t0 = barrier()       # warm-up done: timed evaluations
+    results = []
+    for p in procs:
+        out, err = p.communicate()
+        if p.returncode:
+            raise RuntimeError("oracle worker failed:\n" + err[-2000:])
+        results.append(json.loads(out.strip().splitlines()[-1]))
+    return time.perf_counter() - t0, results
 
 
-def cpu_baseline(workload, w, reps=1):
-    res = run_oracle(workload, CPU_SAMPLE_N, reps)
-    t = statistics.median(res["times"])
-    return {"value": res["n"] * res["nrhs"] / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 numpy KIFMM (dense M2L) evaluate on {res['n']:,} points of the "
-                       f"same distribution, p={w.p}, ncrit={w.ncrit}; tree and operator setup "
-                       f"excluded; {t:.2f} s per evaluate")}
+_DIRECT_WORKER = r"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, {root!r})
+from oracle import direct
+from paper_2303_08394_gb300 import workloads as wl
+w = wl.WORKLOADS[{workload!r}]
+x, q = w.generate(0)
+idx = wl.sample_targets(w.n, {m}, 0)
+direct.build()
+t0 = time.perf_counter()
+phi = direct.direct_sum(x, q, targets=x[idx])
+t = time.perf_counter() - t0
+np.save({out!r}, phi)
+print(json.dumps({{"seconds": t, "threads": direct.num_threads(), "targets": len(idx)}}))
+"""
+
+
+def cpu_baseline(workload, w, ref_sampled=None):
+    """The oracle KIFMM on every host core (one process per core), plus the
+    oracle's OpenMP direct sum of Eq. (1) on the sampled targets of the full
+    workload (checked against the bench's own FP64 reference)."""
+    import numpy as np
+    cores = host_cores()
+    wall, res = run_oracle_workers(workload, CPU_SAMPLE_N, 0, 1, cores)
+    pts = sum(r["n"] * r["nrhs"] * len(r["timed"]) for r in res)
+    per = statistics.median(t for r in res for t in r["timed"])
+    line = {"value": pts / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"{cores} concurrent single-threaded processes of the FP64 numpy KIFMM "
+                       f"(dense M2L), each evaluating its own {CPU_SAMPLE_N:,}-point sample of "
+                       f"the workload's distribution (seeds 0..{cores - 1}, p={w.p}, "
+                       f"ncrit={w.ncrit}, tree depth {res[0]['depth']} against the full "
+                       f"workload's deeper tree); tree and operator setup excluded; "
+                       f"{per:.2f} s per evaluate, {wall:.2f} s wall for all")}
+    m = w.error_samples or 1000
+    with tempfile.TemporaryDirectory() as td:
+        out = os.path.join(td, "phi.npy")
+        env = dict(os.environ)
+        env["OMP_NUM_THREADS"] = str(cores)
+        r = subprocess.run([sys.executable, "-c", _DIRECT_WORKER.format(
+            root=ROOT, workload=workload, m=m, out=out)], capture_output=True, text=True, env=env)
+        if r.returncode == 0:
+            d = json.loads(r.stdout.strip().splitlines()[-1])
+            phi = np.load(out)
+            d["sources"] = w.n
+            d["pairs_per_s"] = w.n * d["targets"] / d["seconds"]
+            d["targets_per_s"] = d["targets"] / d["seconds"]
+            d["what"] = ("oracle/direct.c, FP64 O(N) sum per sampled target over all N sources, "
+                         "OpenMP over targets")
+            if ref_sampled is not None:
+                d["max_rel_diff_vs_bench_reference"] = float(
+                    np.max(np.abs(phi - ref_sampled)) / np.max(np.abs(ref_sampled)))
+            line["direct_sum"] = d
+        else:
+            line["direct_sum"] = {"error": r.stderr[-500:]}
+    return line
 
 
 # ---------------------------------------------------------------------------
@@ -203,33 +301,34 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# accuracy gate: FP64 direct sum of Eq. (1) on sampled targets (numpy)
+# accuracy gate: FP64 direct sum of Eq. (1) on sampled targets, computed with
+# plain torch FP64 operations on the GPU (sources in chunks); the CPU
+# baseline's OpenMP direct sum is checked against it
 # ---------------------------------------------------------------------------
-def direct_sum_sampled(x, q, idx, block=4):
+def _direct_sampled(x, q, idx, dev, gradient=False, chunk=1 << 15):
     import numpy as np
-    out = np.zeros((len(idx), q.shape[1]))
-    for s in range(0, len(idx), block):
-        t = idx[s:s + block]
-        d = x[None, :, :] - x[t][:, None, :]
-        r = np.sqrt(np.einsum("ijk,ijk->ij", d, d))
-        with np.errstate(divide="ignore"):
-            inv = np.where(r > 0, 1.0 / r, 0.0)
-        out[s:s + block] = inv @ q
-    return out / (4 * np.pi)
+    import torch
+    xs = torch.as_tensor(x, dtype=torch.float64, device=dev)
+    qs = torch.as_tensor(np.asarray(q, dtype=np.float64).reshape(len(x), -1), device=dev)
+    xt = xs[torch.as_tensor(idx, device=dev)]
+    out = torch.zeros((len(idx), 3 if gradient else qs.shape[1]), dtype=torch.float64,
+                      device=dev)
+    for s in range(0, len(x), chunk):
+        d = xs[None, s:s + chunk, :] - xt[:, None, :]          # (targets, sources, 3)
+        r = torch.sqrt((d * d).sum(-1))
+        inv = torch.where(r > 0, 1.0 / r, torch.zeros_like(r))
+        if gradient:
+            w3 = inv ** 3 * qs[s:s + chunk, 0][None, :]
+            out += torch.einsum("ij,ijk->ik", w3, d)
+        else:
+            out += inv @ qs[s:s + chunk]
+        del d, r, inv
+    return (out / (4 * np.pi)).cpu().numpy()
 
 
-def direct_gradient_sampled(x, q, idx, block=4):
-    """FP64 gradient of the direct sum at the sampled targets (numpy)."""
+def rel_l2(a, b):
     import numpy as np
-    out = np.zeros((len(idx), 3))
-    for s in range(0, len(idx), block):
-        t = idx[s:s + block]
-        d = x[None, :, :] - x[t][:, None, :]
-        r = np.sqrt(np.einsum("ijk,ijk->ij", d, d))
-        with np.errstate(divide="ignore"):
-            w3 = np.where(r > 0, 1.0 / r ** 3, 0.0) * q[None, :]
-        out[s:s + block] = np.einsum("ij,ijk->ik", w3, d)
-    return out / (4 * np.pi)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 # ---------------------------------------------------------------------------
@@ -267,6 +366,69 @@ def time_mode(plan, qd, out, flush, stream, steps, warmup, world, call=None):
     return [a.elapsed_time(b) for a, b in zip(starts, ends)], phases, launches
 
 
+def mean_phases(phases):
+    return {k: statistics.mean(ph[k] for ph in phases) for k in phases[0]}
+
+
+def reference_arm(a, w, config):
+    """--impl reference: the FP64 oracle KIFMM, as it stands, on every host
+    core (one process per core, each on its own bounded sample)."""
+    cores = host_cores()
+    n = reference_sample_n(a.warmup + a.steps)
+    wall, res = run_oracle_workers(a.workload, n, a.warmup, a.steps, cores)
+    pts = sum(r["n"] * r["nrhs"] * len(r["timed"]) for r in res)
+    value = pts / wall
+    sample = (f"{cores} concurrent single-threaded processes of the FP64 numpy KIFMM (dense "
+              f"M2L), each evaluating its own {n:,}-point sample of the workload's "
+              f"distribution per step (seeds 0..{cores - 1}); tree and operator setup "
+              f"excluded")
+    line = {"impl": "reference", "metric": METRIC, "value": value,
+            "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * wall / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def m2l_roofline(plan, mode, w, m2l_ms, peaks, peak_src, fp32_peak, sm_mhz):
+    """Roofline object of the M2L launch.  Useful flops: 2 k^2 per V pair and
+    right-hand side; the tensor-core modes issue three split products per
+    pair (counted in `achieved`), over tiles whose rows are not all filled
+    (`fill`: V pairs / rows the MMAs process; `mma_flops_per_launch` counts
+    the padded rows and the operand width kpad)."""
+    k = plan.info("rank_m2l")
+    kpad = (k + 15) // 16 * 16
+    v_pairs = plan.info("v_pairs")
+    entries = plan.info("m2l_entries")
+    useful = 2.0 * k * k * v_pairs * w.nrhs
+    fill = v_pairs / max(1, entries * 128)
+    if mode == "fp32":
+        tf = useful / (m2l_ms / 1e3) / 1e12
+        return {"kernel": "k_m2l_simt", "bound": "alu", "achieved": tf,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak,
+                "traffic": TRAFFIC.get(("k_m2l_simt", w.name, mode, kpad)),
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz",
+                "flops_per_launch": useful, "ms_per_launch": m2l_ms, "fill": fill}
+    tc_peak = peaks["bf16_tflops"] * (1.0 if mode == "bf16x3" else 0.5)
+    issued = 3 * useful
+    mma = 3 * 2.0 * kpad * kpad * 128 * entries * w.nrhs
+    return {"kernel": "k_m2l_tc", "bound": "tensor",
+            "achieved": issued / (m2l_ms / 1e3) / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
+            "frac": issued / (m2l_ms / 1e3) / 1e12 / tc_peak,
+            "traffic": TRAFFIC.get(("k_m2l_tc", w.name, mode, kpad)),
+            "peak_source": f"bf16_tflops of {peak_src} (burst)" +
+                           ("" if mode == "bf16x3" else " x 1/2 (tf32)"),
+            "flops_per_launch": issued, "useful_flops_per_launch": useful,
+            "useful_frac_of_bf16_peak": useful / (m2l_ms / 1e3) / 1e12 / peaks["bf16_tflops"],
+            "fill": fill, "mma_flops_per_launch": mma,
+            "mma_frac": mma / (m2l_ms / 1e3) / 1e12 / tc_peak,
+            "ms_per_launch": m2l_ms}
+
+
 def main():
     a = parse()
     rank, world, local = dist_env()
@@ -279,24 +441,8 @@ def main():
               "per_rank": "independent problem (seed = rank)"}
 
     if a.impl == "reference":
-        if rank != 0:
-            return
-        reps = a.warmup + a.steps
-        res = run_oracle(a.workload, reference_sample_n(reps), reps)
-        times = res["times"][a.warmup:]
-        total = sum(times)
-        value = res["n"] * res["nrhs"] * len(times) / total
-        line = {"impl": "reference", "metric": METRIC, "value": value,
-                "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
-                "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": config,
-                "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": f"FP64 numpy KIFMM evaluate on {res['n']:,} points "
-                                           f"of the workload's distribution per step"},
-                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                        "d2h_bytes_per_step": 0}}
-        print(json.dumps(line), flush=True)
+        if rank == 0:
+            reference_arm(a, w, config)
         return
 
     import numpy as np
@@ -333,27 +479,29 @@ def main():
     value = job_value(w.n * w.nrhs, a.steps, world, total_ms / 1e3)
 
     # accuracy gate on sampled targets (FP64 direct sum)
-    err = None
-    idx = ref = None
+    err = idx = ref = None
     if not a.no_error_check and rank == 0:
         idx = wl.sample_targets(w.n, w.error_samples or 1000, 0)
-        ref = direct_sum_sampled(x, q, idx)
         got = out.cpu().numpy()[idx]
-        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        ref = _direct_sampled(x, q, idx, dev)
+        err = rel_l2(got, ref)
 
-    # the plain FP32 path on the same plan, same protocol ("mixed vs FP32")
-    fp32 = None
-    if a.m2l != "fp32" and not a.quick:
-        plan.set_m2l_mode(N.M2L_FP32)
-        f_ms, f_ph, _ = time_mode(plan, qd, out, flush, stream, a.steps, a.warmup, world)
-        f_tot = max_over_ranks(sum(f_ms), world, dev)
-        fp32 = {"value": job_value(w.n * w.nrhs, a.steps, world, f_tot / 1e3),
-                "ms_per_step": f_tot / a.steps,
-                "m2l_ms": statistics.mean(ph["m2l"] for ph in f_ph)}
-        if ref is not None:
-            got = out.cpu().numpy()[idx]
-            fp32["rel_l2_err"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-        fp32["mixed_over_fp32"] = value / fp32["value"]
+    # the other M2L modes on the same plan, same protocol: the plain FP32
+    # path ("mixed vs FP32") and TF32x3 (FP32-like accuracy)
+    legs = {}
+    if not a.quick:
+        for name in ("fp32", "tf32x3", "bf16x3"):
+            if name == a.m2l:
+                continue
+            plan.set_m2l_mode(modes[name])
+            l_ms, l_ph, _ = time_mode(plan, qd, out, flush, stream, a.steps, a.warmup, world)
+            l_tot = max_over_ranks(sum(l_ms), world, dev)
+            leg = {"value": job_value(w.n * w.nrhs, a.steps, world, l_tot / 1e3),
+                   "ms_per_step": l_tot / a.steps, "phase_ms": mean_phases(l_ph)}
+            if ref is not None:
+                leg["rel_l2_err"] = rel_l2(out.cpu().numpy()[idx], ref)
+            leg["value_over_this_leg"] = value / leg["value"]
+            legs[name] = leg
         plan.set_m2l_mode(modes[a.m2l])
 
     # gradients of the potentials (fmm_evaluate_gradient), same protocol, the
@@ -361,7 +509,7 @@ def main():
     gradient = None
     if not a.quick and w.nrhs == 1:
         gout = torch.empty((w.n, 1, 3), dtype=torch.float64, device=dev)
-        g_steps = min(a.steps, 100)
+        g_steps = min(a.steps, 50)
         g_ms, g_ph, g_launch = time_mode(
             plan, qd, out, flush, stream, g_steps, a.warmup, world,
             call=lambda: plan.evaluate_gradient(qd, grad_out=gout, potentials=False,
@@ -369,56 +517,35 @@ def main():
         g_tot = max_over_ranks(sum(g_ms), world, dev)
         gradient = {"value": job_value(w.n, g_steps, world, g_tot / 1e3), "unit": UNIT,
                     "ms_per_step": g_tot / g_steps, "steps": g_steps,
-                    "phase_ms": {k: statistics.mean(ph[k] for ph in g_ph) for k in g_ph[0]},
-                    "gpu_launches": g_launch * g_steps}
+                    "phase_ms": mean_phases(g_ph), "gpu_launches": g_launch * g_steps}
         if idx is not None:
             got = gout.cpu().numpy()[idx, 0, :]
-            gref = direct_gradient_sampled(x, q[:, 0], idx)
-            gradient["rel_l2_err"] = float(np.linalg.norm(got - gref) / np.linalg.norm(gref))
+            gref = _direct_sampled(x, q, idx, dev, gradient=True)
+            gradient["rel_l2_err"] = rel_l2(got, gref)
 
-    # rooflines from the library's per-phase CUDA events (each phase below is
-    # one kernel launch on `stream`)
+    # rooflines from the library's per-phase CUDA events (each phase is
+    # timed on `stream`, the stream its kernels run on)
     peaks, peak_src = load_peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s
-    k = plan.info("rank_m2l")
-    kpad = (k + 15) // 16 * 16
-    v_pairs = plan.info("v_pairs")
     p2p_pairs = plan.info("p2p_pairs")
-    m2l_ms = statistics.mean(ph["m2l"] for ph in phases)
-    leaf_ms = statistics.mean(ph["leaf"] for ph in phases)
-    m2l_flops = 2.0 * k * k * v_pairs * w.nrhs
-    m2l_tf = m2l_flops / (m2l_ms / 1e3) / 1e12
+    ph = mean_phases(phases)
+    m2l_roof = m2l_roofline(plan, a.m2l, w, ph["m2l"], peaks, peak_src, fp32_peak, sm_mhz)
+    leaf_ms = ph["leaf"]
     near_flops = (8.0 + 2.0 * w.nrhs) * p2p_pairs
     leaf_tf = near_flops / (leaf_ms / 1e3) / 1e12
-    if a.m2l == "fp32":
-        m2l_roof = {"kernel": "k_m2l_simt", "bound": "alu", "achieved": m2l_tf,
-                    "peak": fp32_peak, "unit": "TFLOP/s", "frac": m2l_tf / fp32_peak,
-                    "traffic": TRAFFIC.get(("k_m2l_simt", w.name, a.m2l, kpad)),
-                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz",
-                    "flops_per_launch": m2l_flops, "ms_per_launch": m2l_ms}
-    else:
-        tc_peak = peaks["bf16_tflops"] * (1.0 if a.m2l == "bf16x3" else 0.5)
-        issued = 3 * m2l_flops
-        m2l_roof = {"kernel": "k_m2l_tc", "bound": "tensor",
-                    "achieved": issued / (m2l_ms / 1e3) / 1e12,
-                    "peak": tc_peak, "unit": "TFLOP/s",
-                    "frac": issued / (m2l_ms / 1e3) / 1e12 / tc_peak,
-                    "traffic": TRAFFIC.get(("k_m2l_tc", w.name, a.m2l, kpad)),
-                    "peak_source": f"bf16_tflops of {peak_src}" +
-                                   ("" if a.m2l == "bf16x3" else " x 1/2 (tf32)"),
-                    "flops_per_launch": issued, "useful_flops_per_launch": m2l_flops,
-                    "useful_frac_of_bf16_peak": m2l_flops / (m2l_ms / 1e3) / 1e12 /
-                    peaks["bf16_tflops"],
-                    "ms_per_launch": m2l_ms}
     leaf_roof = {"kernel": "k_eval", "bound": "alu", "achieved": leaf_tf, "peak": fp32_peak,
                  "unit": "TFLOP/s", "frac": leaf_tf / fp32_peak,
                  "traffic": TRAFFIC.get(("k_eval", w.name, a.m2l, None)),
+                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz "
+                                "(derived; no measured FP32 figure)",
                  "flops_per_launch": near_flops, "ms_per_launch": leaf_ms,
                  "note": "near-field pair flops only (8 + 2 nrhs per pair); L2P/M2P work "
-                         "uncounted; one leaf pass = one launch per leaf width group (T = 1..4 "
-                         "targets per lane), timed and counted together"}
-    dominant = m2l_roof if m2l_ms >= leaf_ms else leaf_roof
+                         "uncounted; the leaf pass is timed as one phase"}
+    dominant = m2l_roof if ph["m2l"] >= leaf_ms else leaf_roof
+    for name, leg in legs.items():
+        leg["roofline_m2l"] = m2l_roofline(plan, name, w, leg["phase_ms"]["m2l"], peaks,
+                                           peak_src, fp32_peak, sm_mhz)
     if gradient is not None:
         # potential + gradient: 8 (r^2, as above) + 2 (potential) + 3 (q / r^3)
         # + 6 (three FMAs) flops per near-field pair
@@ -430,8 +557,7 @@ def main():
                                 "frac": g_tf / fp32_peak,
                                 "traffic": TRAFFIC.get(("k_eval_grad", w.name, a.m2l, None)),
                                 "flops_per_launch": g_flops, "ms_per_launch": g_leaf,
-                                "note": "near-field pair flops only (19 per pair); one leaf "
-                                        "pass = one launch per leaf width group"}
+                                "note": "near-field pair flops only (19 per pair)"}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -446,18 +572,17 @@ def main():
                 "dtype": "f32" if a.m2l == "fp32" else f"f32 (M2L {a.m2l} split on tensor cores)",
                 "data": "synthetic", "config": config,
                 "rel_l2_err": err, "error_gate_1e-5": (err is not None and err <= 1e-5),
-                "fp32": fp32, "gradient": gradient,
+                "legs": legs, "fp32": legs.get("fp32"), "gradient": gradient,
                 "roofline": dominant, "rooflines": {"m2l": m2l_roof, "leaf": leaf_roof},
-                "phase_ms": {k2: statistics.mean(ph[k2] for ph in phases) for k2 in phases[0]},
-                "e2e": e2e,
+                "phase_ms": ph, "e2e": e2e,
                 "gpu_launches": launches_per_step * a.steps, "clocks": clk,
                 "plan_s": plan_s, "wall_s_timed_region": wall,
                 "tree": {key: plan.info(key) for key in
                          ("nodes", "leaves", "depth", "rank_m2l", "v_pairs", "u_pairs",
-                          "p2p_pairs", "m2l_tiles")},
+                          "p2p_pairs", "m2l_tiles", "m2l_entries")},
                 "peaks": peak_src}
         if world == 1 and not a.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(a.workload, w)
+            line["cpu_baseline"] = cpu_baseline(a.workload, w, ref)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

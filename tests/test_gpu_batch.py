@@ -20,6 +20,7 @@ from oracle.direct import direct_sum
 from oracle.kifmm import KIFMM
 from paper_2303_08394_gb300 import FMMPlan, _native as N
 from paper_2303_08394_gb300 import workloads as wl
+from tests.parity import ELEM_C_DIRECT, check
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -70,8 +71,8 @@ def test_batch_matches_each_problem(mode):
             if len(x) == 1:  # one point: no pair, potential 0
                 assert phi[i][0, r] == 0.0 and phi_s[0, r] == 0.0
                 continue
-            assert rel(phi[i][:, r], phi_o) <= BARS[mode], (i, r)
-            assert rel(phi[i][:, r], phi_s[:, r]) <= BARS[mode], (i, r)
+            check(phi[i][:, r], phi_o, BARS[mode], what=f"problem {i} column {r} vs oracle")
+            check(phi[i][:, r], phi_s[:, r], BARS[mode], what=f"problem {i} column {r} vs alone")
 
 
 def test_batch_upward_and_leaf_work_is_per_problem_exact():
@@ -101,6 +102,8 @@ def test_distinct_targets(mode):
     e_gpu_ora, e_gpu, e_ora = rel(phi, phi_o), rel(phi, ref), rel(phi_o, ref)
     assert e_gpu_ora <= BARS[mode], (e_gpu_ora, e_gpu, e_ora)
     assert e_gpu <= 1.5 * e_ora + FP32_FLOOR, (e_gpu, e_ora)
+    check(phi, phi_o, BARS[mode], what="distinct targets vs oracle")
+    check(phi, ref, 1.5 * e_ora + FP32_FLOOR, c=ELEM_C_DIRECT, what="distinct targets vs direct")
 
 
 def test_batch_with_distinct_targets_and_host_buffers():
@@ -109,10 +112,10 @@ def test_batch_with_distinct_targets_and_host_buffers():
     B = FMMPlan.batch([x0, x1], 5, 32, target_sets=[None, y1])
     q = np.concatenate([q0[:, 0], q1[:, 0]]).astype(np.float32)
     phi = B.split(B.evaluate(q))  # numpy in, numpy out (staged by the library)
-    assert rel(phi[0], KIFMM(x0, 5, 32).evaluate(q0[:, 0])) <= 1e-6
+    check(phi[0], KIFMM(x0, 5, 32).evaluate(q0[:, 0]), 1e-6, what="problem 0 vs oracle")
     u = np.vstack([x1, y1])
     ref1 = KIFMM(u, 5, 32).evaluate(np.concatenate([q1[:, 0], np.zeros(len(y1))]))[len(x1):]
-    assert rel(phi[1], ref1) <= 1e-6
+    check(phi[1], ref1, 1e-6, what="problem 1 (distinct targets) vs oracle")
 
 
 @pytest.mark.slow
@@ -130,3 +133,5 @@ def test_256_problem_batch_sampled_against_direct_sum(mode):
         got.append(phi[i][idx, 0])
     err = rel(np.concatenate(got), np.concatenate(ref))
     assert err <= 1e-5, err
+    check(np.concatenate(got), np.concatenate(ref), 1e-5, c=ELEM_C_DIRECT,
+          what="256 problems vs direct")

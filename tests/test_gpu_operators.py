@@ -18,7 +18,10 @@ along the pseudo-inverse's weakest directions, which the potentials damp:
 * down  (M2L, P2L and L2L through the downward pseudo-inverse):
   K(a_in s, a_out s) rho_down, every box of level >= 2.
 
-Errors are relative L2 over all boxes of a level.
+Errors are relative L2 over all boxes of a level; beside that bar, every
+single box is bounded: its L2 error is at most ELEM_C (8, as in
+tests/parity.py) times the bar times the root mean square of the reference
+norms over the level's boxes, so one wrong box cannot hide in a level's sum.
 """
 import numpy as np
 import pytest
@@ -26,6 +29,7 @@ import pytest
 from oracle import kifmm as ok
 from paper_2303_08394_gb300 import FMMPlan, _native as N
 from paper_2303_08394_gb300 import workloads as wl
+from tests.parity import ELEM_C
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -85,11 +89,14 @@ def test_each_pass_matches_the_oracle(case, mode):
     k_up, k_dn = unit_kernel(AO * s, AI * s), unit_kernel(AI * s, AO * s)
 
     acc = {}   # (pass, level) -> [sum |gpu - oracle|^2, sum |oracle|^2]
+    boxes = {}  # (pass, level) -> per box (|gpu - oracle|^2, |oracle|^2)
 
     def add(name, level, got, ref):
         e = acc.setdefault((name, level), [0.0, 0.0])
-        e[0] += float(np.sum((got - ref) ** 2))
-        e[1] += float(np.sum(ref ** 2))
+        de, dr = float(np.sum((got - ref) ** 2)), float(np.sum(ref ** 2))
+        e[0] += de
+        e[1] += dr
+        boxes.setdefault((name, level), []).append((de, dr))
 
     for i, b in enumerate(keys):
         if b[0] < 2:
@@ -105,3 +112,11 @@ def test_each_pass_matches_the_oracle(case, mode):
     assert {a for a, _ in errs} == {"up", "down", "m2l"}
     worst = max(errs.values())
     assert worst <= BAR[mode], errs
+    # per box: sqrt(err_b) <= ELEM_C * bar * sqrt(mean_b ref_b)
+    ratios = {}
+    for key, v in boxes.items():
+        v = np.asarray(v)
+        ratios[key] = float(np.sqrt(v[:, 0].max()) / (BAR[mode] * np.sqrt(v[:, 1].mean())))
+    print(case, mode, "per-box ratios", {f"{a}@L{l}": f"{v:.2f}" for (a, l), v in
+                                         sorted(ratios.items())})
+    assert max(ratios.values()) <= ELEM_C, ratios

@@ -8,7 +8,10 @@ Bars (FP32 path):
   method is already more accurate than FP32 can resolve, e.g. p = 7, the
   FP32 path is held to that floor instead);
 * column r of an nrhs evaluation equals the single-vector evaluation of
-  charges[:, r] bit for bit (same FP32 operations in the same order).
+  charges[:, r] bit for bit (same FP32 operations in the same order);
+* beside every relative L2 bar, every target's error is bounded by
+  c * bar * rms(reference) (tests/parity.py: c = 8 against the oracle
+  KIFMM, 16 against the direct sum).
 """
 import numpy as np
 import pytest
@@ -17,6 +20,7 @@ from oracle.direct import direct_sum
 from oracle.kifmm import KIFMM
 from paper_2303_08394_gb300 import FMMPlan, _native as N
 from paper_2303_08394_gb300 import workloads as wl
+from tests.parity import ELEM_C_DIRECT, check
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -68,6 +72,10 @@ def test_fmm_matches_oracle(name, gen, n, p, ncrit):
     e_gpu, e_ora = rel(phi, ref), rel(phi_o, ref)
     assert e_gpu_ora <= 1e-6, (e_gpu_ora, e_gpu, e_ora)
     assert e_gpu <= 1.5 * e_ora + FP32_FLOOR, (e_gpu, e_ora)
+    r1 = check(phi, phi_o, 1e-6, what=f"{name} vs oracle")[1]
+    r2 = check(phi, ref, 1.5 * e_ora + FP32_FLOOR, c=ELEM_C_DIRECT,
+               what=f"{name} vs direct")[1]
+    print(name, "element ratios", r1, r2)
     # the lists the GPU ran on are the oracle's lists
     assert plan.info("v_pairs") == sum(len(v) for v in ora.V.values())
     assert plan.info("u_pairs") == sum(len(v) for v in ora.U.values())
@@ -89,7 +97,7 @@ def test_single_leaf_equals_direct_sum():
     assert plan.info("depth") == 0
     phi = gpu_eval(plan, q[:, 0])[:, 0]
     ref = direct_sum(x, q[:, 0])
-    assert rel(phi, ref) < 1e-6
+    check(phi, ref, 1e-6, what="single leaf vs direct")
 
 
 def test_one_point_and_coincident_points():
@@ -102,7 +110,7 @@ def test_one_point_and_coincident_points():
     phi = gpu_eval(plan, q[:, 0])[:, 0]
     ref = direct_sum(x, q[:, 0])
     ora = KIFMM(x, 5, 16).evaluate(q[:, 0])
-    assert rel(phi, ora) < 1e-6
+    check(phi, ora, 1e-6, what="coincident points vs oracle")
     assert np.all(np.isfinite(phi))
 
 
@@ -116,7 +124,7 @@ def test_ragged_tiles_and_deep_tree():
     assert plan.info("w_pairs") > 0 and plan.info("x_pairs") > 0
     phi = gpu_eval(plan, q)[:, 0]
     ora = KIFMM(x, 4, 6).evaluate(q)
-    assert rel(phi, ora) < 1e-6
+    check(phi, ora, 1e-6, what="deep tree vs oracle")
 
 
 def test_host_buffers_match_device_buffers():
@@ -168,7 +176,7 @@ def test_graph_replay_matches_direct_launches():
     for o in outs + [back]:
         np.testing.assert_array_equal(o.cpu().numpy(), direct)
     np.testing.assert_array_equal(out1.cpu().numpy()[:, 0], direct[:, 0])
-    assert rel(tc.cpu().numpy(), direct) < 1e-6
+    check(tc.cpu().numpy(), direct, 1e-6, what="tf32x3 vs fp32")
 
 
 @pytest.mark.parametrize("mode", [N.M2L_FP32, N.M2L_BF16X3], ids=["fp32", "bf16x3"])
@@ -202,7 +210,7 @@ def test_million_point_workload_sampled_against_direct_sum():
     idx = wl.sample_targets(w.n, w.error_samples, 0)
     # the zero-distance self pair is skipped, so these are Eq. (1) potentials
     ref = direct_sum(x, q[:, 0], targets=x[idx])
-    assert rel(phi[idx], ref) <= 1e-5
+    check(phi[idx], ref, 1e-5, c=ELEM_C_DIRECT, what="10^6 cube vs direct")
 
 
 @pytest.mark.parametrize("p,n,ncrit", [(2, 3000, 16), (10, 1500, 32)], ids=["p2", "p10"])
@@ -219,10 +227,14 @@ def test_extreme_orders_every_mode(p, n, ncrit):
     e_ora = rel(ora, ref)
     plan = FMMPlan(x, p, ncrit)
     errs = {}
+    bars = {"fp32": 1e-6, "tf32x3": 1e-6, "bf16x3": 1e-5}
     for mode, name in ((N.M2L_FP32, "fp32"), (N.M2L_TF32X3, "tf32x3"), (N.M2L_BF16X3, "bf16x3")):
         plan.set_m2l_mode(mode)
         phi = gpu_eval(plan, q)[:, 0]
         errs[name] = (rel(phi, ora), rel(phi, ref))
+        check(phi, ora, bars[name], what=f"p={p} {name} vs oracle")
+        if name == "fp32":
+            check(phi, ref, 1.5 * e_ora + FP32_FLOOR, c=ELEM_C_DIRECT, what=f"p={p} fp32 vs direct")
     print(p, "k", plan.info("rank_m2l"), "oracle vs direct", e_ora, errs)
     assert errs["fp32"][0] <= 1e-6 and errs["tf32x3"][0] <= 1e-6, (e_ora, errs)
     assert errs["bf16x3"][0] <= 1e-5, (e_ora, errs)

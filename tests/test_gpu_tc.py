@@ -12,6 +12,7 @@ import pytest
 from oracle.kifmm import KIFMM
 from paper_2303_08394_gb300 import FMMPlan, _native as N
 from paper_2303_08394_gb300 import workloads as wl
+from tests.parity import check
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -54,6 +55,8 @@ def test_tc_m2l_matches_oracle(mode, gen, n, p, ncrit):
     ora = KIFMM(x, p, ncrit).evaluate(q)
     assert rel(tc, ora) <= BARS[mode], (rel(tc, ora), rel(simt, ora))
     assert rel(tc, simt) <= BARS[mode]
+    check(tc, ora, BARS[mode], what="tensor-core M2L vs oracle")
+    check(tc, simt, BARS[mode], what="tensor-core M2L vs FP32 M2L")
 
 
 @pytest.mark.parametrize("mode", [N.M2L_TF32X3, N.M2L_BF16X3], ids=["tf32x3", "bf16x3"])
@@ -73,4 +76,4 @@ def test_tc_deep_adaptive_tree():
     plan = FMMPlan(x, 4, 6, m2l_mode=N.M2L_TF32X3)
     phi = gpu_eval(plan, q)[:, 0]
     ora = KIFMM(x, 4, 6).evaluate(q)
-    assert rel(phi, ora) <= 1e-6
+    check(phi, ora, 1e-6, what="deep tree TF32x3 vs oracle")
