@@ -247,7 +247,11 @@ fmm_status fmm_evaluate_gradient(fmm_plan_t plan, const float *charges, int nrhs
  * The workspace comes from one fixed 64 MiB array in device memory that the
  * library holds on every GPU that loads it, until the process exits.  The
  * first call on a device looks the array up (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.
+ * device current; make that first call before any stream capture.  A reset
+ * of the device's primary context (cudaDeviceReset) gives the array a new
+ * address: the next call notices and looks it up again, so after a reset
+ * that next call, too, should come before any stream capture.  The calling
+ * thread's current device is the same on return as on entry.
  *
  * charges, potentials: device pointers only, layouts as in fmm_evaluate;
  * host pointers return FMM_ERR_INVALID_ARG.  A plan and nrhs whose workspace

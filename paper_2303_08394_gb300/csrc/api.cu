@@ -1016,6 +1016,7 @@ fmm_status create_plan(const double *const *sources, const double *const *target
     if (o.tree_build == FMM_TREE_DEVICE && o.host_only)
         return fail(FMM_ERR_INVALID_ARG, "FMM_TREE_DEVICE needs a device (host_only is set)");
     fmm_plan_s *P = nullptr;
+    kifmm::DeviceGuard dg_;  // the caller's device is current again on return
     try {
         P = new fmm_plan_s();
         P->opts = o;
@@ -1034,7 +1035,7 @@ fmm_status create_plan(const double *const *sources, const double *const *target
                 }
             }
             P->device = dev;
-            cudaError_t e = cudaSetDevice(dev);
+            cudaError_t e = dg_.set(dev);
             if (e != cudaSuccess) {
                 delete P;
                 return fail(FMM_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
@@ -1139,7 +1140,8 @@ fmm_status evaluate_impl(fmm_plan_s *P, const float *charges, int nrhs, double *
     if (!charges) return fail(FMM_ERR_INVALID_ARG, "NULL charges or potentials");
     if (nrhs < 1) return fail(FMM_ERR_INVALID_ARG, "nrhs must be >= 1");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    CK(cudaSetDevice(P->device));
+    kifmm::DeviceGuard dg_;
+    CK(dg_.set(P->device));
     if (fmm_status e = kifmm::plan_check_device_error(P)) return e;
     const bool dq = is_device_pointer(charges);
     const bool dp = !potentials || is_device_pointer(potentials);
@@ -1226,7 +1228,8 @@ fmm_status fmm_plan_set_option(fmm_plan_t plan, int key, double value) {
         if (mode != FMM_M2L_FP32 && mode != FMM_M2L_BF16X3 && mode != FMM_M2L_TF32X3)
             return fail(FMM_ERR_INVALID_ARG, "unknown M2L mode");
         if (mode != FMM_M2L_FP32 && !plan->opts.host_only) {
-            CK(cudaSetDevice(plan->device));
+            kifmm::DeviceGuard dg_;
+            CK(dg_.set(plan->device));
             fmm_status s = prepare_tc(plan, mode);
             if (s != FMM_OK) return s;
         }
@@ -1420,7 +1423,8 @@ fmm_status fmm_plan_get_workspace(fmm_plan_t P, int which, void *dst, int64_t by
     if (!dst) return FMM_OK;
     if (bytes < (int64_t)size) return fail(FMM_ERR_INVALID_ARG, "destination too small");
     if (!src) return fail(FMM_ERR_INVALID_ARG, "no workspace");
-    CK(cudaSetDevice(P->device));
+    kifmm::DeviceGuard dg_;
+    CK(dg_.set(P->device));
     CK(cudaStreamSynchronize(P->last_stream));
     if (size) CK(cudaMemcpy(dst, src, size, cudaMemcpyDeviceToHost));
     return FMM_OK;

@@ -56,7 +56,8 @@ extern "C" fmm_status fmm_evaluate_noalloc(fmm_plan_t plan, const float *charges
     if (nrhs < 1) return fail(FMM_ERR_INVALID_ARG, "nrhs must be >= 1");
     const int dev = kifmm::plan_device(plan);
     if (dev < 0 || dev >= kMaxDevices) return fail(FMM_ERR_UNSUPPORTED, "device ordinal too large");
-    cudaError_t e = cudaSetDevice(dev);
+    kifmm::DeviceGuard guard;  // the caller's device is current again on return
+    cudaError_t e = guard.set(dev);
     if (e != cudaSuccess) return fail(FMM_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
     if (fmm_status err = kifmm::plan_check_device_error(plan)) return err;
     if (!is_device_pointer(charges) || !is_device_pointer(potentials))
@@ -78,6 +79,10 @@ extern "C" fmm_status fmm_evaluate_noalloc(fmm_plan_t plan, const float *charges
     void *base = nullptr;
     {
         std::lock_guard<std::mutex> g(g_mu);
+        // a reset of the device's primary context (cudaDeviceReset) frees the
+        // array's old address: look it up again when the kept one is no
+        // longer device memory of this context
+        if (g_scratch_ptr[dev] && !is_device_pointer(g_scratch_ptr[dev])) g_scratch_ptr[dev] = nullptr;
         if (!g_scratch_ptr[dev]) {
             e = cudaGetSymbolAddress(&g_scratch_ptr[dev], g_scratch);
             if (e != cudaSuccess) {

@@ -38,4 +38,21 @@ fmm_status plan_check_device_error(fmm_plan_s *P);
 fmm_status plan_set_error(fmm_status s, const std::string &msg);
 bool plan_host_only(const fmm_plan_s *P);
 
+// Makes a plan's device current for the guard's lifetime and then makes the
+// caller's device current again, so no entry point leaves it switched.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t set(int device) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        return prev == device ? cudaSuccess : cudaSetDevice(device);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 } // namespace kifmm
