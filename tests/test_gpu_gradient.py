@@ -19,7 +19,7 @@ from oracle.direct import direct_gradient
 from oracle.kifmm import KIFMM
 from paper_2303_08394_gb300 import FMMPlan, _native as N
 from paper_2303_08394_gb300 import workloads as wl
-from tests.parity import ELEM_C_DIRECT, check
+from tests.parity import ELEM_C_GRAD, check
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -62,8 +62,8 @@ def test_gradient_matches_oracle(mode, kind, n, p, ncrit):
     ref = direct_gradient(x, q)
     e_gpu, e_fmm = rel(g[:, 0, :], ref), rel(g_ora, ref)
     assert e_gpu <= 1.5 * e_fmm + BARS[mode], (e_gpu, e_fmm)
-    r1 = check(g[:, 0, :], g_ora, BARS[mode], what=f"{kind} gradient vs oracle")[1]
-    r2 = check(g[:, 0, :], ref, 1.5 * e_fmm + BARS[mode], c=ELEM_C_DIRECT,
+    r1 = check(g[:, 0, :], g_ora, BARS[mode], c=ELEM_C_GRAD, what=f"{kind} gradient vs oracle")[1]
+    r2 = check(g[:, 0, :], ref, 1.5 * e_fmm + BARS[mode], c=ELEM_C_GRAD,
                what=f"{kind} gradient vs direct")[1]
     print(kind, mode, "element ratios", r1, r2)
 
@@ -95,7 +95,8 @@ def test_distinct_targets_and_batches():
     _, g = grad_eval(plan, q)
     ora = KIFMM(np.vstack([x, y]), 5, 24)
     _, g_ora = ora.evaluate(np.concatenate([q, np.zeros(len(y))]), gradient=True)
-    check(g[:, 0, :], g_ora[len(x):], BARS[N.M2L_FP32], what="distinct targets gradient")
+    check(g[:, 0, :], g_ora[len(x):], BARS[N.M2L_FP32], c=ELEM_C_GRAD,
+          what="distinct targets gradient")
     sets = [wl.uniform_cube(n, 80 + n)[0] for n in (2500, 40, 1800)]
     qs = [wl.uniform_cube(len(s), 90 + len(s))[1][:, 0] for s in sets]
     B = FMMPlan.batch(sets, 4, 20)
@@ -103,7 +104,8 @@ def test_distinct_targets_and_batches():
     parts = B.split(gb[:, 0, :])
     for s, qi, got in zip(sets, qs, parts):
         _, want = KIFMM(s, 4, 20).evaluate(qi, gradient=True)
-        check(got, want, BARS[N.M2L_FP32], what=f"batch problem of {len(s)} points, gradient")
+        check(got, want, BARS[N.M2L_FP32], c=ELEM_C_GRAD,
+              what=f"batch problem of {len(s)} points, gradient")
 
 
 def test_benchmark_workload_sampled():
@@ -113,4 +115,4 @@ def test_benchmark_workload_sampled():
     _, g = grad_eval(plan, q[:, 0], potentials=False)
     idx = wl.sample_targets(w.n, w.error_samples, 0)
     ref = direct_gradient(x, q[:, 0], x[idx])
-    check(g[idx, 0, :], ref, 2e-5, c=ELEM_C_DIRECT, what="10^6 cube gradient")  # measured 9.9e-6
+    check(g[idx, 0, :], ref, 2e-5, c=ELEM_C_GRAD, what="10^6 cube gradient")  # measured 9.9e-6
