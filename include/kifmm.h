@@ -182,7 +182,7 @@ enum {
                              same ones; 0: launch the kernels directly.  The
                              legacy default stream (NULL) always launches
                              directly, since it cannot be captured. */
-    FMM_OPT_TEST_M2L_STALL = 5 /* failure-detection test hook, value 0
+    FMM_OPT_TEST_M2L_STALL = 5, /* failure-detection test hook, value 0
                              (default) or 1.  With 1, block 0 of every
                              tensor-core M2L launch first waits on a barrier
                              that nothing completes; the wait gives up after
@@ -193,6 +193,16 @@ enum {
                              with host buffers, else the next evaluation)
                              returns FMM_ERR_TIMEOUT, roles mask 32.  The
                              plan stays usable.  No effect in FP32 mode. */
+    FMM_OPT_M2L_KERNEL = 6 /* which tensor-core M2L kernel the BF16x3 and
+                             TF32x3 modes run: 0 the pair-column kernel
+                             (each V pair one column of a product by S_t,
+                             in windows of up to 256 target boxes; needs an
+                             operand width kpad <= 128, else the target-tile
+                             kernel runs), 1 (default) the target-tile
+                             kernel (128 target boxes of one level and
+                             parity class per product).  Both sum each
+                             target's offsets in the same order: the
+                             results agree to rounding. */
 };
 fmm_status fmm_plan_set_option(fmm_plan_t plan, int key, double value);
 
@@ -296,6 +306,11 @@ enum {
     FMM_INFO_POINTS = 16,     /* points in the tree (2n with distinct
                                  targets) */
     FMM_INFO_PROBLEMS = 17,   /* independent problems */
+    FMM_INFO_M2L_WINDOWS = 20,/* pair-column M2L windows */
+    FMM_INFO_M2L_ITEMS = 21,  /* pair-column M2L items (offset products) */
+    FMM_INFO_M2L_KERNEL = 22, /* M2L kernel of the current mode: 0 FP32 SIMT,
+                                 1 tensor-core target tiles, 2 tensor-core
+                                 pair columns */
     FMM_INFO_OPERATOR_SOURCE = 19, /* where the plan's operators came
                                  from: 0 computed, 1 this process's memory,
                                  2 the operator cache file */
@@ -371,7 +386,21 @@ enum {
                               c_sigma + a_in s / 2) */
     FMM_ARRAY_OP_L2L = 33, /* double [8][rQ][nsurf]: Qu^T K(c_sigma +
                               a_in s / 2, a_out s) / 2 */
-    FMM_ARRAY_OP_QUK = 34  /* double [rQ][k]: Qu^T Uk */
+    FMM_ARRAY_OP_QUK = 34, /* double [rQ][k]: Qu^T Uk */
+    /* the pair-column M2L work table (all int32): windows of target boxes
+     * (boxes with a V list, in plan order), per window its items (one
+     * offset each, in increasing offset order, at most 128 pairs), per item
+     * its pairs (source box, target's place in the window), and the
+     * windows each persistent block takes */
+    FMM_ARRAY_M2L_WIN_TARGET_PTR = 35, /* [windows+1] */
+    FMM_ARRAY_M2L_WIN_TARGETS = 36,    /* [V targets] */
+    FMM_ARRAY_M2L_WIN_ITEM_PTR = 37,   /* [windows+1] */
+    FMM_ARRAY_M2L_ITEM_OFFSET = 38,    /* [items]: offset index */
+    FMM_ARRAY_M2L_ITEM_PAIR_PTR = 39,  /* [items+1] */
+    FMM_ARRAY_M2L_PAIR_SRC = 40,       /* [V pairs]: source box */
+    FMM_ARRAY_M2L_PAIR_SLOT = 41,      /* [V pairs]: target's place in its window */
+    FMM_ARRAY_M2L_CTA_PTR = 42,        /* [blocks+1] */
+    FMM_ARRAY_M2L_CTA_WIN = 43         /* [windows]: window ids per block */
 };
 /* Copy array `which` into dst (capacity `bytes`).  *needed receives the
  * size in bytes (may be NULL).  dst == NULL only queries the size. */

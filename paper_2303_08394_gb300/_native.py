@@ -20,12 +20,14 @@ OPT_GRAPH = 2
 OPT_AUTOTUNE = 3
 OPT_GEMM_SHAPE = 4
 OPT_TEST_M2L_STALL = 5
+OPT_M2L_KERNEL = 6
 TREE_AUTO, TREE_HOST, TREE_DEVICE, TREE_LEVELS_HOST = 0, 1, 2, 3
 
 INFO = {"n": 0, "nodes": 1, "leaves": 2, "depth": 3, "nsurf": 4, "rank_m2l": 5,
         "rank_up": 6, "rank_down": 7, "u_pairs": 8, "v_pairs": 9, "w_pairs": 10,
         "x_pairs": 11, "p2p_pairs": 12, "m2l_tiles": 13, "m2l_entries": 14,
-        "last_launches": 15, "points": 16, "problems": 17, "device_trees": 18, "operator_source": 19}
+        "last_launches": 15, "points": 16, "problems": 17, "device_trees": 18, "operator_source": 19,
+        "m2l_windows": 20, "m2l_items": 21, "m2l_kernel": 22}
 ARRAYS = {"node_keys": (0, "i4"), "node_range": (1, "i8"), "leaf_flag": (2, "i4"),
           "perm": (3, "i8"), "u_ptr": (4, "i8"), "u_idx": (5, "i4"),
           "v_ptr": (6, "i8"), "v_idx": (7, "i4"), "w_ptr": (8, "i8"),
@@ -37,7 +39,11 @@ ARRAYS = {"node_keys": (0, "i4"), "node_range": (1, "i8"), "leaf_flag": (2, "i4"
           "m2l_tile_entry_ptr": (23, "i4"), "m2l_entry_offset": (24, "i4"),
           "m2l_entry_src": (25, "i4"), "op_pu": (26, "f8"), "op_ps": (27, "f8"),
           "op_pv": (28, "f8"), "op_qu": (29, "f8"), "op_qs": (30, "f8"), "op_qv": (31, "f8"),
-          "op_m2m": (32, "f8"), "op_l2l": (33, "f8"), "op_quk": (34, "f8")}
+          "op_m2m": (32, "f8"), "op_l2l": (33, "f8"), "op_quk": (34, "f8"),
+          "m2l_win_target_ptr": (35, "i4"), "m2l_win_targets": (36, "i4"),
+          "m2l_win_item_ptr": (37, "i4"), "m2l_item_offset": (38, "i4"),
+          "m2l_item_pair_ptr": (39, "i4"), "m2l_pair_src": (40, "i4"),
+          "m2l_pair_slot": (41, "i4"), "m2l_cta_ptr": (42, "i4"), "m2l_cta_win": (43, "i4")}
 
 # every symbol include/kifmm.h declares
 EXPORTS = ("fmm_options_init", "fmm_plan_create", "fmm_plan_create_ex",

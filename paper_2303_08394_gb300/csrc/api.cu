@@ -61,6 +61,7 @@ struct fmm_plan_s {
     int device_trees = 0;         // problems whose tree was built on the device
     Tree tree;
     M2LTable m2l;
+    M2LWindows m2lw;              // pair-column M2L work table
     Schedules sched;
     std::shared_ptr<const Operators> ops;
     int ops_source = kOpsComputed;   // FMM_INFO_OPERATOR_SOURCE
@@ -70,6 +71,7 @@ struct fmm_plan_s {
     DevTree dt{};
     DevOps dops{};
     DevM2L dm{};
+    DevM2LPc dpc{};
     int *d_p2m = nullptr, *d_m2m = nullptr, *d_down = nullptr, *d_chunks = nullptr,
         *d_xnodes = nullptr;
     // index lists of the level products: children of every internal box
@@ -99,6 +101,7 @@ struct fmm_plan_s {
     int qh_cap = 0;                             // nrhs the split buffers hold
     int *err_host = nullptr, *err_dev = nullptr;  // mapped pinned error word
     int test_m2l_stall = 0;                     // FMM_OPT_TEST_M2L_STALL
+    int m2l_kernel = 1;                         // FMM_OPT_M2L_KERNEL
     // side stream of the upward pass: each level's M2L projection (qhat =
     // Vk^T rho, needed only by the M2L) runs there while the next level's
     // M2M proceeds; joined before the M2L
@@ -277,8 +280,15 @@ fmm_status prepare_tc(fmm_plan_s *P, int mode) {
             return fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
     }
     CK(configure_m2l_tc(kp, tf));
+    CK(configure_m2l_pc(tf));
     P->tc_ready[idx] = true;
     return FMM_OK;
+}
+
+// The tensor-core modes run the pair-column kernel when the option asks for
+// it and the operand width fits its 128 rows, else the target-tile kernel.
+bool m2l_uses_pair_columns(const fmm_plan_s *P) {
+    return P->m2l_kernel == 0 && P->kpad <= 128 && P->dpc.ncta > 0;
 }
 
 fmm_status upload_plan(fmm_plan_s *P) {
@@ -348,11 +358,12 @@ fmm_status upload_plan(fmm_plan_s *P) {
         // group, so each gets the register budget and occupancy of its width)
         std::vector<int> by_t;
         by_t.reserve(t.leaves.size());
-        d.t_first[4] = 0;
-        for (int w = 4; w >= 1; --w) {
+        d.t_first[kLeafWidths] = 0;
+        for (int w = kLeafWidths; w >= 1; --w) {
             for (int32_t lf : t.leaves) {
                 const int64_t np = t.end[lf] - t.begin[lf];
-                const int tw = (int)std::min<int64_t>(4, std::max<int64_t>(1, (np + 15) / 16));
+                const int tw = (int)std::min<int64_t>(kLeafWidths,
+                                                      std::max<int64_t>(1, (np + 15) / 16));
                 if (tw == w) by_t.push_back(lf);
             }
             d.t_first[w - 1] = (int)by_t.size();
@@ -416,6 +427,24 @@ fmm_status upload_plan(fmm_plan_s *P) {
     m.entry_offset = mt;
     if ((s = P->upload(P->m2l.entry_src, &mt))) return s;
     m.entry_src = mt;
+    {
+        const M2LWindows &wt = P->m2lw;
+        DevM2LPc &pc = P->dpc;
+        pc.ncta = wt.win_targets.empty() ? 0 : wt.ncta;
+#define UPW(vec, field)                                   \
+    if ((s = P->upload(wt.vec, &mt))) return s;           \
+    pc.field = mt;
+        UPW(cta_ptr, cta_ptr);
+        UPW(cta_win, cta_win);
+        UPW(win_target_ptr, win_target_ptr);
+        UPW(win_targets, win_targets);
+        UPW(win_item_ptr, win_item_ptr);
+        UPW(item_offset, item_offset);
+        UPW(item_pair_ptr, item_pair_ptr);
+        UPW(pair_src, pair_src);
+        UPW(pair_slot, pair_slot);
+#undef UPW
+    }
 
     // operators (FP32, transposed for coalesced row access)
     const int ns = o.ns, rP = o.rP, rQ = o.rQ, k = o.k, kp = P->kpad;
@@ -666,7 +695,8 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
     w.xchk = b.xchk;
     w.pot_user = pot;
     w.grad_user = grad;
-    if (!b.chk || !b.ybuf || !b.yp) return fail(FMM_ERR_INVALID_ARG, "workspace is incomplete");
+    if (!b.chk || !b.ybuf || !b.yp)
+        return fail(FMM_ERR_INVALID_ARG, "workspace is incomplete");
     int64_t launches = 0;
     if (P->timing) CK(record_phase(P->ev[0], st));
     CK(launch_gather_charges(P->dt, w, st));
@@ -810,9 +840,14 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
             const int idx = mode == FMM_M2L_TF32X3 ? 1 : 0;
             if (!P->tc_ready[idx] || !b.qh_hi || !b.qh_lo)
                 return fail(FMM_ERR_INVALID_ARG, "tensor-core M2L buffers are not prepared");
-            CK(launch_m2l_tc(P->dm, P->dops, w, (int)t.nodes(), idx == 1, P->tmap[idx][0],
-                             P->tmap[idx][1], b.qh_hi, b.qh_lo, P->err_dev,
-                             P->test_m2l_stall != 0, P->num_sms, st));
+            if (m2l_uses_pair_columns(P))
+                CK(launch_m2l_pc(P->dpc, P->dops, w, (int)t.nodes(), idx == 1, P->tmap[idx][0],
+                                 P->tmap[idx][1], b.qh_hi, b.qh_lo, P->err_dev,
+                                 P->test_m2l_stall != 0, st));
+            else
+                CK(launch_m2l_tc(P->dm, P->dops, w, (int)t.nodes(), idx == 1, P->tmap[idx][0],
+                                 P->tmap[idx][1], b.qh_hi, b.qh_lo, P->err_dev,
+                                 P->test_m2l_stall != 0, P->num_sms, st));
             launches += 2;
         }
     }
@@ -872,13 +907,10 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
         }
     }
     if (P->timing) CK(record_phase(P->ev[3], st));
-    CK(launch_eval(P->dt, P->dops, w, st));
     {
-        int groups = 0;  // non-empty leaf width groups: one launch each per column group
-        for (int tw = 1; tw <= 4; ++tw) groups += P->dt.t_first[tw - 1] > P->dt.t_first[tw];
-        // (gradients: one column per launch)
-        launches += (int64_t)groups * (grad ? nrhs : nrhs / 8 + ((nrhs % 8) >> 2) +
-                                                      ((nrhs % 4) >> 1) + (nrhs % 2));
+        int leaf_launches = 0;
+        CK(launch_eval(P->dt, P->dops, w, st, &leaf_launches));
+        launches += leaf_launches;
     }
     if (P->timing) CK(record_phase(P->ev[4], st));
     P->last_launches = launches;
@@ -1098,10 +1130,22 @@ fmm_status create_plan(const double *const *sources, const double *const *target
             merge_forest(parts, row_off, P->tree);
         }
         build_m2l_table(P->tree, P->m2l);
+        {
+            // one persistent block per SM of the plan's device
+            int nsm = 152;
+            if (!o.host_only &&
+                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device) !=
+                    cudaSuccess) {
+                cudaGetLastError();
+                nsm = 152;
+            }
+            build_m2l_windows(P->tree, nsm, P->m2lw);
+        }
         build_schedules(P->tree, kDownChunk, P->sched);
         if (const char *hook = std::getenv("FMM_TEST_CORRUPT_TABLE"))
             corrupt_table_for_test(P, hook);
-        const std::string bad = check_tables(P->tree, P->sched, P->m2l, P->rows);
+        std::string bad = check_tables(P->tree, P->sched, P->m2l, P->rows);
+        if (bad.empty()) bad = check_windows(P->tree, P->m2lw);
         if (!bad.empty()) {
             delete P;
             return fail(FMM_ERR_UNSUPPORTED, "plan tables failed their check: " + bad);
@@ -1249,6 +1293,12 @@ fmm_status fmm_plan_set_option(fmm_plan_t plan, int key, double value) {
         plan->drop_graph();
         return FMM_OK;
     }
+    if (key == FMM_OPT_M2L_KERNEL) {
+        if (value != 0.0 && value != 1.0) return fail(FMM_ERR_INVALID_ARG, "value 0 or 1");
+        plan->m2l_kernel = (int)value;
+        plan->drop_graph();
+        return FMM_OK;
+    }
     if (key == FMM_OPT_TEST_M2L_STALL) {
         if (value != 0.0 && value != 1.0) return fail(FMM_ERR_INVALID_ARG, "value 0 or 1");
         plan->test_m2l_stall = (int)value;
@@ -1309,6 +1359,11 @@ fmm_status fmm_plan_info(fmm_plan_t P, int key, int64_t *value) {
     case FMM_INFO_M2L_TILES: *value = (int64_t)P->m2l.tile_level.size(); break;
     case FMM_INFO_M2L_ENTRIES: *value = (int64_t)P->m2l.entry_offset.size(); break;
     case FMM_INFO_LAST_LAUNCHES: *value = P->last_launches; break;
+    case FMM_INFO_M2L_WINDOWS: *value = (int64_t)P->m2lw.win_item_ptr.size() - 1; break;
+    case FMM_INFO_M2L_ITEMS: *value = (int64_t)P->m2lw.item_offset.size(); break;
+    case FMM_INFO_M2L_KERNEL:
+        *value = P->opts.m2l_mode == FMM_M2L_FP32 ? 0 : (m2l_uses_pair_columns(P) ? 2 : 1);
+        break;
     default: return fail(FMM_ERR_INVALID_ARG, "unknown info key");
     }
     return FMM_OK;
@@ -1393,6 +1448,21 @@ fmm_status fmm_plan_get_array(fmm_plan_t P, int which, void *dst, int64_t bytes,
         src = P->m2l.entry_src.data();
         size = P->m2l.entry_src.size() * 4;
         break;
+#define WARR(id, vec)                       \
+    case id:                                \
+        src = P->m2lw.vec.data();           \
+        size = P->m2lw.vec.size() * 4;      \
+        break;
+    WARR(FMM_ARRAY_M2L_WIN_TARGET_PTR, win_target_ptr)
+    WARR(FMM_ARRAY_M2L_WIN_TARGETS, win_targets)
+    WARR(FMM_ARRAY_M2L_WIN_ITEM_PTR, win_item_ptr)
+    WARR(FMM_ARRAY_M2L_ITEM_OFFSET, item_offset)
+    WARR(FMM_ARRAY_M2L_ITEM_PAIR_PTR, item_pair_ptr)
+    WARR(FMM_ARRAY_M2L_PAIR_SRC, pair_src)
+    WARR(FMM_ARRAY_M2L_PAIR_SLOT, pair_slot)
+    WARR(FMM_ARRAY_M2L_CTA_PTR, cta_ptr)
+    WARR(FMM_ARRAY_M2L_CTA_WIN, cta_win)
+#undef WARR
     default: return fail(FMM_ERR_INVALID_ARG, "unknown array");
     }
     if (needed) *needed = (int64_t)size;

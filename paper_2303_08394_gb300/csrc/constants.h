@@ -9,5 +9,8 @@ constexpr int kNumOffsets = 316;
 constexpr int kTileRows = 128;
 // Finest level representable by the 16-bit integer coordinates.
 constexpr int kKeyBits = 16;
+// Width groups of the leaf pass: leaves of up to 16 T points take T targets
+// per lane, T = 1 .. kLeafWidths (larger leaves join the widest group).
+constexpr int kLeafWidths = 8;
 
 } // namespace kifmm

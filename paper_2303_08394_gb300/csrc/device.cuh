@@ -38,13 +38,13 @@ struct DevTree {
     const int *level;       // nodes
     const int *parent;      // nodes
     const int *child;       // nodes x 8
-    const int *leaves;      // nleaves, grouped by the leaf pass's targets per
-                            // lane T = min(4, ceil(points / 16)): the leaves
-                            // with T = 4 first, then 3, 2, 1 (plan order
-                            // within each group)
+    const int *leaves;      // nleaves, grouped by the leaf pass's width
+                            // T = min(kLeafWidths, ceil(points / 16)): the
+                            // widest group first (plan order within each)
     int nleaves;
-    int t_first[5];         // leaves[t_first[T] .. t_first[T - 1]) have width T
-                            // (t_first[4] = 0, t_first[0] = nleaves)
+    int t_first[kLeafWidths + 1];  // leaves[t_first[T] .. t_first[T - 1]) have
+                                   // width T (t_first[kLeafWidths] = 0,
+                                   // t_first[0] = nleaves)
     const int *u_ptr, *u_idx, *w_ptr, *w_idx, *x_ptr, *x_idx, *v_ptr;
     const int *x_slot;      // nodes: row block in the P2L buffer or -1
 };
@@ -77,6 +77,15 @@ struct DevM2L {
     const int *tile_entry_ptr;  // ntiles + 1
     const int *entry_offset;    // entries
     const int *entry_src;       // entries x 128
+};
+
+// Pair-column M2L tables (plan.h, M2LWindows).
+struct DevM2LPc {
+    int ncta;
+    const int *cta_ptr, *cta_win;
+    const int *win_target_ptr, *win_targets, *win_item_ptr;
+    const int *item_offset, *item_pair_ptr;
+    const int *pair_src, *pair_slot;
 };
 
 // Buffers of one evaluation.  Densities: [node][rhs][round4(ns)];
@@ -149,8 +158,10 @@ cudaError_t launch_p2l(const DevTree &t, const DevOps &o, const DevWork &w,
                        const int *nodes, int count, cudaStream_t s);
 cudaError_t launch_m2l_simt(const DevM2L &m, const DevOps &o, const DevWork &w,
                             cudaStream_t s);
+// Leaf pass (k_eval.cu): near field, L2P and M2P into the caller's rows;
+// *launches receives the kernels it enqueued.
 cudaError_t launch_eval(const DevTree &t, const DevOps &o, const DevWork &w,
-                        cudaStream_t s);
+                        cudaStream_t s, int *launches);
 
 // Tensor-core M2L (k_m2l_tc.cu).  qh_hi/qh_lo hold (nnodes*nrhs + 1) rows of
 // kpad operand elements (BF16, or TF32 in 32-bit words), the last row zero;
@@ -165,6 +176,18 @@ cudaError_t launch_m2l_tc(const DevM2L &m, const DevOps &o, const DevWork &w, in
                           bool tf32, const CUtensorMap &s_hi, const CUtensorMap &s_lo,
                           void *qh_hi, void *qh_lo, int *err, bool test_stall, int num_sms,
                           cudaStream_t st);
+
+// Split qhat (nrows rows of kpad FP32) into hi/lo operand rows (BF16, or
+// TF32 in 32-bit words), plus one zero row after the last.
+cudaError_t launch_split_qhat(const float *qhat, int64_t nrows, int kp, bool tf32, void *hi,
+                              void *lo, cudaStream_t st);
+// Pair-column tensor-core M2L (k_m2l_pc.cu): the same operands as
+// launch_m2l_tc (it splits qhat itself), work from the window tables; kpad
+// at most 128.  ncta persistent blocks.
+cudaError_t launch_m2l_pc(const DevM2LPc &m, const DevOps &o, const DevWork &w, int nnodes,
+                          bool tf32, const CUtensorMap &s_hi, const CUtensorMap &s_lo,
+                          void *qh_hi, void *qh_lo, int *err, bool test_stall, cudaStream_t st);
+cudaError_t configure_m2l_pc(bool tf32);
 
 // Nodes per down-pass chunk (chunks never mix child positions).
 constexpr int kDownChunk = 32;

@@ -12,13 +12,15 @@
 // shifted into B's frame (leaf-relative coordinates plus the exact dyadic
 // difference of box centres, so no precision is lost at deep levels).
 //
-// Compute: a warp owns a chunk of 16 T targets, T = 1..4 chosen per leaf
-// from its size (the plan groups the leaves by T and each group runs as its
-// own kernel, so the narrow widths keep fewer registers and more resident
-// blocks): lane l holds targets (l mod 16) + 16 i, i < T, and the two
-// half-warps take alternate staged sources, so one shared-memory access
-// (two adjacent 16-byte words) feeds 2 T pairs per lane.  Leaves with at
-// most 16 T targets use one chunk and the four warps split the sources.
+// Compute: the block works on a chunk of 16 T targets, T = 1..8 chosen per
+// leaf from its size (the plan groups the leaves by T and each group runs as
+// its own kernel, so the narrow widths keep fewer registers and more
+// resident blocks; many charge columns cap T at 4 and take several chunks):
+// lane l holds targets (l mod 16) + 16 i, i < T, and the two half-warps
+// take alternate staged sources, so one shared-memory access (two adjacent
+// 16-byte words) feeds 2 T pairs per lane.  The four warps always split the
+// sources of a chunk between them, whatever T, so the rounding does not
+// depend on T.
 // The staged count is padded with zero charges far away so the inner loop
 // is unrolled; the r > 0 test that drops the self pair runs only over B's
 // own points.
@@ -47,9 +49,11 @@ constexpr int kWarps = 4, kThreads = 32 * kWarps;
 constexpr int kSegCap = 256;       // segments per table window
 constexpr float kFar = 1.0e15f;    // position of padding sources (charge 0)
 
-// Staged sources per round; targets per lane go up to kTMax for every NR so
-// that the work split (and the rounding) is the same for every column.
-constexpr int kTMax = 4;
+// Targets per lane the register budget allows for NR columns (or the
+// gradient); wider leaves take one pass per chunk of 16 TMax targets.
+template <int NR, bool kGrad> struct TMax {
+    static constexpr int v = (NR == 1 && !kGrad) ? kLeafWidths : 4;
+};
 // minb: resident blocks per SM the register allocation must allow.
 // sums per target and launch: NR potentials, or potential + gradient
 template <int NR, bool kGrad> struct Sums {
@@ -60,8 +64,11 @@ template <int NR, bool kGrad> struct Sums {
 // minb: resident blocks per SM the register allocation must allow; the
 // narrow widths (T <= 2, the bulk of the leaves at ncrit ~ 150) fit more.
 template <int NR, int T> struct Cfg {
-    static constexpr int cap = NR == 1 ? 1024 : (NR == 2 ? 768 : 512);
-    static constexpr int minb = NR == 1 ? (T <= 2 ? 7 : (T == 3 ? 6 : 5)) : (NR == 2 ? (T <= 2 ? 5 : 4) : 1);
+    // staged sources per round (a multiple of 256, see run()); the narrow
+    // widths take fewer so that more blocks fit the shared memory
+    static constexpr int cap = NR == 1 ? (T <= 3 ? 512 : 1024) : (NR == 2 ? 768 : 512);
+    static constexpr int minb = NR == 1 ? (T <= 2 ? 7 : (T == 3 ? 6 : (T == 4 ? 5 : (T <= 7 ? 4 : 3))))
+                                        : (NR == 2 ? (T <= 2 ? 5 : 4) : 1);
 };
 
 // s = fl(a + b); err receives the exact rounding error (a + b = s + err).
@@ -113,7 +120,7 @@ template <> struct Charges<8> {
 // recomputed from the position residuals (see run()).
 constexpr float kCloseFrac = 0.125f;
 
-template <int NR> struct Smem;
+template <int NR, int CAP> struct Smem;
 
 template <bool kSelf>
 __device__ __forceinline__ void pair_terms(float4 p, float3 x, float &r2, float &inv) {
@@ -125,55 +132,91 @@ __device__ __forceinline__ void pair_terms(float4 p, float3 x, float &r2, float 
     if (kSelf) inv = r2 > 0.f ? inv : 0.f;
 }
 
-// Residual of staged source k (round `base`): what its FP32 position in B's
-// frame dropped.  Recomputed from the segment table exactly as the staging
-// formed the FP32 position (only surfaces, which are never close, have none).
-template <int NR>
-__device__ float3 staged_residual(const DevTree &t, const Smem<NR> &sm, int nsegw, int f);
-
 // Close pairs.  Positions are FP32 offsets from the target leaf's centre, so
 // a pair at distance r << h (leaf half-width) computed from them alone has
-// relative error ~ eps h / r.  The main loop tracks the smallest r^2 of
-// every block of eight sources (a target with itself excluded); a block
-// whose minimum in any lane is below thr2 = (kCloseFrac h)^2 is handed to
-// fix_block(), which recomputes the FP32 term of each close pair exactly and
-// adds q (1/r_accurate - 1/r_fp32), r_accurate from the position residuals
-// (position = hi + lo to about 2^-48 h).  Such blocks are rare, so the
-// common cost is one min per pair.
-template <int NR, int T, bool kGrad>
-__device__ __forceinline__ void fix_block(const DevTree &t, const Smem<NR> &sm, int nsegw, int base,
-                                       int j, bool self_run, const float3 (&x)[T], int t0,
-                                       int leaf_begin, int nt, float thr2,
-                                       float (&part)[T][Sums<NR, kGrad>::n]);
+// relative error ~ eps h / r.  Every staged source carries, beside its FP32
+// position in B's frame, what that position dropped (the rounding of the
+// move into B's frame plus the point's own residual, position = hi + lo to
+// about 2^-48 h).  After a source's T pairs, a lane whose smallest r^2 (the
+// target itself excluded) is below thr2 = (kCloseFrac h)^2 sets the
+// source's bit in a 32-bit mask of the run (a run is at most 32 sources per
+// lane); at the end of the run the lane recomputes the close pairs of its
+// marked sources from the exact difference (p - x) + (p_lo - x_lo) and adds
+// q (1/r_accurate - 1/r_fp32).  Distinct points that coincide in FP32 are so
+// resolved as in FP64 (exact duplicates keep r = 0 and drop out).  On points
+// spread over a surface most sources have a close target somewhere in the
+// leaf, but few for any one lane, so marking costs a predicated OR per
+// source and the corrections are paid per close source of the lane only.
+template <int NR, int T, bool kSelf, bool kGrad, int CAP>
+__device__ __forceinline__ void fix_source(const DevTree &t, const Smem<NR, CAP> &sm, int k,
+                                           int base, const float3 (&x)[T], int t0,
+                                           int leaf_begin, float thr2,
+                                           float (&part)[T][Sums<NR, kGrad>::n]) {
+    const float4 p = sm.u.st.spos[k], pl = sm.u.st.sres[k];
+    float q[NR];
+    if constexpr (NR == 1) {
+        q[0] = p.w;
+    } else {
+        Charges<NR>::get(sm.u.st.sq, k, q);
+    }
+#pragma unroll
+    for (int i = 0; i < T; ++i) {
+        float r2, inv;
+        pair_terms<kSelf>(p, x[i], r2, inv);
+        if (!(r2 < thr2) || (kSelf && base + k == t0 + 16 * i)) continue;
+        // a close pair has a valid target: padding targets are far
+        const float4 xl = __ldg(t.pts_lo + leaf_begin + t0 + 16 * i);
+        const float dx = (p.x - x[i].x) + (pl.x - xl.x);
+        const float dy = (p.y - x[i].y) + (pl.y - xl.y);
+        const float dz = (p.z - x[i].z) + (pl.z - xl.z);
+        const float r2a = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float ia = r2a > 0.f ? KIFMM_RSQRT(r2a) : 0.f;
+        const float d = ia - inv;
+        if constexpr (kGrad) {
+            // replace the main loop's FP32 term w3 (p - x) by the accurate one
+            part[i][0] = fmaf(q[0], d, part[i][0]);
+            const float w3 = q[0] * (inv * inv * inv);
+            const float wa = q[0] * (ia * ia * ia);
+            part[i][1] = fmaf(wa, dx, fmaf(-w3, p.x - x[i].x, part[i][1]));
+            part[i][2] = fmaf(wa, dy, fmaf(-w3, p.y - x[i].y, part[i][2]));
+            part[i][3] = fmaf(wa, dz, fmaf(-w3, p.z - x[i].z, part[i][3]));
+        } else {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) part[i][r] = fmaf(q[r], d, part[i][r]);
+        }
+    }
+}
 
 // Staged sources j = a + 2u + h (j < e; a and e multiples of 16) against
 // this lane's T targets; h is the lane's half-warp.
 // t0: index of the lane's first target among B's points (target i is
 // t0 + 16 i); B's own points are staged first, in order, so in the self run
 // a target meets itself at staged index t0 + 16 i.
-template <int NR, int T, bool kSelf, bool kGrad>
-__device__ __forceinline__ void run(const DevTree &t, const Smem<NR> &sm, int nsegw, int base,
-                                    int a, int e, int h, const float3 (&x)[T], int t0,
-                                    int leaf_begin, int nt, float thr2,
-                                    float (&part)[T][Sums<NR, kGrad>::n]) {
+template <int NR, int T, bool kSelf, bool kGrad, int CAP>
+__device__ __forceinline__ void run(const DevTree &t, const Smem<NR, CAP> &sm, int base, int a,
+                                    int e, int h, const float3 (&x)[T], int t0, int leaf_begin,
+                                    float thr2, float (&part)[T][Sums<NR, kGrad>::n]) {
     const float4 *spos = sm.u.st.spos;
     const float *sq = sm.u.st.sq;
-    for (int j = a + h; j < e; j += 16) {
-        float r2min = 3.0e38f;
+    uint32_t close = 0;  // bit 8 it + u: source a + h + 16 it + 2 u has a close target
+    int it = 0;
+    for (int j = a + h; j < e; j += 16, ++it) {
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const float4 p = spos[j + 2 * u];
+            const int k = j + 2 * u;
+            const float4 p = spos[k];
             float q[NR];
             if constexpr (NR == 1) {
                 q[0] = p.w;
             } else {
-                Charges<NR>::get(sq, j + 2 * u, q);
+                Charges<NR>::get(sq, k, q);
             }
+            float r2min = 3.0e38f;
 #pragma unroll
             for (int i = 0; i < T; ++i) {
                 float r2, inv;
                 pair_terms<kSelf>(p, x[i], r2, inv);
-                if (!kSelf || base + j + 2 * u != t0 + 16 * i) r2min = fminf(r2min, r2);
+                if (!kSelf || base + k != t0 + 16 * i) r2min = fminf(r2min, r2);
                 if constexpr (kGrad) {
                     const float w3 = q[0] * (inv * inv * inv);
                     part[i][0] = fmaf(q[0], inv, part[i][0]);
@@ -185,112 +228,38 @@ __device__ __forceinline__ void run(const DevTree &t, const Smem<NR> &sm, int ns
                     for (int r = 0; r < NR; ++r) part[i][r] = fmaf(q[r], inv, part[i][r]);
                 }
             }
+            if (r2min < thr2) close |= 1u << (8 * it + u);
         }
-        if (__any_sync(0xffffffffu, r2min < thr2))
-            fix_block<NR, T, kGrad>(t, sm, nsegw, base, j, kSelf, x, t0, leaf_begin, nt, thr2,
-                                    part);
+    }
+    // a run spans at most 64 staged sources, so four iterations of eight
+#pragma unroll 1
+    while (close) {
+        const int bit = __ffs(close) - 1;
+        close &= close - 1;
+        const int k = a + h + 16 * (bit >> 3) + 2 * (bit & 7);
+        fix_source<NR, T, kSelf, kGrad>(t, sm, k, base, x, t0, leaf_begin, thr2, part);
     }
 }
 
-template <int NR> struct Smem {
+template <int NR, int CAP> struct Smem {
     union {
         struct {
-            float4 spos[Cfg<NR, 1>::cap];
-            float sq[NR > 1 ? Cfg<NR, 1>::cap * NR : 4];
+            float4 spos[CAP];
+            float4 sres[CAP];   // what each staged position dropped (see fix_source)
+            float sq[NR > 1 ? CAP * NR : 4];
         } st;
-        // partial sums of the source slices (used after the last round)
-        float2 red[kWarps][kTMax * (NR > 4 ? NR : 4)][16];
+        // partial sums of the source slices (used after the last round):
+        // T x sums per target, up to 8 x 1 (potentials) or 4 x 4 (gradients)
+        float2 red[kWarps][NR == 1 ? 16 : 4 * (NR > 4 ? NR : 4)][16];
     } u;
     float4 seg_off[kSegCap];  // centre offset, surface radius
     int seg_node[kSegCap], seg_kind[kSegCap], seg_start[kSegCap + 1];
     int warp_sum[kWarps];
 };
 
-template <int NR>
-__device__ float3 staged_residual(const DevTree &t, const Smem<NR> &sm, int nsegw, int f) {
-    int lo = 0;
-#pragma unroll
-    for (int step = kSegCap / 2; step > 0; step >>= 1) {
-        const int mid = lo + step;
-        if (mid < nsegw && sm.seg_start[mid] <= f) lo = mid;
-    }
-    if (lo >= nsegw || sm.seg_kind[lo] != 0 || f >= sm.seg_start[nsegw])
-        return make_float3(0.f, 0.f, 0.f);
-    const int i = sm.seg_node[lo] + (f - sm.seg_start[lo]);
-    const float4 so = sm.seg_off[lo];
-    const float4 p = __ldg(t.pts + i), pl = __ldg(t.pts_lo + i);
-    float ex, ey, ez;
-    two_sum(p.x, so.x, ex);
-    two_sum(p.y, so.y, ey);
-    two_sum(p.z, so.z, ez);
-    return make_float3(ex + pl.x, ey + pl.y, ez + pl.z);
-}
-
-template <int NR, int T, bool kGrad>
-__device__ __forceinline__ void fix_block(const DevTree &t, const Smem<NR> &sm, int nsegw, int base,
-                                       int j, bool self_run, const float3 (&x)[T], int t0,
-                                       int leaf_begin, int nt, float thr2,
-                                       float (&part)[T][Sums<NR, kGrad>::n]) {
-    float3 xl[T];  // the targets' residuals
-#pragma unroll
-    for (int i = 0; i < T; ++i) {
-        xl[i] = make_float3(0.f, 0.f, 0.f);
-        if (t0 + 16 * i < nt) {
-            const float4 v = __ldg(t.pts_lo + leaf_begin + t0 + 16 * i);
-            xl[i] = make_float3(v.x, v.y, v.z);
-        }
-    }
-    for (int u = 0; u < 8; ++u) {
-        const int k = j + 2 * u;
-        const float4 p = sm.u.st.spos[k];
-        float r2[T], inv[T];
-        bool any = false;
-#pragma unroll
-        for (int i = 0; i < T; ++i) {
-            if (self_run) pair_terms<true>(p, x[i], r2[i], inv[i]);
-            else pair_terms<false>(p, x[i], r2[i], inv[i]);
-            if (self_run && base + k == t0 + 16 * i) r2[i] = thr2;  // a target with itself
-            any |= r2[i] < thr2;
-        }
-        if (!any) continue;
-        float q[NR];
-        if constexpr (NR == 1) {
-            q[0] = p.w;
-        } else {
-            Charges<NR>::get(sm.u.st.sq, k, q);
-        }
-        const float3 pl = staged_residual<NR>(t, sm, nsegw, base + k);
-#pragma unroll
-        for (int i = 0; i < T; ++i) {
-            if (!(r2[i] < thr2)) continue;
-            // fl(p - x) is exact to eps |p - x|; the residuals carry what the
-            // FP32 positions dropped.  Distinct points that coincide in FP32
-            // are resolved (exact duplicates keep r2a = 0 and drop out).
-            const float dx = (p.x - x[i].x) + (pl.x - xl[i].x);
-            const float dy = (p.y - x[i].y) + (pl.y - xl[i].y);
-            const float dz = (p.z - x[i].z) + (pl.z - xl[i].z);
-            const float r2a = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float ia = r2a > 0.f ? KIFMM_RSQRT(r2a) : 0.f;
-            const float d = ia - inv[i];
-            if constexpr (kGrad) {
-                // replace the main loop's FP32 term w3 (p - x) by the accurate one
-                part[i][0] = fmaf(q[0], d, part[i][0]);
-                const float w3 = q[0] * (inv[i] * inv[i] * inv[i]);
-                const float wa = q[0] * (ia * ia * ia);
-                part[i][1] = fmaf(wa, dx, fmaf(-w3, p.x - x[i].x, part[i][1]));
-                part[i][2] = fmaf(wa, dy, fmaf(-w3, p.y - x[i].y, part[i][2]));
-                part[i][3] = fmaf(wa, dz, fmaf(-w3, p.z - x[i].z, part[i][3]));
-            } else {
-#pragma unroll
-                for (int r = 0; r < NR; ++r) part[i][r] = fmaf(q[r], d, part[i][r]);
-            }
-        }
-    }
-}
-
 template <int NR, int T, bool kGrad>
 __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const DevWork &w, int r0,
-                                     Smem<NR> &sm, int b, int2 rb, int nt) {
+                                     Smem<NR, Cfg<NR, T>::cap> &sm, int b, int2 rb, int nt) {
     constexpr int NQ = Sums<NR, kGrad>::n;
     constexpr int CAP = Cfg<NR, T>::cap;
     static_assert(CAP % (64 * kWarps) == 0, "rounds must hold whole runs for every slicing");
@@ -303,11 +272,11 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
     const int nseg = nu + nl2p + nw;
     const int ns = o.ns, nsp = (o.ns + 3) & ~3;
 
-    // warp roles: nsplit source slices x CW target-chunk workers
+    // warp roles: kWarps source slices of one target chunk per pass
     constexpr int CH = 16 * T;
     const int nchunk = (nt + CH - 1) / CH;
-    const int nsplit = nchunk >= kWarps ? 1 : kWarps / nchunk;
-    const int CW = kWarps / nsplit;
+    const int nsplit = kWarps;
+    const int CW = 1;
     const int split = wid / CW, cw = wid - split * CW;
     const int npass = (nchunk + CW - 1) / CW;
     const int self_end16 = (nt + 15) & ~15;
@@ -402,6 +371,7 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
                     const int k = tid + it * kThreads;
                     if ((k & ~31) >= mp) break;  // whole warp past the end
                     float4 pos = make_float4(kFar, kFar, kFar, 0.f);
+                    float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
                     float q[NR];
 #pragma unroll
                     for (int r = 0; r < NR; ++r) q[r] = 0.f;
@@ -415,9 +385,11 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
                         const int kind = sm.seg_kind[seg];
                         if (kind == 0) {
                             const int i = sm.seg_node[seg] + off;
-                            const float4 p = __ldg(t.pts + i);
-                            pos = make_float4(__fadd_rn(p.x, so.x), __fadd_rn(p.y, so.y),
-                                              __fadd_rn(p.z, so.z), 0.f);
+                            const float4 p = __ldg(t.pts + i), pl = __ldg(t.pts_lo + i);
+                            float ex, ey, ez;
+                            pos = make_float4(two_sum(p.x, so.x, ex), two_sum(p.y, so.y, ey),
+                                              two_sum(p.z, so.z, ez), 0.f);
+                            res = make_float4(ex + pl.x, ey + pl.y, ez + pl.z, 0.f);
                             const float *qi = w.qs + (size_t)i * w.nrhs + r0;
 #pragma unroll
                             for (int r = 0; r < NR; ++r) q[r] = __ldg(qi + r);
@@ -440,6 +412,7 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
                             for (int r = 0; r < NR; ++r) sm.u.st.sq[k * NR + r] = q[r];
                         }
                         sm.u.st.spos[k] = pos;
+                        sm.u.st.sres[k] = res;
                     }
                 }
                 __syncthreads();
@@ -458,10 +431,10 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
 #pragma unroll
                             for (int r = 0; r < NQ; ++r) part[i][r] = 0.f;
                         if (js > j0)
-                            run<NR, T, true, kGrad>(t, sm, nsegw, base, j0, js, half, x, t0, rb.x,
-                                                    nt, thr2, part);
-                        run<NR, T, false, kGrad>(t, sm, nsegw, base, js, j1, half, x, t0, rb.x, nt,
-                                                 thr2, part);
+                            run<NR, T, true, kGrad>(t, sm, base, j0, js, half, x, t0, rb.x, thr2,
+                                                    part);
+                        run<NR, T, false, kGrad>(t, sm, base, js, j1, half, x, t0, rb.x, thr2,
+                                                 part);
 #pragma unroll
                         for (int i = 0; i < T; ++i)
 #pragma unroll
@@ -534,9 +507,9 @@ struct Occupancy {
 
 template <int NR, int T, bool kGrad>
 __global__ void __launch_bounds__(kThreads, (Occupancy<NR, T, kGrad>::minb))
-    k_eval(DevTree t, DevOps o, DevWork w, int r0) {
-    __shared__ __align__(16) Smem<NR> sm;
-    const int b = t.leaves[t.t_first[T] + blockIdx.x];
+    k_eval(DevTree t, DevOps o, DevWork w, int r0, int first) {
+    __shared__ __align__(16) Smem<NR, Cfg<NR, T>::cap> sm;
+    const int b = t.leaves[first + blockIdx.x];
     const int2 rb = t.range[b];
     const int nt = rb.y - rb.x;
     if (nt <= 0) return;
@@ -544,37 +517,61 @@ __global__ void __launch_bounds__(kThreads, (Occupancy<NR, T, kGrad>::minb))
 }
 
 // one launch per non-empty width group, widest first (longest blocks
-// start first)
+// start first); group Tg runs with min(Tg, TMax) targets per lane
+template <int NR, bool kGrad, int T>
+void launch_width(const DevTree &t, const DevOps &o, const DevWork &w, int r0, int first,
+                  int n, cudaStream_t s) {
+    k_eval<NR, T, kGrad><<<n, kThreads, 0, s>>>(t, o, w, r0, first);
+}
+
 template <int NR, bool kGrad = false>
 cudaError_t launch_eval_nr(const DevTree &t, const DevOps &o, const DevWork &w, int r0,
-                           cudaStream_t s) {
-    static_assert(kTMax == 4, "width groups 1..4");
-    const int n4 = t.t_first[3] - t.t_first[4], n3 = t.t_first[2] - t.t_first[3];
-    const int n2 = t.t_first[1] - t.t_first[2], n1 = t.t_first[0] - t.t_first[1];
-    if (n4 > 0) k_eval<NR, 4, kGrad><<<n4, kThreads, 0, s>>>(t, o, w, r0);
-    if (n3 > 0) k_eval<NR, 3, kGrad><<<n3, kThreads, 0, s>>>(t, o, w, r0);
-    if (n2 > 0) k_eval<NR, 2, kGrad><<<n2, kThreads, 0, s>>>(t, o, w, r0);
-    if (n1 > 0) k_eval<NR, 1, kGrad><<<n1, kThreads, 0, s>>>(t, o, w, r0);
+                           cudaStream_t s, int *launches) {
+    for (int Tg = kLeafWidths; Tg >= 1; --Tg) {
+        const int n = t.t_first[Tg - 1] - t.t_first[Tg], first = t.t_first[Tg];
+        if (n <= 0) continue;
+        const int T = Tg < TMax<NR, kGrad>::v ? Tg : TMax<NR, kGrad>::v;
+        switch (T) {
+        case 1: launch_width<NR, kGrad, 1>(t, o, w, r0, first, n, s); break;
+        case 2: launch_width<NR, kGrad, 2>(t, o, w, r0, first, n, s); break;
+        case 3: launch_width<NR, kGrad, 3>(t, o, w, r0, first, n, s); break;
+        case 4: launch_width<NR, kGrad, 4>(t, o, w, r0, first, n, s); break;
+        default:
+            if constexpr (TMax<NR, kGrad>::v > 4) {
+                switch (T) {
+                case 5: launch_width<NR, kGrad, 5>(t, o, w, r0, first, n, s); break;
+                case 6: launch_width<NR, kGrad, 6>(t, o, w, r0, first, n, s); break;
+                case 7: launch_width<NR, kGrad, 7>(t, o, w, r0, first, n, s); break;
+                default: launch_width<NR, kGrad, 8>(t, o, w, r0, first, n, s); break;
+                }
+            }
+            break;
+        }
+        ++*launches;
+    }
     return cudaGetLastError();
 }
 
 } // namespace
 
-cudaError_t launch_eval(const DevTree &t, const DevOps &o, const DevWork &w, cudaStream_t s) {
+cudaError_t launch_eval(const DevTree &t, const DevOps &o, const DevWork &w, cudaStream_t s,
+                        int *launches) {
+    *launches = 0;
     if (w.grad_user) {
         // potentials (if w.pot_user) and gradients, one column per launch
         cudaError_t e = cudaSuccess;
-        for (int r0 = 0; r0 < w.nrhs && e == cudaSuccess; ++r0) e = launch_eval_nr<1, true>(t, o, w, r0, s);
+        for (int r0 = 0; r0 < w.nrhs && e == cudaSuccess; ++r0)
+            e = launch_eval_nr<1, true>(t, o, w, r0, s, launches);
         return e;
     }
     int r0 = 0;
     cudaError_t e = cudaSuccess;
     while (r0 < w.nrhs && e == cudaSuccess) {
         int left = w.nrhs - r0;
-        if (left >= 8) { e = launch_eval_nr<8>(t, o, w, r0, s); r0 += 8; }
-        else if (left >= 4) { e = launch_eval_nr<4>(t, o, w, r0, s); r0 += 4; }
-        else if (left >= 2) { e = launch_eval_nr<2>(t, o, w, r0, s); r0 += 2; }
-        else { e = launch_eval_nr<1>(t, o, w, r0, s); r0 += 1; }
+        if (left >= 8) { e = launch_eval_nr<8>(t, o, w, r0, s, launches); r0 += 8; }
+        else if (left >= 4) { e = launch_eval_nr<4>(t, o, w, r0, s, launches); r0 += 4; }
+        else if (left >= 2) { e = launch_eval_nr<2>(t, o, w, r0, s, launches); r0 += 2; }
+        else { e = launch_eval_nr<1>(t, o, w, r0, s, launches); r0 += 1; }
     }
     return e;
 }

@@ -389,6 +389,17 @@ __global__ void k_split_qhat(const float *__restrict__ qhat, int64_t nrows, int 
 
 } // namespace
 
+cudaError_t launch_split_qhat(const float *qhat, int64_t nrows, int kp, bool tf32, void *hi,
+                              void *lo, cudaStream_t st) {
+    const int64_t total = (nrows + 1) * kp;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)152 * 16);
+    if (tf32)
+        k_split_qhat<true><<<blocks, 256, 0, st>>>(qhat, nrows, kp, hi, lo);
+    else
+        k_split_qhat<false><<<blocks, 256, 0, st>>>(qhat, nrows, kp, hi, lo);
+    return cudaGetLastError();
+}
+
 size_t m2l_tc_smem(int kpad, int *stages) {
     const size_t stage = 2 * 128 * 128 + 2 * (size_t)kpad * 128;
     const size_t budget = 227 * 1024 - 1024 - 256;
@@ -410,13 +421,7 @@ cudaError_t launch_m2l_tc(const DevM2L &m, const DevOps &o, const DevWork &w, in
         return cudaErrorInvalidValue;
     // 1. operand split of the compressed multipoles
     {
-        int64_t total = (nrows + 1) * kp;
-        int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 16);
-        if (tf32)
-            k_split_qhat<true><<<blocks, 256, 0, st>>>(w.qhat, nrows, kp, qh_hi, qh_lo);
-        else
-            k_split_qhat<false><<<blocks, 256, 0, st>>>(w.qhat, nrows, kp, qh_hi, qh_lo);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_split_qhat(w.qhat, nrows, kp, tf32, qh_hi, qh_lo, st);
         if (e != cudaSuccess) return e;
     }
     TcArgs a;

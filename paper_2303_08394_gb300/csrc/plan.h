@@ -152,6 +152,28 @@ struct M2LTable {
 };
 void build_m2l_table(const Tree &tree, M2LTable &table);
 
+// M2L work decomposition of the pair-column tensor-core kernel: the boxes
+// with a V list, in plan order, are cut into windows of at most
+// kWinTargets boxes with about equal cost; within a window, the (target,
+// source) pairs of each offset t form items of at most kItemCols pairs, in
+// offset order and, within an item, in target order.  Each item is one
+// product S_t [q_A ...] whose columns are its pairs.  The windows are dealt
+// to `ncta` persistent blocks, longest first, to the least loaded block.
+constexpr int kWinTargets = 256;
+constexpr int kItemCols = 128;
+struct M2LWindows {
+    int ncta = 0;
+    std::vector<int32_t> cta_ptr, cta_win;      // ncta + 1; windows per block
+    std::vector<int32_t> win_target_ptr;        // windows + 1
+    std::vector<int32_t> win_targets;           // target boxes, window by window
+    std::vector<int32_t> win_item_ptr;          // windows + 1
+    std::vector<int32_t> item_offset;           // items: offset index t
+    std::vector<int32_t> item_pair_ptr;         // items + 1
+    std::vector<int32_t> pair_src;              // pairs: source box
+    std::vector<int32_t> pair_slot;             // pairs: target's place in its window
+};
+void build_m2l_windows(const Tree &tree, int ncta, M2LWindows &w);
+
 // Node schedules for the up and down passes.
 struct Schedules {
     std::vector<int32_t> p2m_nodes;       // leaves at level >= 2
@@ -174,6 +196,9 @@ void build_schedules(const Tree &tree, int chunk, Schedules &s);
 // value the upload narrows to 32 bits representable.  Empty when the plan
 // is sound, else a message naming the first table that is not.
 std::string check_tables(const Tree &t, const Schedules &s, const M2LTable &m, int64_t rows);
+// The same for the pair-column M2L table (every index inside its array,
+// window and item sizes within the kernel's limits).
+std::string check_windows(const Tree &t, const M2LWindows &w);
 
 } // namespace kifmm
 

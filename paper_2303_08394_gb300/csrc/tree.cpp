@@ -579,6 +579,127 @@ void build_m2l_table(const Tree &t, M2LTable &m) {
     }
 }
 
+void build_m2l_windows(const Tree &t, int ncta, M2LWindows &w) {
+    w = M2LWindows();
+    w.ncta = std::max(1, ncta);
+    std::vector<int32_t> tg;
+    for (int64_t b = 0; b < t.nodes(); ++b)
+        if (t.v_ptr[b + 1] > t.v_ptr[b]) tg.push_back((int32_t)b);
+    const int64_t ntg = (int64_t)tg.size();
+    // cost of a window: per item a fixed share (its operator tile), per
+    // pair column its 16-wide share of the product
+    constexpr int64_t kItemCost = kItemCols;
+    auto r16 = [](int64_t n) { return (n + 15) / 16 * 16; };
+    auto items = [](int64_t n) { return (n + kItemCols - 1) / kItemCols; };
+    std::vector<int32_t> cnt(kNumOffsets, 0);
+    std::vector<int> touched;
+    auto delta = [&](int32_t b) {
+        int64_t d = 0;
+        for (int64_t e = t.v_ptr[b]; e < t.v_ptr[b + 1]; ++e) {
+            const int64_t n = cnt[t.v_off[e]];
+            d += (items(n + 1) - items(n)) * kItemCost + r16(n + 1) - r16(n);
+        }
+        return d;
+    };
+    auto add = [&](int32_t b) {
+        for (int64_t e = t.v_ptr[b]; e < t.v_ptr[b + 1]; ++e) {
+            const int o = t.v_off[e];
+            if (cnt[o]++ == 0) touched.push_back(o);
+        }
+    };
+    auto reset = [&]() {
+        for (int o : touched) cnt[o] = 0;
+        touched.clear();
+    };
+    // greedy cut in plan order under a cost cap (and kWinTargets boxes)
+    auto greedy = [&](int64_t cap, std::vector<int32_t> *starts, std::vector<int64_t> *costs) {
+        reset();
+        int64_t nwin = 0, cost = 0, size = 0;
+        for (int64_t i = 0; i < ntg; ++i) {
+            int64_t d = delta(tg[i]);
+            if (size > 0 && (size == kWinTargets || cost + d > cap)) {
+                if (costs) costs->push_back(cost);
+                reset();
+                cost = size = 0;
+                d = delta(tg[i]);
+            }
+            if (size == 0) {
+                ++nwin;
+                if (starts) starts->push_back((int32_t)i);
+            }
+            add(tg[i]);
+            cost += d;
+            ++size;
+        }
+        if (size > 0 && costs) costs->push_back(cost);
+        reset();
+        return nwin;
+    };
+    w.win_target_ptr.push_back(0);
+    w.win_item_ptr.push_back(0);
+    w.item_pair_ptr.push_back(0);
+    w.cta_ptr.assign(w.ncta + 1, 0);
+    if (ntg == 0) return;
+    // as many windows as a whole number of rounds over the blocks needs, so
+    // that every block gets the same number of windows of about equal cost
+    const int64_t rounds = (ntg + (int64_t)kWinTargets * w.ncta - 1) / ((int64_t)kWinTargets * w.ncta);
+    const int64_t want = std::min<int64_t>(ntg, rounds * w.ncta);
+    int64_t lo = 1, hi = 1;
+    while (greedy(hi, nullptr, nullptr) > want) hi *= 2;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (greedy(mid, nullptr, nullptr) <= want) hi = mid;
+        else lo = mid + 1;
+    }
+    std::vector<int32_t> starts;
+    std::vector<int64_t> costs;
+    greedy(hi, &starts, &costs);
+    const int64_t nwin = (int64_t)starts.size();
+    starts.push_back((int32_t)ntg);
+    // items: per window, per offset in increasing order, pairs in window order
+    std::vector<std::vector<std::pair<int32_t, int32_t>>> bucket(kNumOffsets);
+    for (int64_t wi = 0; wi < nwin; ++wi) {
+        for (int32_t i = starts[wi]; i < starts[wi + 1]; ++i) {
+            const int32_t b = tg[i];
+            w.win_targets.push_back(b);
+            for (int64_t e = t.v_ptr[b]; e < t.v_ptr[b + 1]; ++e)
+                bucket[t.v_off[e]].push_back({i - starts[wi], t.v_idx[e]});
+        }
+        w.win_target_ptr.push_back((int32_t)w.win_targets.size());
+        for (int o = 0; o < kNumOffsets; ++o) {
+            std::vector<std::pair<int32_t, int32_t>> &v = bucket[o];
+            for (size_t a = 0; a < v.size(); a += kItemCols) {
+                const size_t z = std::min(v.size(), a + (size_t)kItemCols);
+                w.item_offset.push_back(o);
+                for (size_t k = a; k < z; ++k) {
+                    w.pair_slot.push_back(v[k].first);
+                    w.pair_src.push_back(v[k].second);
+                }
+                w.item_pair_ptr.push_back((int32_t)w.pair_src.size());
+            }
+            v.clear();
+        }
+        w.win_item_ptr.push_back((int32_t)w.item_offset.size());
+    }
+    // longest window first to the least loaded block
+    std::vector<int32_t> order(nwin);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return costs[a] > costs[b]; });
+    std::vector<int64_t> load(w.ncta, 0);
+    std::vector<std::vector<int32_t>> per(w.ncta);
+    for (int32_t wi : order) {
+        const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        per[c].push_back(wi);
+        load[c] += costs[wi];
+    }
+    for (int c = 0; c < w.ncta; ++c) {
+        std::sort(per[c].begin(), per[c].end());
+        w.cta_win.insert(w.cta_win.end(), per[c].begin(), per[c].end());
+        w.cta_ptr[c + 1] = (int32_t)w.cta_win.size();
+    }
+}
+
 void build_schedules(const Tree &t, int chunk, Schedules &s) {
     s = Schedules();
     for (int32_t lf : t.leaves)
@@ -652,6 +773,48 @@ std::string check_csr(const char *name, const std::vector<T> &ptr, int64_t rows,
 }
 
 } // namespace
+
+std::string check_windows(const Tree &t, const M2LWindows &w) {
+    const int64_t nn = t.nodes();
+    auto csr = [](const std::vector<int32_t> &ptr, size_t count, const char *name) -> std::string {
+        if (ptr.empty() || ptr.front() != 0 || (size_t)ptr.back() != count)
+            return std::string(name) + ": offsets do not span their array";
+        for (size_t k = 1; k < ptr.size(); ++k)
+            if (ptr[k] < ptr[k - 1]) return std::string(name) + ": offsets decrease";
+        return std::string();
+    };
+    const int64_t nwin = (int64_t)w.win_item_ptr.size() - 1;
+    std::string e;
+    if ((int64_t)w.win_target_ptr.size() != nwin + 1) return "m2l windows: inconsistent sizes";
+    if (!(e = csr(w.win_target_ptr, w.win_targets.size(), "m2l window targets")).empty()) return e;
+    if (!(e = csr(w.win_item_ptr, w.item_offset.size(), "m2l window items")).empty()) return e;
+    if ((int64_t)w.item_pair_ptr.size() != (int64_t)w.item_offset.size() + 1)
+        return "m2l items: inconsistent sizes";
+    if (!(e = csr(w.item_pair_ptr, w.pair_src.size(), "m2l item pairs")).empty()) return e;
+    if (w.pair_slot.size() != w.pair_src.size()) return "m2l pairs: inconsistent sizes";
+    if ((int64_t)w.cta_ptr.size() != (int64_t)w.ncta + 1) return "m2l blocks: inconsistent sizes";
+    if (!(e = csr(w.cta_ptr, w.cta_win.size(), "m2l block windows")).empty()) return e;
+    for (int32_t x : w.cta_win)
+        if (x < 0 || x >= nwin) return "m2l block windows: window out of range";
+    for (int32_t x : w.win_targets)
+        if (x < 0 || x >= nn) return "m2l window targets: node out of range";
+    for (int32_t x : w.pair_src)
+        if (x < 0 || x >= nn) return "m2l pairs: source out of range";
+    for (int32_t x : w.item_offset)
+        if (x < 0 || x >= kNumOffsets) return "m2l items: offset out of range";
+    for (int64_t wi = 0; wi < nwin; ++wi) {
+        const int32_t ntw = w.win_target_ptr[wi + 1] - w.win_target_ptr[wi];
+        if (ntw > kWinTargets) return "m2l window: too many targets";
+        for (int32_t it = w.win_item_ptr[wi]; it < w.win_item_ptr[wi + 1]; ++it) {
+            const int32_t np = w.item_pair_ptr[it + 1] - w.item_pair_ptr[it];
+            if (np < 1 || np > kItemCols) return "m2l item: pair count out of range";
+            for (int32_t k = w.item_pair_ptr[it]; k < w.item_pair_ptr[it + 1]; ++k)
+                if (w.pair_slot[k] < 0 || w.pair_slot[k] >= ntw)
+                    return "m2l pairs: slot outside its window";
+        }
+    }
+    return std::string();
+}
 
 std::string check_tables(const Tree &t, const Schedules &s, const M2LTable &m, int64_t rows) {
     const int64_t nn = t.nodes(), n = t.n;

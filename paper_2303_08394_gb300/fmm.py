@@ -157,6 +157,11 @@ class FMMPlan:
         """Force one level-product tile shape (0, 1, 2) or -1 for automatic."""
         N.check(N.lib().fmm_plan_set_option(self._h, N.OPT_GEMM_SHAPE, float(shape)))
 
+    def set_m2l_kernel(self, kernel: int):
+        """Tensor-core M2L kernel: 0 pair columns (operand width <= 128),
+        1 target tiles (the default) (FMM_OPT_M2L_KERNEL)."""
+        N.check(N.lib().fmm_plan_set_option(self._h, N.OPT_M2L_KERNEL, float(kernel)))
+
     def set_graph(self, on: bool):
         """Capture/replay evaluations as a CUDA graph (default on; never on
         the legacy default stream)."""

@@ -1,6 +1,7 @@
 """Failure detection in the tensor-core M2L, made to happen without a fault.
 
-Every wait inside k_m2l_tc is bounded; when one expires the block records
+Every wait inside the tensor-core M2L kernels (target tiles and pair
+columns) is bounded; when one expires the block records
 its role in the plan's mapped error word, drains what it issued, frees its
 tensor memory and returns, and the host reports FMM_ERR_TIMEOUT.  The test
 hook FMM_OPT_TEST_M2L_STALL makes block 0 wait on a barrier that nothing
@@ -28,10 +29,13 @@ def stall(plan, on):
     N.check(N.lib().fmm_plan_set_option(plan._h, N.OPT_TEST_M2L_STALL, 1.0 if on else 0.0))
 
 
+@pytest.mark.parametrize("kernel", [0, 1], ids=["pair_columns", "target_tiles"])
 @pytest.mark.parametrize("mode", [N.M2L_BF16X3, N.M2L_TF32X3], ids=["bf16x3", "tf32x3"])
-def test_expired_wait_is_reported_and_the_plan_recovers(mode):
+def test_expired_wait_is_reported_and_the_plan_recovers(mode, kernel):
     x, q = wl.uniform_cube(20_000, 61, nrhs=2)
     plan = FMMPlan(x, 5, 24, m2l_mode=mode)
+    plan.set_m2l_kernel(kernel)
+    assert plan.info("m2l_kernel") == (2 if kernel == 0 else 1)
     qd = torch.as_tensor(q.astype(np.float32), device="cuda")
     ref = plan.evaluate(qd)
     torch.cuda.synchronize()

@@ -118,3 +118,86 @@ def test_m2l_table_empty_below_level_two():
     P = FMMPlan(x, 4, 64, host_only=1)
     assert P.info("m2l_tiles") == 0 and P.info("m2l_entries") == 0
     assert len(P.array("m2l_tile_entry_ptr")) == 1
+
+
+# ---------------------------------------------------------------------------
+# the pair-column table (windows of target boxes, items of one offset)
+# ---------------------------------------------------------------------------
+WIN_TARGETS, ITEM_COLS = 256, 128
+
+
+def check_windows(P, ncta=None):
+    keys = P.array("node_keys").reshape(-1, 4).astype(np.int64)
+    vptr, vidx = P.array("v_ptr"), P.array("v_idx").astype(np.int64)
+    wtp, wt = P.array("m2l_win_target_ptr"), P.array("m2l_win_targets")
+    wip, ioff = P.array("m2l_win_item_ptr"), P.array("m2l_item_offset")
+    ipp, psrc, pslot = P.array("m2l_item_pair_ptr"), P.array("m2l_pair_src"), P.array("m2l_pair_slot")
+    cptr, cwin = P.array("m2l_cta_ptr"), P.array("m2l_cta_win")
+    nwin = len(wip) - 1
+    assert nwin == P.info("m2l_windows") and len(ioff) == P.info("m2l_items")
+    # windows cut the boxes with a V list, in plan order, into <= 256
+    vlen = np.diff(vptr)
+    assert np.array_equal(wt, np.flatnonzero(vlen > 0))
+    assert wtp[0] == 0 and wtp[-1] == len(wt) and np.all(np.diff(wtp) >= 1)
+    assert np.all(np.diff(wtp) <= WIN_TARGETS)
+    # every window is dealt to exactly one block
+    assert cptr[0] == 0 and cptr[-1] == nwin and np.all(np.diff(cptr) >= 0)
+    assert np.array_equal(np.sort(cwin), np.arange(nwin))
+    if ncta is not None:
+        assert len(cptr) == ncta + 1
+    # every V pair appears once, in its target's window, at the offset whose
+    # S_t translates from the source to the target; items of a window in
+    # increasing offset order, pairs in window order, at most 128 per item
+    got = set()
+    for w in range(nwin):
+        tgt_of_slot = wt[wtp[w]:wtp[w + 1]]
+        offs = ioff[wip[w]:wip[w + 1]]
+        assert np.all(np.diff(offs) >= 0)
+        for it in range(wip[w], wip[w + 1]):
+            a, z = ipp[it], ipp[it + 1]
+            assert 1 <= z - a <= ITEM_COLS
+            sl = pslot[a:z]
+            assert np.all(np.diff(sl) > 0) and sl.min() >= 0 and sl.max() < len(tgt_of_slot)
+            tb = tgt_of_slot[sl]
+            d = keys[psrc[a:z], 1:] - keys[tb, 1:]
+            assert np.all(np.abs(d) <= 3) and np.all(np.abs(d).max(1) >= 2)
+            np.testing.assert_array_equal(
+                (d[:, 0] + 3) * 49 + (d[:, 1] + 3) * 7 + (d[:, 2] + 3),
+                OFFSET_LEX[ioff[it]])
+            for b, s in zip(tb, psrc[a:z]):
+                assert (b, s) not in got
+                got.add((b, s))
+    want = {(b, s) for b in np.flatnonzero(vlen > 0) for s in vidx[vptr[b]:vptr[b + 1]]}
+    assert got == want
+
+
+OFFSET_LEX = np.array([(a + 3) * 49 + (b + 3) * 7 + (c + 3) for a, b, c in OFFSETS])
+
+
+@pytest.mark.parametrize("gen,n,p,ncrit", [
+    (wl.uniform_cube, 20_000, 4, 32),
+    (wl.sphere_surface, 30_000, 4, 24),
+    (wl.gaussian_mixture, 15_000, 4, 8),
+], ids=["cube", "sphere", "gauss"])
+def test_pair_column_windows_cover_every_v_pair(gen, n, p, ncrit):
+    x, _ = gen(n, 11)
+    P = FMMPlan(x, p, ncrit, host_only=1)
+    check_windows(P, ncta=152)
+
+
+def test_pair_column_windows_of_a_batch_and_of_a_plan_without_v_lists():
+    xs = [wl.uniform_cube(m, 30 + m)[0] for m in (5000, 300, 12000)]
+    check_windows(FMMPlan.batch(xs, 4, 32, host_only=1))
+    P = FMMPlan(wl.uniform_cube(100, 3)[0], 4, 64, host_only=1)
+    assert P.info("v_pairs") == 0 and P.info("m2l_windows") == 0
+    check_windows(P)
+
+
+def test_pair_column_windows_balance_the_blocks():
+    x, _ = wl.sphere_surface(200_000, 12)
+    P = FMMPlan(x, 4, 32, host_only=1)
+    cptr = P.array("m2l_cta_ptr")
+    per = np.diff(cptr)
+    # a whole number of windows per block, so no block idles
+    assert per.min() == per.max() >= 1
+    check_windows(P, ncta=152)
