@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--m2l", default="bf16x3", choices=["fp32", "bf16x3", "tf32x3"])
+    ap.add_argument("--m2l-kernel", default="tiles", choices=["tiles", "pairs"],
+                    help="tensor-core M2L kernel: target tiles or pair columns")
     ap.add_argument("--eps-svd", type=float, default=None,
                     help="M2L compression tolerance (rank: singular values above eps * max); "
                          "default per workload")
@@ -400,12 +402,22 @@ def m2l_roofline(plan, mode, w, m2l_ms, peaks, peak_src, fp32_peak, sm_mhz):
     pair (counted in `achieved`), over tiles whose rows are not all filled
     (`fill`: V pairs / rows the MMAs process; `mma_flops_per_launch` counts
     the padded rows and the operand width kpad)."""
+    import numpy as np
     k = plan.info("rank_m2l")
     kpad = (k + 15) // 16 * 16
     v_pairs = plan.info("v_pairs")
-    entries = plan.info("m2l_entries")
     useful = 2.0 * k * k * v_pairs * w.nrhs
-    fill = v_pairs / max(1, entries * 128)
+    pairs_kernel = mode != "fp32" and plan.info("m2l_kernel") == 2
+    if pairs_kernel:
+        # pair columns: M = 128 coefficient rows, N = the item's pairs rounded to 16
+        cols = np.diff(plan.array("m2l_item_pair_ptr").astype(np.int64))
+        padded = float(((cols + 15) // 16 * 16).sum())
+        fill = v_pairs / max(1.0, padded)
+        mma_rows = padded * 128.0 / kpad   # in units of kpad-wide rows, as below
+    else:
+        entries = plan.info("m2l_entries")
+        fill = v_pairs / max(1, entries * 128)
+        mma_rows = entries * 128.0
     if mode == "fp32":
         tf = useful / (m2l_ms / 1e3) / 1e12
         return {"kernel": "k_m2l_simt", "bound": "alu", "achieved": tf,
@@ -415,8 +427,8 @@ def m2l_roofline(plan, mode, w, m2l_ms, peaks, peak_src, fp32_peak, sm_mhz):
                 "flops_per_launch": useful, "ms_per_launch": m2l_ms, "fill": fill}
     tc_peak = peaks["bf16_tflops"] * (1.0 if mode == "bf16x3" else 0.5)
     issued = 3 * useful
-    mma = 3 * 2.0 * kpad * kpad * 128 * entries * w.nrhs
-    return {"kernel": "k_m2l_tc", "bound": "tensor",
+    mma = 3 * 2.0 * kpad * kpad * mma_rows * w.nrhs
+    return {"kernel": "k_m2l_pc" if pairs_kernel else "k_m2l_tc", "bound": "tensor",
             "achieved": issued / (m2l_ms / 1e3) / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
             "frac": issued / (m2l_ms / 1e3) / 1e12 / tc_peak,
             "traffic": TRAFFIC.get(("k_m2l_tc", w.name, mode, kpad)),
@@ -435,7 +447,7 @@ def main():
     from paper_2303_08394_gb300 import workloads as wl
     w = wl.WORKLOADS[a.workload]
     config = {"workload": w.name, "n": w.n, "p": w.p, "ncrit": w.ncrit, "nrhs": w.nrhs,
-              "points": w.kind, "m2l": a.m2l, "eps_svd": a.eps_svd,
+              "points": w.kind, "m2l": a.m2l, "m2l_kernel": a.m2l_kernel, "eps_svd": a.eps_svd,
               "graph": "CUDA graph replay on a side stream",
               "l2_flush": "256 MB write before every step",
               "per_rank": "independent problem (seed = rank)"}
@@ -461,6 +473,7 @@ def main():
     x, q = w.generate(rank)
     t0 = time.perf_counter()
     plan = FMMPlan(x, w.p, w.ncrit, m2l_mode=modes[a.m2l], eps_svd=a.eps_svd)
+    plan.set_m2l_kernel(0 if a.m2l_kernel == "pairs" else 1)
     plan_s = time.perf_counter() - t0
     qd = torch.as_tensor(q.astype(np.float32), device=dev)
     out = torch.empty((w.n, w.nrhs), dtype=torch.float64, device=dev)

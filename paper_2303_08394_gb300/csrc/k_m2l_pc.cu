@@ -350,6 +350,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t s = 0, ph = 0, gi = 0;
             bool ready = false, ok = true;
             const int ks_last = (kp - (a.nch - 1) * F::kc) / F::kstep;
+            // operand descriptors of stage 0; stage s is kStageBytes * s further
+            const uint64_t da_hi0 = tc::sdesc_k128(tc::smem_u32(a_tile(0, 0)), 1024);
+            const uint64_t da_lo0 = tc::sdesc_k128(tc::smem_u32(a_tile(0, 1)), 1024);
+            const uint64_t db_hi0 = tc::sdesc_k128(tc::smem_u32(b_tile(0, 0)), 1024);
+            const uint64_t db_lo0 = tc::sdesc_k128(tc::smem_u32(b_tile(0, 1)), 1024);
             if (a.test_stall && blockIdx.x == 0) {
                 ok = tc::mbar_wait(done, 0, abort_flag, kTestStallLimit);
                 if (!ok && !*abort_flag) fail(5);
@@ -371,7 +376,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int n = a.m.item_pair_ptr[it + 1] - a.m.item_pair_ptr[it];
                         const uint32_t N = (uint32_t)((n + 15) & ~15);
                         const uint32_t id = tc::idesc(F::ab, 128, N);
-                        uint32_t accumulate = 0;
                         for (int c = 0; c < a.nch; ++c) {
                             if (!ready) {
                                 ok = tc::mbar_wait(&full[s], ph, abort_flag, kWaitLimit);
@@ -385,18 +389,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const uint32_t ph1 = s1 == 0 ? ph ^ 1 : ph;
                             const bool ready1 = tc::mbar_try_wait(&full[s1], ph1);
                             const int ksteps = c == a.nch - 1 ? ks_last : F::kc / F::kstep;
-                            const uint32_t ah = tc::smem_u32(a_tile(s, 0)), al = tc::smem_u32(a_tile(s, 1));
-                            const uint32_t bh = tc::smem_u32(b_tile(s, 0)), bl = tc::smem_u32(b_tile(s, 1));
-                            for (int k = 0; k < ksteps; ++k) {
-                                const uint32_t koff = (uint32_t)k * 32;
-                                const uint64_t dah = tc::sdesc_k128(ah + koff, 1024);
-                                const uint64_t dal = tc::sdesc_k128(al + koff, 1024);
-                                const uint64_t dbh = tc::sdesc_k128(bh + koff, 1024);
-                                const uint64_t dbl = tc::sdesc_k128(bl + koff, 1024);
-                                tc::mma<kTF32>(acc, dah, dbh, id, accumulate);
-                                accumulate = 1;
-                                tc::mma<kTF32>(acc, dah, dbl, id, 1);
-                                tc::mma<kTF32>(acc, dal, dbh, id, 1);
+                            const uint32_t so = s * kStageBytes;
+                            const uint64_t dah = tc::sdesc_advance(da_hi0, so);
+                            const uint64_t dal = tc::sdesc_advance(da_lo0, so);
+                            const uint64_t dbh = tc::sdesc_advance(db_hi0, so);
+                            const uint64_t dbl = tc::sdesc_advance(db_lo0, so);
+                            // K steps of 32 bytes; the first product of the
+                            // item overwrites the accumulator
+                            if (c == 0) {
+                                tc::mma_c<kTF32, false>(acc, dah, dbh, id);
+                            } else {
+                                tc::mma_c<kTF32, true>(acc, dah, dbh, id);
+                            }
+                            tc::mma_c<kTF32, true>(acc, dah, dbl, id);
+                            tc::mma_c<kTF32, true>(acc, dal, dbh, id);
+#pragma unroll
+                            for (int k = 1; k < 4; ++k) {
+                                if (k >= ksteps) break;
+                                const uint32_t kb = 32u * k;
+                                tc::mma_c<kTF32, true>(acc, tc::sdesc_advance(dah, kb),
+                                                       tc::sdesc_advance(dbh, kb), id);
+                                tc::mma_c<kTF32, true>(acc, tc::sdesc_advance(dah, kb),
+                                                       tc::sdesc_advance(dbl, kb), id);
+                                tc::mma_c<kTF32, true>(acc, tc::sdesc_advance(dal, kb),
+                                                       tc::sdesc_advance(dbh, kb), id);
                             }
                             tc::mma_commit(&empty[s]);
                             s = s1;

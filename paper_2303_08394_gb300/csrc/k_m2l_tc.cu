@@ -296,6 +296,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ready = false;
             bool ok = true;
             const int ks_last = (kp - (a.nch - 1) * F::kc) / F::kstep;
+            // operand descriptors of stage 0; stage s is stage_bytes * s further
+            const uint64_t da_hi0 = tc::sdesc_k128(tc::smem_u32(a_tile(0, 0)), 1024);
+            const uint64_t da_lo0 = tc::sdesc_k128(tc::smem_u32(a_tile(0, 1)), 1024);
+            const uint64_t db_hi0 = tc::sdesc_k128(tc::smem_u32(b_tile(0, 0)), 1024);
+            const uint64_t db_lo0 = tc::sdesc_k128(tc::smem_u32(b_tile(0, 1)), 1024);
             if (a.test_stall && blockIdx.x == 0) {
                 ok = tc::mbar_wait(done, 0, abort_flag, kTestStallLimit);
                 if (!ok && !*abort_flag) fail(5);
@@ -313,7 +318,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     tc::tc_fence_after();
-                    uint32_t accumulate = 0;
+                    bool first = true;  // the group's first product overwrites the accumulator
                     const int eend = min(e1, eg + a.group);
                     for (int e = eg; e < eend && ok; ++e) {
                         for (int c = 0; c < a.nch; ++c) {
@@ -329,18 +334,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const uint32_t ph1 = s1 == 0 ? ph ^ 1 : ph;
                             const bool ready1 = tc::mbar_try_wait(&full[s1], ph1);
                             const int ksteps = c == a.nch - 1 ? ks_last : F::kc / F::kstep;
-                            const uint32_t ah = tc::smem_u32(a_tile(s, 0)), al = tc::smem_u32(a_tile(s, 1));
-                            const uint32_t bh = tc::smem_u32(b_tile(s, 0)), bl = tc::smem_u32(b_tile(s, 1));
-                            for (int k = 0; k < ksteps; ++k) {
-                                const uint32_t koff = (uint32_t)k * 32;
-                                const uint64_t dah = tc::sdesc_k128(ah + koff, 1024);
-                                const uint64_t dal = tc::sdesc_k128(al + koff, 1024);
-                                const uint64_t dbh = tc::sdesc_k128(bh + koff, 1024);
-                                const uint64_t dbl = tc::sdesc_k128(bl + koff, 1024);
-                                tc::mma<kTF32>(tmem + acc_col, dah, dbh, id, accumulate);
-                                accumulate = 1;
-                                tc::mma<kTF32>(tmem + acc_col, dah, dbl, id, 1);
-                                tc::mma<kTF32>(tmem + acc_col, dal, dbh, id, 1);
+                            const uint32_t so = s * stage_bytes;
+                            const uint64_t dah = tc::sdesc_advance(da_hi0, so);
+                            const uint64_t dal = tc::sdesc_advance(da_lo0, so);
+                            const uint64_t dbh = tc::sdesc_advance(db_hi0, so);
+                            const uint64_t dbl = tc::sdesc_advance(db_lo0, so);
+                            const uint32_t d = tmem + acc_col;
+                            if (first) {
+                                tc::mma_c<kTF32, false>(d, dah, dbh, id);
+                                first = false;
+                            } else {
+                                tc::mma_c<kTF32, true>(d, dah, dbh, id);
+                            }
+                            tc::mma_c<kTF32, true>(d, dah, dbl, id);
+                            tc::mma_c<kTF32, true>(d, dal, dbh, id);
+#pragma unroll
+                            for (int k = 1; k < 4; ++k) {
+                                if (k >= ksteps) break;
+                                const uint32_t kb = 32u * k;
+                                tc::mma_c<kTF32, true>(d, tc::sdesc_advance(dah, kb),
+                                                       tc::sdesc_advance(dbh, kb), id);
+                                tc::mma_c<kTF32, true>(d, tc::sdesc_advance(dah, kb),
+                                                       tc::sdesc_advance(dbl, kb), id);
+                                tc::mma_c<kTF32, true>(d, tc::sdesc_advance(dal, kb),
+                                                       tc::sdesc_advance(dbh, kb), id);
                             }
                             tc::mma_commit(&empty[s]);
                             s = s1;

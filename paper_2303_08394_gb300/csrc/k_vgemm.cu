@@ -15,9 +15,10 @@
 // shapes are compiled -- 64 x 32, 32 x 64 and 128 x 16 -- and the plan's
 // autotuner picks one per call site; every shape computes each output with
 // the same K-ordered FMA chain, so the choice never changes a bit of the
-// result.  K advances in chunks of 16, copied global -> shared with
-// cp.async, kStages chunks in flight, so the per-chunk L2 round trip is paid
-// once per kStages chunks.  Missing sources and the ragged end of K are
+// result.  K advances in chunks of 32, copied global -> shared with
+// cp.async, Stages<BM> chunks in flight, so the per-chunk L2 round trip is
+// paid once per Stages<BM> chunks; the source row of each vector is looked up
+// once per segment, not per chunk.  Missing sources and the ragged end of K are
 // zero-filled by the copies themselves (source size below 16 bytes).  Every
 // source and operator row stride is a multiple of 4 floats, so each 16-byte
 // copy is aligned.
@@ -27,8 +28,10 @@ namespace kifmm {
 
 namespace {
 
-constexpr int BK = 16, kStages = 4;
+constexpr int BK = 32;
 constexpr int XLD = BK + 4;  // padded row of the vector tile (floats)
+// chunks in flight (the tiles of the widest shape take more shared memory)
+template <int BM> struct Stages { static constexpr int v = BM >= 128 ? 2 : 3; };
 // The split-K decision uses this reference shape whatever shape runs, so it
 // (and the rounding it implies) is the same for every variant.
 constexpr int kRefBM = 64, kRefBV = 32;
@@ -40,18 +43,20 @@ __device__ __forceinline__ void cp16(void *dst, const void *src, int bytes) {
                  : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_stages() {
+template <int kStages> __device__ __forceinline__ void cp_wait_stages() {
     asm volatile("cp.async.wait_group %0;" ::"n"(kStages - 1) : "memory");
 }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 template <int BM>
 __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
+    constexpr int kStages = Stages<BM>::v;
     constexpr int TR = BM / 4;          // row groups of 4
     constexpr int TV = 128 / TR;        // vector lanes
     constexpr int BV = 4 * TV;          // vectors per block
-    constexpr int XP = BV * 4;          // 16-byte pieces of one X chunk
-    constexpr int AP = BM * 4;          // 16-byte pieces of one A chunk
+    constexpr int XQ = BK / 4;          // 16-byte pieces of one vector's chunk
+    constexpr int XP = BV * XQ;         // 16-byte pieces of one X chunk
+    constexpr int AP = BM * BK / 4;     // 16-byte pieces of one A chunk
     constexpr int XH = (XP + 127) / 128, AH = AP / 128;
     static_assert(AP % 128 == 0, "whole A pieces per thread");
     __shared__ __align__(16) float As[kStages][BK][BM];     // As[.][j][i]
@@ -68,8 +73,8 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
 #pragma unroll
     for (int h = 0; h < XH; ++h) {
         const int q = tid + h * 128;
-        lv[h] = q >> 2;
-        lq[h] = q & 3;
+        lv[h] = q / XQ;
+        lq[h] = q % XQ;
         const int vload = v0 + lv[h];
         const bool in = q < XP && vload < nvec;
         pos_l[h] = in ? vload / g.nrhs : -1;
@@ -83,20 +88,37 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
     int total_chunks = 0;
     for (int s = s_first; s < s_end; ++s) total_chunks += (g.seg[s].n + BK - 1) / BK;
 
-    // copy chunk `c` (flattened over the segments) into stage `st`
+    // the issue side walks the chunks in order: segment is_, chunk icc of
+    // it, and each X piece's source row for that segment
+    int is_ = s_first, icc = 0, inch = s_first < s_end ? (g.seg[s_first].n + BK - 1) / BK : 0;
+    const float *xrow[XH];
+    auto set_rows = [&](int s) {
+        const VSeg &sg = g.seg[s];
+#pragma unroll
+        for (int h = 0; h < XH; ++h) {
+            xrow[h] = nullptr;
+            if (tid + h * 128 < XP && pos_l[h] >= 0) {
+                const int node = sg.src_idx ? sg.src_idx[pos_l[h]] : sg.src_base + pos_l[h];
+                if (node >= 0) xrow[h] = sg.src + ((size_t)node * g.nrhs + rhs_l[h]) * sg.src_ld;
+            }
+        }
+    };
+    if (s_first < s_end) set_rows(s_first);
+    // copy the next chunk (the c-th, flattened over the segments) into stage c % kStages
     auto issue = [&](int c) {
         if (c < total_chunks) {
-            int s = s_first, cc = c;
-            while (cc >= (g.seg[s].n + BK - 1) / BK) {
-                cc -= (g.seg[s].n + BK - 1) / BK;
-                ++s;
+            while (icc == inch) {
+                ++is_;
+                icc = 0;
+                inch = (g.seg[is_].n + BK - 1) / BK;
+                set_rows(is_);
             }
-            const VSeg &sg = g.seg[s];
+            const VSeg &sg = g.seg[is_];
             const int st = c % kStages;
-            const int j0 = cc * BK;
+            const int j0 = icc * BK;
 #pragma unroll
             for (int h = 0; h < AH; ++h) {
-                const int q = tid + h * 128;            // 16 rows x BM/4 pieces
+                const int q = tid + h * 128;            // BK rows x BM/4 pieces
                 const int jj = q / (BM / 4), ii = (q % (BM / 4)) * 4;
                 const int j = j0 + jj, i = i0 + ii;
                 const bool in = j < sg.n && i < mp;
@@ -107,16 +129,14 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
                 if (tid + h * 128 >= XP) continue;
                 int bytes = 0;
                 const float *src = sg.src;
-                if (pos_l[h] >= 0) {
-                    const int node = sg.src_idx ? sg.src_idx[pos_l[h]] : sg.src_base + pos_l[h];
-                    const int j = j0 + lq[h] * 4;
-                    if (node >= 0 && j < sg.n) {
-                        src = sg.src + ((size_t)node * g.nrhs + rhs_l[h]) * sg.src_ld + j;
-                        bytes = 4 * min(4, sg.n - j);
-                    }
+                const int j = j0 + lq[h] * 4;
+                if (xrow[h] && j < sg.n) {
+                    src = xrow[h] + j;
+                    bytes = 4 * min(4, sg.n - j);
                 }
                 cp16(&Xs[st][lv[h]][lq[h] * 4], src, bytes);
             }
+            ++icc;
         }
         cp_commit();
     };
@@ -130,7 +150,7 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
     for (int c = 0; c < kStages - 1; ++c) issue(c);
     for (int c = 0; c < total_chunks; ++c) {
         issue(c + kStages - 1);
-        cp_wait_stages();
+        cp_wait_stages<kStages>();
         __syncthreads();
         const int st = c % kStages;
 #pragma unroll

@@ -183,6 +183,32 @@ __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bd
             : "memory");
     }
 }
+// The same with the accumulate flag as a constant (no predicate set-up per
+// instruction): kAcc false overwrites D, true adds to it.
+template <bool kTF32, bool kAcc>
+__device__ __forceinline__ void mma_c(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                      uint32_t idsc) {
+    // the predicate comes from a compile-time constant
+    if (kTF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.eq.u32 p, %4, 1;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idsc), "r"(kAcc ? 1u : 0u)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.eq.u32 p, %4, 1;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idsc), "r"(kAcc ? 1u : 0u)
+            : "memory");
+    }
+}
+// Descriptor of the same K-major 128-byte swizzled operand advanced by
+// `bytes` along K (the address field counts 16-byte units; operand tiles
+// stay far below its 256 KB range, so the addition never carries out).
+__device__ __forceinline__ uint64_t sdesc_advance(uint64_t desc, uint32_t bytes) {
+    return desc + (uint64_t)(bytes >> 4);
+}
 // Arrive on *bar once every MMA issued so far by this thread has completed.
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile(
