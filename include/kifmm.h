@@ -311,6 +311,8 @@ enum {
     FMM_INFO_M2L_KERNEL = 22, /* M2L kernel of the current mode: 0 FP32 SIMT,
                                  1 tensor-core target tiles, 2 tensor-core
                                  pair columns */
+    FMM_INFO_TUNINGS = 23,    /* autotuning evaluations so far (one per nrhs;
+                                 the choices are kept per nrhs) */
     FMM_INFO_OPERATOR_SOURCE = 19, /* where the plan's operators came
                                  from: 0 computed, 1 this process's memory,
                                  2 the operator cache file */

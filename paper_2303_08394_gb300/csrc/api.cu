@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
 #include <stdexcept>
 #include <string>
@@ -108,26 +109,35 @@ struct fmm_plan_s {
     cudaStream_t s_side = nullptr;
     cudaEvent_t ev_side[2] = {nullptr, nullptr};
     // Autotuner: tile shape per level-product call site (in enqueue order),
-    // chosen by timing every shape during the first evaluation of each nrhs;
-    // forced_shape >= 0 applies one shape everywhere instead.
+    // chosen by timing every shape during the first evaluation of each nrhs
+    // and kept per nrhs; forced_shape >= 0 applies one shape everywhere
+    // instead.  gemm_shape holds the choices of the evaluation being
+    // enqueued.
     bool autotune = true;
     int forced_shape = -1;
-    int tuned_nrhs = 0;
     bool tuning = false;
+    std::map<int, std::vector<int>> tuned_shapes;   // nrhs -> shapes per site
     std::vector<int> gemm_shape;
     std::vector<float> gemm_ms;   // best time per site (ms) of the last tuning
-    // CUDA graph of one evaluation, replayed while its key holds: the
-    // caller's buffers, nrhs, the M2L mode and the workspace generation
+    // CUDA graphs of recent evaluations, each replayed while its key holds:
+    // the caller's buffers, nrhs, the M2L mode and kernel, and the workspace
+    // generation; the least recently used of kGraphCache is dropped first
     bool use_graph = true;
-    cudaGraphExec_t graph_exec = nullptr;
-    const void *g_charges = nullptr;
-    const void *g_pot = nullptr;
-    const void *g_grad = nullptr;
-    int g_nrhs = 0, g_mode = -1;
-    uint64_t ws_gen = 0, g_ws_gen = 0;
+    struct GraphEntry {
+        cudaGraphExec_t exec = nullptr;
+        const void *charges = nullptr, *pot = nullptr, *grad = nullptr;
+        int nrhs = 0, mode = -1, kernel = -1;
+        uint64_t ws_gen = 0, used = 0;
+    };
+    static constexpr int kGraphCache = 4;
+    GraphEntry graphs[kGraphCache];
+    uint64_t graph_clock = 0;
+    uint64_t ws_gen = 0;
     void drop_graph() {
-        if (graph_exec) cudaGraphExecDestroy(graph_exec);
-        graph_exec = nullptr;
+        for (GraphEntry &g : graphs) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            g = GraphEntry();
+        }
     }
 
     ~fmm_plan_s() {
@@ -613,26 +623,44 @@ fmm_status enqueue(fmm_plan_s *P, const float *charges, int nrhs, double *pot, d
 // the kernels are launched directly.
 fmm_status run_evaluation(fmm_plan_s *P, const float *charges, int nrhs, double *pot,
                           double *grad, cudaStream_t st) {
-    if (P->autotune && P->forced_shape < 0 && P->tuned_nrhs != nrhs) {
-        // this evaluation tunes the level products (direct launches, timed
-        // one by one) and is itself the result
-        P->tuning = true;
-        fmm_status s = enqueue(P, charges, nrhs, pot, grad, st);
-        P->tuning = false;
-        if (s != FMM_OK) return s;
-        P->tuned_nrhs = nrhs;
-        P->drop_graph();
-        return FMM_OK;
+    if (P->autotune && P->forced_shape < 0) {
+        auto it = P->tuned_shapes.find(nrhs);
+        if (it == P->tuned_shapes.end()) {
+            // this evaluation tunes the level products (direct launches,
+            // timed one by one) and is itself the result
+            P->tuning = true;
+            fmm_status s = enqueue(P, charges, nrhs, pot, grad, st);
+            P->tuning = false;
+            if (s != FMM_OK) return s;
+            P->tuned_shapes[nrhs] = P->gemm_shape;
+            return FMM_OK;
+        }
+        P->gemm_shape = it->second;
+    } else if (!P->autotune) {
+        P->gemm_shape.clear();  // the default shape everywhere
     }
     const bool legacy = st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread;
     if (!P->use_graph || legacy) return enqueue(P, charges, nrhs, pot, grad, st);
     const int mode = P->opts.m2l_mode;
-    if (P->graph_exec && P->g_charges == charges && P->g_pot == pot && P->g_grad == grad &&
-        P->g_nrhs == nrhs && P->g_mode == mode && P->g_ws_gen == P->ws_gen) {
-        CK(cudaGraphLaunch(P->graph_exec, st));
-        return FMM_OK;
+    ++P->graph_clock;
+    for (fmm_plan_s::GraphEntry &g : P->graphs)
+        if (g.exec && g.charges == charges && g.pot == pot && g.grad == grad && g.nrhs == nrhs &&
+            g.mode == mode && g.kernel == P->m2l_kernel && g.ws_gen == P->ws_gen) {
+            g.used = P->graph_clock;
+            CK(cudaGraphLaunch(g.exec, st));
+            return FMM_OK;
+        }
+    // a free entry, else the least recently used one
+    fmm_plan_s::GraphEntry *slot = &P->graphs[0];
+    for (fmm_plan_s::GraphEntry &g : P->graphs) {
+        if (!g.exec) {
+            slot = &g;
+            break;
+        }
+        if (g.used < slot->used) slot = &g;
     }
-    P->drop_graph();
+    if (slot->exec) cudaGraphExecDestroy(slot->exec);
+    *slot = fmm_plan_s::GraphEntry();
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     const int64_t before = P->last_launches;
     fmm_status s = enqueue(P, charges, nrhs, pot, grad, st);
@@ -647,19 +675,21 @@ fmm_status run_evaluation(fmm_plan_s *P, const float *charges, int nrhs, double 
         if (g) cudaGraphDestroy(g);
         return fail(FMM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     }
-    e = cudaGraphInstantiate(&P->graph_exec, g, 0);
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-        P->graph_exec = nullptr;
+    if (e != cudaSuccess)
         return fail(FMM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-    }
-    P->g_charges = charges;
-    P->g_pot = pot;
-    P->g_grad = grad;
-    P->g_nrhs = nrhs;
-    P->g_mode = mode;
-    P->g_ws_gen = P->ws_gen;
-    CK(cudaGraphLaunch(P->graph_exec, st));
+    slot->exec = exec;
+    slot->charges = charges;
+    slot->pot = pot;
+    slot->grad = grad;
+    slot->nrhs = nrhs;
+    slot->mode = mode;
+    slot->kernel = P->m2l_kernel;
+    slot->ws_gen = P->ws_gen;
+    slot->used = P->graph_clock;
+    CK(cudaGraphLaunch(exec, st));
     return FMM_OK;
 }
 
@@ -1282,7 +1312,7 @@ fmm_status fmm_plan_set_option(fmm_plan_t plan, int key, double value) {
     }
     if (key == FMM_OPT_AUTOTUNE) {
         plan->autotune = value != 0.0;
-        plan->tuned_nrhs = 0;
+        plan->tuned_shapes.clear();
         plan->drop_graph();
         return FMM_OK;
     }
@@ -1359,6 +1389,7 @@ fmm_status fmm_plan_info(fmm_plan_t P, int key, int64_t *value) {
     case FMM_INFO_M2L_TILES: *value = (int64_t)P->m2l.tile_level.size(); break;
     case FMM_INFO_M2L_ENTRIES: *value = (int64_t)P->m2l.entry_offset.size(); break;
     case FMM_INFO_LAST_LAUNCHES: *value = P->last_launches; break;
+    case FMM_INFO_TUNINGS: *value = (int64_t)P->tuned_shapes.size(); break;
     case FMM_INFO_M2L_WINDOWS: *value = (int64_t)P->m2lw.win_item_ptr.size() - 1; break;
     case FMM_INFO_M2L_ITEMS: *value = (int64_t)P->m2lw.item_offset.size(); break;
     case FMM_INFO_M2L_KERNEL:

@@ -239,3 +239,21 @@ def test_extreme_orders_every_mode(p, n, ncrit):
     assert errs["fp32"][0] <= 1e-6 and errs["tf32x3"][0] <= 1e-6, (e_ora, errs)
     assert errs["bf16x3"][0] <= 1e-5, (e_ora, errs)
     assert errs["fp32"][1] <= 1.5 * e_ora + FP32_FLOOR, (e_ora, errs)
+
+
+def test_tuned_shapes_are_kept_per_nrhs():
+    """The autotuner keeps its choice per nrhs: a caller that alternates the
+    number of charge columns tunes once per count, and every evaluation with
+    a count returns the bits of the first one."""
+    x, q = wl.gaussian_mixture(20000, 50, nrhs=3)
+    plan = FMMPlan(x, 5, 40)
+    first = {1: gpu_eval(plan, q[:, :1]), 3: gpu_eval(plan, q)}
+    assert plan.info("tunings") == 2
+    s = torch.cuda.Stream()
+    for r in (1, 3, 1, 3):
+        np.testing.assert_array_equal(gpu_eval(plan, q[:, :r]), first[r])
+        with torch.cuda.stream(s):   # graph replay for both counts
+            got = plan.evaluate(torch.as_tensor(q[:, :r].astype(np.float32), device="cuda"))
+        s.synchronize()
+        np.testing.assert_array_equal(got.cpu().numpy(), first[r])
+    assert plan.info("tunings") == 2
