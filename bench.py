@@ -542,10 +542,15 @@ def main():
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s
     p2p_pairs = plan.info("p2p_pairs")
+    surf_pairs = plan.info("surf_pairs")
     ph = mean_phases(phases)
     m2l_roof = m2l_roofline(plan, a.m2l, w, ph["m2l"], peaks, peak_src, fp32_peak, sm_mhz)
     leaf_ms = ph["leaf"]
-    near_flops = (8.0 + 2.0 * w.nrhs) * p2p_pairs
+    # every (target, source) pair the leaf kernel evaluates: the near field
+    # over U, L2P from the leaf's own downward surface and M2P from the W
+    # surfaces; the same arithmetic per pair
+    leaf_pairs = p2p_pairs + surf_pairs
+    near_flops = (8.0 + 2.0 * w.nrhs) * leaf_pairs
     leaf_tf = near_flops / (leaf_ms / 1e3) / 1e12
     leaf_roof = {"kernel": "k_eval", "bound": "alu", "achieved": leaf_tf, "peak": fp32_peak,
                  "unit": "TFLOP/s", "frac": leaf_tf / fp32_peak,
@@ -553,8 +558,9 @@ def main():
                  "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz "
                                 "(derived; no measured FP32 figure)",
                  "flops_per_launch": near_flops, "ms_per_launch": leaf_ms,
-                 "note": "near-field pair flops only (8 + 2 nrhs per pair); L2P/M2P work "
-                         "uncounted; the leaf pass is timed as one phase"}
+                 "pairs": {"near_field": p2p_pairs, "l2p_m2p": surf_pairs},
+                 "note": "8 + 2 nrhs flops per evaluated pair (near field, L2P, M2P); "
+                         "the leaf pass (its width-group launches) is timed as one phase"}
     dominant = m2l_roof if ph["m2l"] >= leaf_ms else leaf_roof
     for name, leg in legs.items():
         leg["roofline_m2l"] = m2l_roofline(plan, name, w, leg["phase_ms"]["m2l"], peaks,
@@ -563,14 +569,14 @@ def main():
         # potential + gradient: 8 (r^2, as above) + 2 (potential) + 3 (q / r^3)
         # + 6 (three FMAs) flops per near-field pair
         g_leaf = gradient["phase_ms"]["leaf"]
-        g_flops = 19.0 * p2p_pairs
+        g_flops = 19.0 * leaf_pairs
         g_tf = g_flops / (g_leaf / 1e3) / 1e12
         gradient["roofline"] = {"kernel": "k_eval (gradient variant)", "bound": "alu",
                                 "achieved": g_tf, "peak": fp32_peak, "unit": "TFLOP/s",
                                 "frac": g_tf / fp32_peak,
                                 "traffic": TRAFFIC.get(("k_eval_grad", w.name, a.m2l, None)),
                                 "flops_per_launch": g_flops, "ms_per_launch": g_leaf,
-                                "note": "near-field pair flops only (19 per pair)"}
+                                "note": "19 flops per evaluated pair (near field, L2P, M2P)"}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None

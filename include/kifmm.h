@@ -313,6 +313,10 @@ enum {
                                  pair columns */
     FMM_INFO_TUNINGS = 23,    /* autotuning evaluations so far (one per nrhs;
                                  the choices are kept per nrhs) */
+    FMM_INFO_SURF_PAIRS = 24, /* leaf-pass (point, surface point) pairs:
+                                 L2P from the leaf's own downward equivalent
+                                 surface (levels >= 2) and M2P from the
+                                 upward equivalent surface of every W box */
     FMM_INFO_OPERATOR_SOURCE = 19, /* where the plan's operators came
                                  from: 0 computed, 1 this process's memory,
                                  2 the operator cache file */

@@ -27,7 +27,8 @@ INFO = {"n": 0, "nodes": 1, "leaves": 2, "depth": 3, "nsurf": 4, "rank_m2l": 5,
         "rank_up": 6, "rank_down": 7, "u_pairs": 8, "v_pairs": 9, "w_pairs": 10,
         "x_pairs": 11, "p2p_pairs": 12, "m2l_tiles": 13, "m2l_entries": 14,
         "last_launches": 15, "points": 16, "problems": 17, "device_trees": 18, "operator_source": 19,
-        "m2l_windows": 20, "m2l_items": 21, "m2l_kernel": 22, "tunings": 23}
+        "m2l_windows": 20, "m2l_items": 21, "m2l_kernel": 22, "tunings": 23,
+        "surf_pairs": 24}
 ARRAYS = {"node_keys": (0, "i4"), "node_range": (1, "i8"), "leaf_flag": (2, "i4"),
           "perm": (3, "i8"), "u_ptr": (4, "i8"), "u_idx": (5, "i4"),
           "v_ptr": (6, "i8"), "v_idx": (7, "i4"), "w_ptr": (8, "i8"),

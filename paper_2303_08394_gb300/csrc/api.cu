@@ -1386,6 +1386,17 @@ fmm_status fmm_plan_info(fmm_plan_t P, int key, int64_t *value) {
     case FMM_INFO_W_PAIRS: *value = (int64_t)t.w_idx.size(); break;
     case FMM_INFO_X_PAIRS: *value = (int64_t)t.x_idx.size(); break;
     case FMM_INFO_P2P_PAIRS: *value = t.p2p_pairs; break;
+    case FMM_INFO_SURF_PAIRS: {
+        // the leaf pass's L2P (own downward surface, levels >= 2) and M2P
+        // (each W box's upward surface) pairs, counted like the near field
+        int64_t s = 0;
+        for (int64_t b : t.leaves) {
+            const int64_t nsurf = (t.key[4 * b] >= 2 ? 1 : 0) + (t.w_ptr[b + 1] - t.w_ptr[b]);
+            s += (t.end[b] - t.begin[b]) * nsurf;
+        }
+        *value = s * P->ops->ns;
+        break;
+    }
     case FMM_INFO_M2L_TILES: *value = (int64_t)P->m2l.tile_level.size(); break;
     case FMM_INFO_M2L_ENTRIES: *value = (int64_t)P->m2l.entry_offset.size(); break;
     case FMM_INFO_LAST_LAUNCHES: *value = P->last_launches; break;

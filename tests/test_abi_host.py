@@ -213,7 +213,7 @@ def test_batch_plan_is_the_forest_of_single_plans():
     roots = B.array("root").reshape(-1, 4)
     lists = {nm: (B.array(nm + "_ptr"), B.array(nm + "_idx")) for nm in "uvwx"}
     pt_base = row_base = 0
-    pairs = {"p2p_pairs": 0, "v_pairs": 0, "u_pairs": 0}
+    pairs = {"p2p_pairs": 0, "v_pairs": 0, "u_pairs": 0, "surf_pairs": 0}
     for i, x in enumerate(sets):
         S = FMMPlan(x, 4, 20, targets=targets[i], host_only=1)
         ids = np.nonzero(owner == i)[0]
@@ -354,3 +354,24 @@ def test_null_and_negative_arguments():
     assert L.fmm_plan_set_option(P._h, 99, 1.0) == N.FMM_ERR_INVALID_ARG
     assert L.fmm_plan_set_option(P._h, N.OPT_M2L_MODE, 7.0) == N.FMM_ERR_INVALID_ARG
     assert L.fmm_plan_set_option(P._h, N.OPT_GEMM_SHAPE, 5.0) == N.FMM_ERR_INVALID_ARG
+
+
+def test_surface_pair_count():
+    """FMM_INFO_SURF_PAIRS counts the leaf pass's surface pairs: for every
+    leaf, its points times the surface points of its own downward equivalent
+    surface (levels >= 2) and of each W box's upward equivalent surface."""
+    x, _ = wl.gaussian_mixture(6000, 3)
+    for p in (3, 5):
+        P = FMMPlan(x, p, 24, host_only=1)
+        keys = P.array("node_keys").reshape(-1, 4)
+        rng = P.array("node_range").reshape(-1, 2)
+        leaf = P.array("leaf_flag") > 0
+        wptr = P.array("w_ptr")
+        ns = 6 * (p - 1) ** 2 + 2
+        assert P.info("nsurf") == ns
+        want = 0
+        for b in np.nonzero(leaf)[0]:
+            surfaces = int(keys[b, 0] >= 2) + int(wptr[b + 1] - wptr[b])
+            want += int(rng[b, 1] - rng[b, 0]) * surfaces * ns
+        assert np.count_nonzero(np.diff(wptr)[leaf]) > 0  # W lists present
+        assert P.info("surf_pairs") == want
