@@ -79,6 +79,30 @@ __device__ __forceinline__ float two_sum(float a, float b, float &err) {
     return s;
 }
 
+// asynchronous 16- and 4-byte copies global -> shared (cp.async), their
+// commit and waits
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_one() {
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
 struct Kahan {
     float s = 0.f, c = 0.f;
     __device__ __forceinline__ void add(float x) {
@@ -147,17 +171,17 @@ __device__ __forceinline__ void pair_terms(float4 p, float3 x, float &r2, float 
 // spread over a surface most sources have a close target somewhere in the
 // leaf, but few for any one lane, so marking costs a predicated OR per
 // source and the corrections are paid per close source of the lane only.
-template <int NR, int T, bool kSelf, bool kGrad, int CAP>
-__device__ __forceinline__ void fix_source(const DevTree &t, const Smem<NR, CAP> &sm, int k,
-                                           int base, const float3 (&x)[T], int t0,
-                                           int leaf_begin, float thr2,
+template <int NR, int T, bool kSelf, bool kGrad>
+__device__ __forceinline__ void fix_source(const float4 *spos, const float4 *sres,
+                                           const float *sq, const float4 *xlo, int k, int base,
+                                           const float3 (&x)[T], int t0, int tl, float thr2,
                                            float (&part)[T][Sums<NR, kGrad>::n]) {
-    const float4 p = sm.u.st.spos[k], pl = sm.u.st.sres[k];
+    const float4 p = spos[k], pl = sres[k];
     float q[NR];
     if constexpr (NR == 1) {
         q[0] = p.w;
     } else {
-        Charges<NR>::get(sm.u.st.sq, k, q);
+        Charges<NR>::get(sq, k, q);
     }
 #pragma unroll
     for (int i = 0; i < T; ++i) {
@@ -165,7 +189,7 @@ __device__ __forceinline__ void fix_source(const DevTree &t, const Smem<NR, CAP>
         pair_terms<kSelf>(p, x[i], r2, inv);
         if (!(r2 < thr2) || (kSelf && base + k == t0 + 16 * i)) continue;
         // a close pair has a valid target: padding targets are far
-        const float4 xl = __ldg(t.pts_lo + leaf_begin + t0 + 16 * i);
+        const float4 xl = xlo[tl + 16 * i];
         const float dx = (p.x - x[i].x) + (pl.x - xl.x);
         const float dy = (p.y - x[i].y) + (pl.y - xl.y);
         const float dz = (p.z - x[i].z) + (pl.z - xl.z);
@@ -188,16 +212,19 @@ __device__ __forceinline__ void fix_source(const DevTree &t, const Smem<NR, CAP>
 }
 
 // Staged sources j = a + 2u + h (j < e; a and e multiples of 16) against
-// this lane's T targets; h is the lane's half-warp.
-// t0: index of the lane's first target among B's points (target i is
-// t0 + 16 i); B's own points are staged first, in order, so in the self run
-// a target meets itself at staged index t0 + 16 i.
-template <int NR, int T, bool kSelf, bool kGrad, int CAP>
-__device__ __forceinline__ void run(const DevTree &t, const Smem<NR, CAP> &sm, int base, int a,
-                                    int e, int h, const float3 (&x)[T], int t0, int leaf_begin,
-                                    float thr2, float (&part)[T][Sums<NR, kGrad>::n]) {
-    const float4 *spos = sm.u.st.spos;
-    const float *sq = sm.u.st.sq;
+// this lane's T targets; h is the lane's half-warp.  base + j is the
+// source's index in the window's source list; t0: index of the lane's first
+// target among B's points (target i is t0 + 16 i), and tl its slot in the
+// staged target residuals.  B's own points are listed first, in order, so
+// in the self run a target meets itself at source index t0 + 16 i.
+// kClose = false: every source of [a, e) is provably farther than
+// kCloseFrac h from every target (see far_from in leaf()), so the close
+// marking is left out; the sums are those of kClose = true.
+template <int NR, int T, bool kSelf, bool kGrad, bool kClose>
+__device__ __forceinline__ void run(const float4 *spos, const float4 *sres, const float *sq,
+                                    const float4 *xlo, int base, int a, int e, int h,
+                                    const float3 (&x)[T], int t0, int tl, float thr2,
+                                    float (&part)[T][Sums<NR, kGrad>::n]) {
     uint32_t close = 0;  // bit 8 it + u: source a + h + 16 it + 2 u has a close target
     int it = 0;
     for (int j = a + h; j < e; j += 16, ++it) {
@@ -216,7 +243,9 @@ __device__ __forceinline__ void run(const DevTree &t, const Smem<NR, CAP> &sm, i
             for (int i = 0; i < T; ++i) {
                 float r2, inv;
                 pair_terms<kSelf>(p, x[i], r2, inv);
-                if (!kSelf || base + k != t0 + 16 * i) r2min = fminf(r2min, r2);
+                if constexpr (kClose) {
+                    if (!kSelf || base + k != t0 + 16 * i) r2min = fminf(r2min, r2);
+                }
                 if constexpr (kGrad) {
                     const float w3 = q[0] * (inv * inv * inv);
                     part[i][0] = fmaf(q[0], inv, part[i][0]);
@@ -228,33 +257,62 @@ __device__ __forceinline__ void run(const DevTree &t, const Smem<NR, CAP> &sm, i
                     for (int r = 0; r < NR; ++r) part[i][r] = fmaf(q[r], inv, part[i][r]);
                 }
             }
-            if (r2min < thr2) close |= 1u << (8 * it + u);
+            if constexpr (kClose) {
+                if (r2min < thr2) close |= 1u << (8 * it + u);
+            }
         }
     }
-    // a run spans at most 64 staged sources, so four iterations of eight
+    if constexpr (kClose) {
+        // a run spans at most 64 staged sources, so four iterations of eight
 #pragma unroll 1
-    while (close) {
-        const int bit = __ffs(close) - 1;
-        close &= close - 1;
-        const int k = a + h + 16 * (bit >> 3) + 2 * (bit & 7);
-        fix_source<NR, T, kSelf, kGrad>(t, sm, k, base, x, t0, leaf_begin, thr2, part);
+        while (close) {
+            const int bit = __ffs(close) - 1;
+            close &= close - 1;
+            const int k = a + h + 16 * (bit >> 3) + 2 * (bit & 7);
+            fix_source<NR, T, kSelf, kGrad>(spos, sres, sq, xlo, k, base, x, t0, tl, thr2, part);
+        }
     }
 }
 
-template <int NR, int CAP> struct Smem {
+// Segment table of one window and the residuals of a pass's targets.
+struct SegTable {
+    float4 xlo[128];          // residuals of the chunk's 16 T <= 128 targets
+    float4 seg_off[kSegCap];  // centre offset, surface radius
+    int seg_node[kSegCap], seg_kind[kSegCap], seg_start[kSegCap + 1];
+    int warp_sum[kWarps], warp_nf[kWarps];
+};
+
+// Several columns: the block stages rounds of CAP sources together.
+template <int NR, int CAP> struct Smem : SegTable {
     union {
         struct {
             float4 spos[CAP];
             float4 sres[CAP];   // what each staged position dropped (see fix_source)
-            float sq[NR > 1 ? CAP * NR : 4];
+            float sq[CAP * NR];
         } st;
-        // partial sums of the source slices (used after the last round):
-        // T x sums per target, up to 8 x 1 (potentials) or 4 x 4 (gradients)
-        float2 red[kWarps][NR == 1 ? 16 : 4 * (NR > 4 ? NR : 4)][16];
+        // partial sums of the source slices (used after the last round)
+        float2 red[kWarps][4 * (NR > 4 ? NR : 4)][16];
     } u;
-    float4 seg_off[kSegCap];  // centre offset, surface radius
-    int seg_node[kSegCap], seg_kind[kSegCap], seg_start[kSegCap + 1];
-    int warp_sum[kWarps];
+    __device__ float2 *red(int w, int row) { return u.red[w][row]; }
+};
+
+// One column: every warp stages its own runs of 64 sources, double
+// buffered: cp.async copies the raw data of the warp's next run while it
+// computes the current one; each lane then moves its own two slots into B's
+// frame in place (position, charge in w; residual), so no block barrier
+// separates the runs.
+template <int CAP> struct Smem<1, CAP> : SegTable {
+    union {
+        struct {
+            float4 pos[kWarps][2][64];  // raw position, then staged position + charge
+            float4 lo[kWarps][2][64];   // raw point residual, then staged residual
+            float q[kWarps][2][64];     // raw charge or density
+        } w;
+        // partial sums of the source slices: T x sums per target, up to
+        // 8 x 1 (potentials) or 4 x 4 (gradients)
+        float2 red[kWarps][16][16];
+    } u;
+    __device__ float2 *red(int w, int row) { return u.red[w][row]; }
 };
 
 template <int NR, int T, bool kGrad>
@@ -272,38 +330,41 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
     const int nseg = nu + nl2p + nw;
     const int ns = o.ns, nsp = (o.ns + 3) & ~3;
 
-    // warp roles: kWarps source slices of one target chunk per pass
+    // the four warps are the source slices of one target chunk per pass
     constexpr int CH = 16 * T;
     const int nchunk = (nt + CH - 1) / CH;
-    const int nsplit = kWarps;
-    const int CW = 1;
-    const int split = wid / CW, cw = wid - split * CW;
-    const int npass = (nchunk + CW - 1) / CW;
+    const int split = wid;
     const int self_end16 = (nt + 15) & ~15;
+    const float thr = kCloseFrac * gb.w, thr2 = thr * thr;
+    // a source at least this far (L-infinity, root units) from B's cube is
+    // farther than thr from every target, with room for FP32 rounding
+    const float far_sep = 1.01f * thr;
 
-    for (int pass = 0; pass < npass; ++pass) {
-        const int chunk = pass * CW + cw;
-        const bool active = chunk < nchunk;
+    for (int chunk = 0; chunk < nchunk; ++chunk) {
         float3 x[T];
         bool valid[T];
         const int t0 = chunk * CH + tl;  // target i is B's point t0 + 16 i
 #pragma unroll
         for (int i = 0; i < T; ++i) {
             const int tt = t0 + 16 * i;
-            valid[i] = active && tt < nt;
+            valid[i] = tt < nt;
             x[i] = make_float3(-kFar, -kFar, -kFar);
             if (valid[i]) {
                 const float4 p = t.pts[rb.x + tt];
                 x[i] = make_float3(p.x, p.y, p.z);
             }
         }
-        const float thr2 = (kCloseFrac * gb.w) * (kCloseFrac * gb.w);
+        if (tid < CH) {
+            const int tt = chunk * CH + tid;
+            sm.xlo[tid] = tt < nt ? t.pts_lo[rb.x + tt] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         Kahan acc[T][NQ];
 
         for (int sw = 0; sw < nseg; sw += kSegCap) {
             const int nsegw = min(kSegCap, nseg - sw);
             // ---- segment table: logical order [B] + U\{B} + [DE(B)] + W
             int cnt2[2];
+            int nf = -1;  // last segment of this thread that may hold a close source
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) {
                 const int s = 2 * tid + hh;
@@ -324,6 +385,8 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
                     }
                     const float4 ga = t.geom[node];
                     float rad = 0.f;
+                    const float ox = ga.x - gb.x, oy = ga.y - gb.y, oz = ga.z - gb.z;
+                    bool far = false;
                     if (kind == 0) {
                         const int2 ra = t.range[node];
                         c = ra.y - ra.x;
@@ -332,9 +395,18 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
                         c = ns;
                         sm.seg_node[s] = node;
                         rad = kind == 1 ? o.ao * gb.w : o.ai * ga.w;
+                        // surface points lie on the cube of half-width rad
+                        // about the box centre: B's own downward surface
+                        // encloses B with a gap rad - h; a W box's surface
+                        // is at least max|offset| - rad - h from B's cube
+                        const float sep =
+                            kind == 1 ? rad - gb.w
+                                      : fmaxf(fabsf(ox), fmaxf(fabsf(oy), fabsf(oz))) - rad - gb.w;
+                        far = sep >= far_sep;
                     }
+                    if (!far) nf = s;
                     sm.seg_kind[s] = kind;
-                    sm.seg_off[s] = make_float4(ga.x - gb.x, ga.y - gb.y, ga.z - gb.z, rad);
+                    sm.seg_off[s] = make_float4(ox, oy, oz, rad);
                 }
                 cnt2[hh] = c;
             }
@@ -346,102 +418,190 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
                 const int v = __shfl_up_sync(0xffffffffu, incl, d);
                 if (lane >= d) incl += v;
             }
-            if (lane == 31) sm.warp_sum[wid] = incl;
+            nf = __reduce_max_sync(0xffffffffu, nf);
+            if (lane == 31) {
+                sm.warp_sum[wid] = incl;
+                sm.warp_nf[wid] = nf;
+            }
             __syncthreads();
-            int base_w = 0, total = 0;
+            int base_w = 0, total = 0, nfmax = -1;
 #pragma unroll
             for (int k = 0; k < kWarps; ++k) {
                 const int v = sm.warp_sum[k];
                 if (k < wid) base_w += v;
                 total += v;
+                nfmax = max(nfmax, sm.warp_nf[k]);
             }
             const int excl = base_w + incl - mine;
             if (2 * tid < nsegw) sm.seg_start[2 * tid] = excl;
             if (2 * tid + 1 < nsegw) sm.seg_start[2 * tid + 1] = excl + cnt2[0];
             if (tid == 0) sm.seg_start[nsegw] = total;
             __syncthreads();
+            // sources from far_from on are far from every target
+            const int far_from = sm.seg_start[nfmax + 1];
+            const int self_hi = sw == 0 ? self_end16 : 0;
 
-            // ---- rounds of at most CAP staged sources
+            // Runs of 64 sources (32 per half-warp) go round-robin to the
+            // slices: run r of the window (sources 64 r ..) to warp r mod 4,
+            // whatever the staging, so the rounding depends on the source
+            // order only.  run_sources: the sources [g0, g0 + e) of run g0 / 64
+            // are staged at spos[0 .. e).
+            auto run_sources = [&](const float4 *spos, const float4 *sres, const float *sq,
+                                   int g0, int e) {
+                const int js = min(max(self_hi - g0, 0), e);
+                float part[T][NQ];
+#pragma unroll
+                for (int i = 0; i < T; ++i)
+#pragma unroll
+                    for (int r = 0; r < NQ; ++r) part[i][r] = 0.f;
+                if (js > 0)
+                    run<NR, T, true, kGrad, true>(spos, sres, sq, sm.xlo, g0, 0, js, half, x, t0,
+                                                  tl, thr2, part);
+                if (g0 >= far_from)
+                    run<NR, T, false, kGrad, false>(spos, sres, sq, sm.xlo, g0, js, e, half, x,
+                                                    t0, tl, thr2, part);
+                else
+                    run<NR, T, false, kGrad, true>(spos, sres, sq, sm.xlo, g0, js, e, half, x,
+                                                   t0, tl, thr2, part);
+#pragma unroll
+                for (int i = 0; i < T; ++i)
+#pragma unroll
+                    for (int r = 0; r < NQ; ++r) acc[i][r].add(part[i][r]);
+            };
+
             int seg = 0;  // segment of this thread's next source (sources ascend)
-            for (int base = 0; base < total; base += CAP) {
-                const int m = min(CAP, total - base);
-                const int mp = (m + 15) & ~15;
-#pragma unroll 4
-                for (int it = 0; it < CAP / kThreads; ++it) {
-                    const int k = tid + it * kThreads;
-                    if ((k & ~31) >= mp) break;  // whole warp past the end
-                    float4 pos = make_float4(kFar, kFar, kFar, 0.f);
-                    float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
-                    float q[NR];
+            if constexpr (NR == 1) {
+                // ---- warp-private runs r = wid, wid + 4, ...; lane l stages
+                // slots l and l + 32 of each
+                const int nrun = (total + 63) >> 6;
+                float4(*wpos)[64] = sm.u.w.pos[wid];
+                float4(*wlo)[64] = sm.u.w.lo[wid];
+                float(*wq)[64] = sm.u.w.q[wid];
+                int sg_next[2];
+                auto issue = [&](int r, int bb) {
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) q[r] = 0.f;
-                    if (k < m) {
-                        // f < total = seg_start[nsegw], so the scan stops at
-                        // a segment index below nsegw
-                        const int f = base + k;
-                        while (sm.seg_start[seg + 1] <= f) ++seg;
-                        const int off = f - sm.seg_start[seg];
-                        const float4 so = sm.seg_off[seg];
-                        const int kind = sm.seg_kind[seg];
-                        if (kind == 0) {
-                            const int i = sm.seg_node[seg] + off;
-                            const float4 p = __ldg(t.pts + i), pl = __ldg(t.pts_lo + i);
-                            float ex, ey, ez;
-                            pos = make_float4(two_sum(p.x, so.x, ex), two_sum(p.y, so.y, ey),
-                                              two_sum(p.z, so.z, ez), 0.f);
-                            res = make_float4(ex + pl.x, ey + pl.y, ez + pl.z, 0.f);
-                            const float *qi = w.qs + (size_t)i * w.nrhs + r0;
-#pragma unroll
-                            for (int r = 0; r < NR; ++r) q[r] = __ldg(qi + r);
-                        } else {
-                            const float4 sp = __ldg(o.surf + off);
-                            pos = make_float4(fmaf(so.w, sp.x, so.x), fmaf(so.w, sp.y, so.y),
-                                              fmaf(so.w, sp.z, so.z), 0.f);
-                            const float *dens = kind == 1 ? w.down : w.up;
-                            const float *d =
-                                dens + ((size_t)sm.seg_node[seg] * w.nrhs + r0) * nsp + off;
-#pragma unroll
-                            for (int r = 0; r < NR; ++r) q[r] = __ldg(d + (size_t)r * nsp);
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const int k = lane + 32 * h2, f = 64 * r + k;
+                        int sg = -1;
+                        if (f < total) {
+                            // f < total = seg_start[nsegw], so the scan stops
+                            // at a segment index below nsegw
+                            while (sm.seg_start[seg + 1] <= f) ++seg;
+                            sg = seg;
+                            const int off = f - sm.seg_start[seg];
+                            const int kind = sm.seg_kind[seg];
+                            if (kind == 0) {
+                                const int i = sm.seg_node[seg] + off;
+                                cp_async16(&wpos[bb][k], t.pts + i);
+                                cp_async16(&wlo[bb][k], t.pts_lo + i);
+                                cp_async4(&wq[bb][k], w.qs + (size_t)i * w.nrhs + r0);
+                            } else {
+                                const float *dens = kind == 1 ? w.down : w.up;
+                                cp_async16(&wpos[bb][k], o.surf + off);
+                                cp_async4(&wq[bb][k],
+                                          dens + ((size_t)sm.seg_node[seg] * w.nrhs + r0) * nsp +
+                                              off);
+                            }
                         }
+                        sg_next[h2] = sg;
                     }
-                    if (k < mp) {
-                        if constexpr (NR == 1) {
-                            pos.w = q[0];
-                        } else {
+                    cp_async_commit();
+                };
+                int r = wid, bb = 0;
+                if (r < nrun) issue(r, 0);
+                for (; r < nrun; r += kWarps, bb ^= 1) {
+                    const int sg_cur[2] = {sg_next[0], sg_next[1]};
+                    if (r + kWarps < nrun) {
+                        issue(r + kWarps, bb ^ 1);
+                        cp_async_wait_one();
+                    } else {
+                        cp_async_wait_all();
+                    }
+                    // this lane's two slots into B's frame, in place
+#pragma unroll
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const int k = lane + 32 * h2, sg = sg_cur[h2];
+                        float4 pos = make_float4(kFar, kFar, kFar, 0.f);
+                        float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (sg >= 0) {
+                            const float4 so = sm.seg_off[sg], p = wpos[bb][k];
+                            const float q = wq[bb][k];
+                            if (sm.seg_kind[sg] == 0) {
+                                const float4 pl = wlo[bb][k];
+                                float ex, ey, ez;
+                                pos = make_float4(two_sum(p.x, so.x, ex), two_sum(p.y, so.y, ey),
+                                                  two_sum(p.z, so.z, ez), q);
+                                res = make_float4(ex + pl.x, ey + pl.y, ez + pl.z, 0.f);
+                            } else {
+                                pos = make_float4(fmaf(so.w, p.x, so.x), fmaf(so.w, p.y, so.y),
+                                                  fmaf(so.w, p.z, so.z), q);
+                            }
+                        }
+                        wpos[bb][k] = pos;
+                        wlo[bb][k] = res;
+                    }
+                    __syncwarp();
+                    const int g0 = 64 * r;
+                    run_sources(wpos[bb], wlo[bb], nullptr, g0,
+                                (min(64, total - g0) + 15) & ~15);
+                    __syncwarp();
+                }
+                // the next window's table replaces this one
+                __syncthreads();
+            } else {
+                // ---- rounds of at most CAP sources staged by the block
+                for (int base = 0; base < total; base += CAP) {
+                    const int m = min(CAP, total - base);
+                    const int mp = (m + 15) & ~15;
+#pragma unroll 4
+                    for (int it = 0; it < CAP / kThreads; ++it) {
+                        const int k = tid + it * kThreads;
+                        if ((k & ~31) >= mp) break;  // whole warp past the end
+                        float4 pos = make_float4(kFar, kFar, kFar, 0.f);
+                        float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
+                        float q[NR];
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) q[r] = 0.f;
+                        if (k < m) {
+                            const int f = base + k;
+                            while (sm.seg_start[seg + 1] <= f) ++seg;
+                            const int off = f - sm.seg_start[seg];
+                            const float4 so = sm.seg_off[seg];
+                            const int kind = sm.seg_kind[seg];
+                            if (kind == 0) {
+                                const int i = sm.seg_node[seg] + off;
+                                const float4 p = __ldg(t.pts + i), pl = __ldg(t.pts_lo + i);
+                                float ex, ey, ez;
+                                pos = make_float4(two_sum(p.x, so.x, ex), two_sum(p.y, so.y, ey),
+                                                  two_sum(p.z, so.z, ez), 0.f);
+                                res = make_float4(ex + pl.x, ey + pl.y, ez + pl.z, 0.f);
+                                const float *qi = w.qs + (size_t)i * w.nrhs + r0;
+#pragma unroll
+                                for (int r = 0; r < NR; ++r) q[r] = __ldg(qi + r);
+                            } else {
+                                const float4 sp = __ldg(o.surf + off);
+                                pos = make_float4(fmaf(so.w, sp.x, so.x), fmaf(so.w, sp.y, so.y),
+                                                  fmaf(so.w, sp.z, so.z), 0.f);
+                                const float *dens = kind == 1 ? w.down : w.up;
+                                const float *d =
+                                    dens + ((size_t)sm.seg_node[seg] * w.nrhs + r0) * nsp + off;
+#pragma unroll
+                                for (int r = 0; r < NR; ++r) q[r] = __ldg(d + (size_t)r * nsp);
+                            }
+                        }
+                        if (k < mp) {
 #pragma unroll
                             for (int r = 0; r < NR; ++r) sm.u.st.sq[k * NR + r] = q[r];
+                            sm.u.st.spos[k] = pos;
+                            sm.u.st.sres[k] = res;
                         }
-                        sm.u.st.spos[k] = pos;
-                        sm.u.st.sres[k] = res;
                     }
+                    __syncthreads();
+                    for (int j0 = 64 * split; j0 < mp; j0 += 64 * kWarps)
+                        run_sources(sm.u.st.spos + j0, sm.u.st.sres + j0, sm.u.st.sq + j0 * NR,
+                                    base + j0, min(64, mp - j0));
+                    __syncthreads();
                 }
-                __syncthreads();
-                if (active) {
-                    // runs of 64 sources (32 per half-warp) go round-robin to
-                    // the slices; CAP is a multiple of 256, so which slice sums
-                    // which run (and so the rounding) depends on the source
-                    // order only
-                    const int self_hi = sw == 0 ? self_end16 - base : 0;
-                    for (int j0 = 64 * split; j0 < mp; j0 += 64 * nsplit) {
-                        const int j1 = min(j0 + 64, mp);
-                        const int js = min(max(self_hi, j0), j1);
-                        float part[T][NQ];
-#pragma unroll
-                        for (int i = 0; i < T; ++i)
-#pragma unroll
-                            for (int r = 0; r < NQ; ++r) part[i][r] = 0.f;
-                        if (js > j0)
-                            run<NR, T, true, kGrad>(t, sm, base, j0, js, half, x, t0, rb.x, thr2,
-                                                    part);
-                        run<NR, T, false, kGrad>(t, sm, base, js, j1, half, x, t0, rb.x, thr2,
-                                                 part);
-#pragma unroll
-                        for (int i = 0; i < T; ++i)
-#pragma unroll
-                            for (int r = 0; r < NQ; ++r) acc[i][r].add(part[i][r]);
-                    }
-                }
-                __syncthreads();
             }
         }
 
@@ -454,21 +614,21 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
                 const float c2 = __shfl_down_sync(0xffffffffu, acc[i][r].c, 16);
                 if (half == 0) acc[i][r].merge(s2, c2);
             }
-        if (nsplit > 1 && split > 0 && active && half == 0) {
+        if (split > 0 && half == 0) {
 #pragma unroll
             for (int i = 0; i < T; ++i)
 #pragma unroll
                 for (int r = 0; r < NQ; ++r)
-                    sm.u.red[wid][i * NQ + r][tl] = make_float2(acc[i][r].s, acc[i][r].c);
+                    sm.red(wid, i * NQ + r)[tl] = make_float2(acc[i][r].s, acc[i][r].c);
         }
         __syncthreads();
-        if (split == 0 && active && half == 0) {
-            for (int s = 1; s < nsplit; ++s) {
+        if (split == 0 && half == 0) {
+            for (int s = 1; s < kWarps; ++s) {
 #pragma unroll
                 for (int i = 0; i < T; ++i)
 #pragma unroll
                     for (int r = 0; r < NQ; ++r) {
-                        const float2 v = sm.u.red[s * CW + cw][i * NQ + r][tl];
+                        const float2 v = sm.red(s, i * NQ + r)[tl];
                         acc[i][r].merge(v.x, v.y);
                     }
             }
