@@ -543,13 +543,15 @@ def main():
     fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s
     p2p_pairs = plan.info("p2p_pairs")
     surf_pairs = plan.info("surf_pairs")
+    wx_pairs = plan.info("wx_direct_pairs")
     ph = mean_phases(phases)
     m2l_roof = m2l_roofline(plan, a.m2l, w, ph["m2l"], peaks, peak_src, fp32_peak, sm_mhz)
     leaf_ms = ph["leaf"]
     # every (target, source) pair the leaf kernel evaluates: the near field
-    # over U, L2P from the leaf's own downward surface and M2P from the W
-    # surfaces; the same arithmetic per pair
-    leaf_pairs = p2p_pairs + surf_pairs
+    # over U, the small W / X leaves taken directly, L2P from the leaf's own
+    # downward surface and M2P from the other W surfaces; the same
+    # arithmetic per pair
+    leaf_pairs = p2p_pairs + wx_pairs + surf_pairs
     near_flops = (8.0 + 2.0 * w.nrhs) * leaf_pairs
     leaf_tf = near_flops / (leaf_ms / 1e3) / 1e12
     leaf_roof = {"kernel": "k_eval", "bound": "alu", "achieved": leaf_tf, "peak": fp32_peak,
@@ -558,8 +560,10 @@ def main():
                  "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz "
                                 "(derived; no measured FP32 figure)",
                  "flops_per_launch": near_flops, "ms_per_launch": leaf_ms,
-                 "pairs": {"near_field": p2p_pairs, "l2p_m2p": surf_pairs},
-                 "note": "8 + 2 nrhs flops per evaluated pair (near field, L2P, M2P); "
+                 "pairs": {"near_field": p2p_pairs, "direct_w_x": wx_pairs,
+                           "l2p_m2p": surf_pairs},
+                 "note": "8 + 2 nrhs flops per evaluated pair (near field, direct W/X "
+                         "leaves, L2P, M2P); "
                          "the leaf pass (its width-group launches) is timed as one phase"}
     dominant = m2l_roof if ph["m2l"] >= leaf_ms else leaf_roof
     for name, leg in legs.items():
@@ -576,7 +580,8 @@ def main():
                                 "frac": g_tf / fp32_peak,
                                 "traffic": TRAFFIC.get(("k_eval_grad", w.name, a.m2l, None)),
                                 "flops_per_launch": g_flops, "ms_per_launch": g_leaf,
-                                "note": "19 flops per evaluated pair (near field, L2P, M2P)"}
+                                "note": "19 flops per evaluated pair (near field, direct "
+                                        "W/X leaves, L2P, M2P)"}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -598,7 +603,8 @@ def main():
                 "plan_s": plan_s, "wall_s_timed_region": wall,
                 "tree": {key: plan.info(key) for key in
                          ("nodes", "leaves", "depth", "rank_m2l", "v_pairs", "u_pairs",
-                          "p2p_pairs", "m2l_tiles", "m2l_entries")},
+                          "p2p_pairs", "wx_direct_pairs", "surf_pairs", "m2l_tiles",
+                          "m2l_entries")},
                 "peaks": peak_src}
         if world == 1 and not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(a.workload, w, ref)

@@ -83,7 +83,15 @@ typedef struct {
     int32_t device;     /* CUDA device ordinal; -1 = current device (-1) */
     int32_t tree_build; /* fmm_tree_build: where the octree and the lists
                            are built (FMM_TREE_AUTO) */
-    int32_t reserved[6];
+    int32_t direct_wx;  /* 1: a W-list box with no more points than a
+                           surface (6(p-1)^2+2) acts on the leaf's points
+                           through its points instead of its upward
+                           equivalent surface (M2P), and a leaf with no
+                           more points than a surface takes its X list's
+                           points directly instead of through its downward
+                           check surface (P2L); exact, and fewer pairs.
+                           0: M2P and P2L for every W and X entry (1) */
+    int32_t reserved[5];
 } fmm_options;
 
 void fmm_options_init(fmm_options *opts);
@@ -172,9 +180,10 @@ enum {
                              shapes give bit-identical results.  0: the
                              default shape everywhere. */
     FMM_OPT_GEMM_SHAPE = 4,/* value -1 (default): shapes as the autotuner
-                             (or its default) chooses; 0, 1, 2: that shape
-                             (64x32, 32x64, 128x16 rows x vectors) for every
-                             level product. */
+                             (or its default) chooses; 0 .. 4: that shape
+                             (64x32, 32x64, 128x16 with 4x4 tiles per
+                             thread, 64x64, 128x32 with 8x4 tiles; rows x
+                             vectors) for every level product. */
     FMM_OPT_GRAPH = 2,    /* value 1 (default): fmm_evaluate captures its
                              kernels into a CUDA graph on the first call for
                              a given (charges, potentials, nrhs, M2L mode)
@@ -316,7 +325,10 @@ enum {
     FMM_INFO_SURF_PAIRS = 24, /* leaf-pass (point, surface point) pairs:
                                  L2P from the leaf's own downward equivalent
                                  surface (levels >= 2) and M2P from the
-                                 upward equivalent surface of every W box */
+                                 upward equivalent surface of every W box
+                                 not taken directly (see direct_wx) */
+    FMM_INFO_WX_DIRECT_PAIRS = 25, /* leaf-pass (point, point) pairs from W
+                                 boxes and X leaves taken directly */
     FMM_INFO_OPERATOR_SOURCE = 19, /* where the plan's operators came
                                  from: 0 computed, 1 this process's memory,
                                  2 the operator cache file */

@@ -17,6 +17,11 @@ What it computes, in the paper's order ("The Fast Multipole Method" and
   from level 2), then near field over U, L2P and M2P at the leaves.  Every
   operator is a kernel evaluation followed by a pseudo-inverse of a
   check-to-equivalent matrix, exactly as written, with no compression.
+* With ``direct_wx`` (the default, as in the library) a leaf with no more
+  points than a surface interacts through its points in the W and X lists:
+  as a W-list box of leaf B its points act on B's points directly (no
+  M2P), and as a box with an X list it takes the X leaves' points directly
+  (no P2L).  The sum is the same; those terms become exact.
 
 Readings where the paper is silent (each is also listed in the design
 notes of the repository):
@@ -351,8 +356,10 @@ class KIFMM:
 
     def __init__(self, points, p: int, ncrit: int, alpha_inner=1.05,
                  alpha_outer=2.95, rcond=1e-7, balance=True,
-                 max_level=KEY_BITS):
+                 max_level=KEY_BITS, direct_wx=True):
         self.tree = Octree(points, ncrit, max_level=max_level, balance=balance)
+        # small W / X leaves interact through their points (see evaluate)
+        self.direct_wx = bool(direct_wx)
         self.p = int(p)
         self.alpha_inner = float(alpha_inner)
         self.alpha_outer = float(alpha_outer)
@@ -413,6 +420,13 @@ class KIFMM:
         ne = len(self.surf)
         ai, ao = self.alpha_inner, self.alpha_outer
 
+        def small(key):
+            """A leaf with no more points than a surface: as a W-list box it
+            acts on the leaf through its points (instead of M2P), and as the
+            target of an X list it takes the X leaves' points directly
+            (instead of P2L); either way the same sum, evaluated exactly."""
+            return self.direct_wx and t.is_leaf(key) and len(t.points[key]) <= ne
+
         # P2M: leaf sources -> upward check potential -> upward density
         up = {}
         for b in t.leaves:
@@ -439,7 +453,7 @@ class KIFMM:
                     check += self._m2l_matrix(b, a) @ up[a]
                 if b in self.V:
                     m2l_check[b] = check.copy()
-                if b in self.X:
+                if b in self.X and not small(b):
                     dc = self._surface(b, ai)
                     for a in self.X[b]:
                         idx = t.points[a]
@@ -469,7 +483,15 @@ class KIFMM:
             if b[0] >= 2:
                 apply(tidx, xt, self._surface(b, ao), down[b], far)
             for a in self.W.get(b, ()):
-                apply(tidx, xt, self._surface(a, ai), up[a], far)
+                if small(a):
+                    sidx = t.points[a]
+                    apply(tidx, xt, t.x[sidx], q[sidx], far)
+                else:
+                    apply(tidx, xt, self._surface(a, ai), up[a], far)
+            if small(b):
+                for a in self.X.get(b, ()):
+                    sidx = t.points[a]
+                    apply(tidx, xt, t.x[sidx], q[sidx], far)
         self.up, self.down, self.down_check = up, down, down_check
         self.m2l_check = m2l_check
         self.near, self.far = near, far

@@ -28,7 +28,7 @@ INFO = {"n": 0, "nodes": 1, "leaves": 2, "depth": 3, "nsurf": 4, "rank_m2l": 5,
         "x_pairs": 11, "p2p_pairs": 12, "m2l_tiles": 13, "m2l_entries": 14,
         "last_launches": 15, "points": 16, "problems": 17, "device_trees": 18, "operator_source": 19,
         "m2l_windows": 20, "m2l_items": 21, "m2l_kernel": 22, "tunings": 23,
-        "surf_pairs": 24}
+        "surf_pairs": 24, "wx_direct_pairs": 25}
 ARRAYS = {"node_keys": (0, "i4"), "node_range": (1, "i8"), "leaf_flag": (2, "i4"),
           "perm": (3, "i8"), "u_ptr": (4, "i8"), "u_idx": (5, "i4"),
           "v_ptr": (6, "i8"), "v_idx": (7, "i4"), "w_ptr": (8, "i8"),
@@ -58,7 +58,7 @@ class Options(ctypes.Structure):
                 ("max_level", ctypes.c_int32), ("balance", ctypes.c_int32),
                 ("m2l_mode", ctypes.c_int32), ("host_only", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("tree_build", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("direct_wx", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class FMMError(RuntimeError):

@@ -388,6 +388,7 @@ fmm_status upload_plan(fmm_plan_s *P) {
     UP32(t.x_idx, x_idx);
     UP32(to32(t.v_ptr), v_ptr);
     UP32(P->sched.x_slot, x_slot);
+    UP32(P->sched.w_direct, w_direct);
 #undef UP32
     if ((s = P->upload(P->sched.p2m_nodes, &P->d_p2m))) return s;
     if ((s = P->upload(P->sched.m2m_nodes, &P->d_m2m))) return s;
@@ -1075,6 +1076,8 @@ fmm_status create_plan(const double *const *sources, const double *const *target
         return fail(FMM_ERR_INVALID_ARG, "unknown M2L mode");
     if (o.tree_build < FMM_TREE_AUTO || o.tree_build > FMM_TREE_LEVELS_HOST)
         return fail(FMM_ERR_INVALID_ARG, "unknown tree_build");
+    if (o.direct_wx != 0 && o.direct_wx != 1)
+        return fail(FMM_ERR_INVALID_ARG, "direct_wx is 0 or 1");
     if (o.tree_build == FMM_TREE_DEVICE && o.host_only)
         return fail(FMM_ERR_INVALID_ARG, "FMM_TREE_DEVICE needs a device (host_only is set)");
     fmm_plan_s *P = nullptr;
@@ -1171,7 +1174,9 @@ fmm_status create_plan(const double *const *sources, const double *const *target
             }
             build_m2l_windows(P->tree, nsm, P->m2lw);
         }
-        build_schedules(P->tree, kDownChunk, P->sched);
+        // points on a check or equivalent surface: 6 (p - 1)^2 + 2
+        const int nsurf = 6 * (p - 1) * (p - 1) + 2;
+        build_schedules(P->tree, kDownChunk, o.direct_wx ? nsurf : -1, P->sched);
         if (const char *hook = std::getenv("FMM_TEST_CORRUPT_TABLE"))
             corrupt_table_for_test(P, hook);
         std::string bad = check_tables(P->tree, P->sched, P->m2l, P->rows);
@@ -1270,6 +1275,7 @@ void fmm_options_init(fmm_options *o) {
     o->host_only = 0;
     o->device = -1;
     o->tree_build = FMM_TREE_AUTO;
+    o->direct_wx = 1;
 }
 
 fmm_status fmm_plan_create(const double *sources, const double *targets, int64_t n, int p,
@@ -1318,7 +1324,7 @@ fmm_status fmm_plan_set_option(fmm_plan_t plan, int key, double value) {
     }
     if (key == FMM_OPT_GEMM_SHAPE) {
         const int sh = (int)value;
-        if (sh < -1 || sh >= kGemmShapes) return fail(FMM_ERR_INVALID_ARG, "shape in [-1, 2]");
+        if (sh < -1 || sh >= kGemmShapes) return fail(FMM_ERR_INVALID_ARG, "shape in [-1, 4]");
         plan->forced_shape = sh;
         plan->drop_graph();
         return FMM_OK;
@@ -1386,15 +1392,28 @@ fmm_status fmm_plan_info(fmm_plan_t P, int key, int64_t *value) {
     case FMM_INFO_W_PAIRS: *value = (int64_t)t.w_idx.size(); break;
     case FMM_INFO_X_PAIRS: *value = (int64_t)t.x_idx.size(); break;
     case FMM_INFO_P2P_PAIRS: *value = t.p2p_pairs; break;
-    case FMM_INFO_SURF_PAIRS: {
+    case FMM_INFO_SURF_PAIRS:
+    case FMM_INFO_WX_DIRECT_PAIRS: {
         // the leaf pass's L2P (own downward surface, levels >= 2) and M2P
-        // (each W box's upward surface) pairs, counted like the near field
-        int64_t s = 0;
+        // (W boxes' upward surfaces) pairs, and its direct W / X pairs,
+        // counted like the near field
+        int64_t surf = 0, direct = 0;
         for (int64_t b : t.leaves) {
-            const int64_t nsurf = (t.key[4 * b] >= 2 ? 1 : 0) + (t.w_ptr[b + 1] - t.w_ptr[b]);
-            s += (t.end[b] - t.begin[b]) * nsurf;
+            const int64_t nb = t.end[b] - t.begin[b];
+            int64_t nsurf = t.key[4 * b] >= 2 ? 1 : 0;
+            for (int64_t e = t.w_ptr[b]; e < t.w_ptr[b + 1]; ++e) {
+                const int64_t a = t.w_idx[e];
+                if (P->sched.w_direct[a]) direct += nb * (t.end[a] - t.begin[a]);
+                else ++nsurf;
+            }
+            if (P->sched.x_slot[b] < 0)
+                for (int64_t e = t.x_ptr[b]; e < t.x_ptr[b + 1]; ++e) {
+                    const int64_t a = t.x_idx[e];
+                    direct += nb * (t.end[a] - t.begin[a]);
+                }
+            surf += nb * nsurf;
         }
-        *value = s * P->ops->ns;
+        *value = key == FMM_INFO_SURF_PAIRS ? surf * P->ops->ns : direct;
         break;
     }
     case FMM_INFO_M2L_TILES: *value = (int64_t)P->m2l.tile_level.size(); break;

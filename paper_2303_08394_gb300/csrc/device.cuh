@@ -46,7 +46,12 @@ struct DevTree {
                                    // width T (t_first[kLeafWidths] = 0,
                                    // t_first[0] = nleaves)
     const int *u_ptr, *u_idx, *w_ptr, *w_idx, *x_ptr, *x_idx, *v_ptr;
-    const int *x_slot;      // nodes: row block in the P2L buffer or -1
+    const int *x_slot;      // nodes: row block in the P2L buffer or -1; a
+                            // leaf with an X list and no slot takes the X
+                            // leaves' points in the leaf pass
+    const int *w_direct;    // nodes: 1 if the box, as a W-list entry, acts
+                            // on the leaf through its points instead of its
+                            // upward equivalent surface
 };
 
 // FP32 operators.  Every matrix is stored as the transpose AT (n x m) of
@@ -144,8 +149,9 @@ struct VGemm {
 constexpr int kSplitBlocks = 4 * 152;
 size_t vgemm_split_floats(int m, int count, int nrhs, int nseg);  // 0: no split
 // Tile shapes of the level products (rows x vectors per block): 0 = 64 x 32,
-// 1 = 32 x 64, 2 = 128 x 16.  Bit-identical results; speed differs by shape.
-constexpr int kGemmShapes = 3;
+// 1 = 32 x 64, 2 = 128 x 16 (4 x 4 per thread), 3 = 64 x 64, 4 = 128 x 32
+// (8 x 4 per thread).  Bit-identical results; speed differs by shape.
+constexpr int kGemmShapes = 5;
 cudaError_t launch_vgemm(const VGemm &g, cudaStream_t s, int shape = 0);
 
 // Upward check potentials of leaves (k_updown.cu): chk[pos*nrhs + r][j] for

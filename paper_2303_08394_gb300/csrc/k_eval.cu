@@ -5,8 +5,11 @@
 //
 // One block of 128 threads owns one target leaf B.  Its sources form a list
 // of segments: B's own points, the points of the other leaves in U(B), B's
-// downward equivalent surface (charges = downward density) and the upward
-// equivalent surface of every box in W(B) (charges = upward density).  The
+// downward equivalent surface (charges = downward density), the upward
+// equivalent surface of every box in W(B) (charges = upward density) -- or,
+// for a W box that is a leaf with no more points than a surface, its points
+// -- and, when B itself has no more points than a surface, the points of
+// the leaves in X(B) (their P2L is then skipped).  The
 // segment table is built in shared memory with a block scan; then all 128
 // threads copy up to CAP sources at once into shared memory, positions
 // shifted into B's frame (leaf-relative coordinates plus the exact dyadic
@@ -225,11 +228,11 @@ __device__ __forceinline__ void run(const float4 *spos, const float4 *sres, cons
                                     const float4 *xlo, int base, int a, int e, int h,
                                     const float3 (&x)[T], int t0, int tl, float thr2,
                                     float (&part)[T][Sums<NR, kGrad>::n]) {
-    uint32_t close = 0;  // bit 8 it + u: source a + h + 16 it + 2 u has a close target
+    uint32_t close = 0;  // bit 4 it + u: source a + h + 8 it + 2 u has a close target
     int it = 0;
-    for (int j = a + h; j < e; j += 16, ++it) {
+    for (int j = a + h; j < e; j += 8, ++it) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 4; ++u) {
             const int k = j + 2 * u;
             const float4 p = spos[k];
             float q[NR];
@@ -258,17 +261,17 @@ __device__ __forceinline__ void run(const float4 *spos, const float4 *sres, cons
                 }
             }
             if constexpr (kClose) {
-                if (r2min < thr2) close |= 1u << (8 * it + u);
+                if (r2min < thr2) close |= 1u << (4 * it + u);
             }
         }
     }
     if constexpr (kClose) {
-        // a run spans at most 64 staged sources, so four iterations of eight
+        // a run spans at most 64 staged sources, so eight iterations of four
 #pragma unroll 1
         while (close) {
             const int bit = __ffs(close) - 1;
             close &= close - 1;
-            const int k = a + h + 16 * (bit >> 3) + 2 * (bit & 7);
+            const int k = a + h + 8 * (bit >> 2) + 2 * (bit & 3);
             fix_source<NR, T, kSelf, kGrad>(spos, sres, sq, xlo, k, base, x, t0, tl, thr2, part);
         }
     }
@@ -327,7 +330,9 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
     const int u0 = t.u_ptr[b], nu = t.u_ptr[b + 1] - u0;
     const int w0 = t.w_ptr[b], nw = t.w_ptr[b + 1] - w0;
     const int nl2p = t.level[b] >= 2 ? 1 : 0;
-    const int nseg = nu + nl2p + nw;
+    // X leaves taken directly (no P2L slot for B)
+    const int x0 = t.x_ptr[b], nxd = t.x_slot[b] < 0 ? t.x_ptr[b + 1] - x0 : 0;
+    const int nseg = nu + nl2p + nw + nxd;
     const int ns = o.ns, nsp = (o.ns + 3) & ~3;
 
     // the four warps are the source slices of one target chunk per pass
@@ -363,6 +368,7 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
         for (int sw = 0; sw < nseg; sw += kSegCap) {
             const int nsegw = min(kSegCap, nseg - sw);
             // ---- segment table: logical order [B] + U\{B} + [DE(B)] + W
+            // (surfaces, or points of the small leaves) + X taken directly
             int cnt2[2];
             int nf = -1;  // last segment of this thread that may hold a close source
 #pragma unroll
@@ -379,9 +385,12 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
                     } else if (ls < nu + nl2p) {
                         node = b;
                         kind = 1;
-                    } else {
+                    } else if (ls < nu + nl2p + nw) {
                         node = t.w_idx[w0 + ls - nu - nl2p];
-                        kind = 2;
+                        kind = t.w_direct[node] ? 0 : 2;
+                    } else {
+                        node = t.x_idx[x0 + ls - nu - nl2p - nw];
+                        kind = 0;
                     }
                     const float4 ga = t.geom[node];
                     float rad = 0.f;
@@ -391,6 +400,11 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
                         const int2 ra = t.range[node];
                         c = ra.y - ra.x;
                         sm.seg_node[s] = ra.x;
+                        // a W or X leaf does not touch B: its points are at
+                        // least max|offset| - h_A - h from B's cube
+                        if (ls >= nu)
+                            far = fmaxf(fabsf(ox), fmaxf(fabsf(oy), fabsf(oz))) - ga.w - gb.w >=
+                                  far_sep;
                     } else {
                         c = ns;
                         sm.seg_node[s] = node;

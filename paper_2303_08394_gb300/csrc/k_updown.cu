@@ -78,69 +78,130 @@ __global__ void __launch_bounds__(512) k_p2m_check(DevTree t, DevOps o, DevWork 
 
 // P2L: downward check potential of box B (radius ai, normalised by h_B)
 // from the points of every leaf in X(B), for NR right-hand sides from r0.
-// One block per box and one thread per check point (the block is ns rounded
-// up to a warp); the X leaves' points are staged in shared memory in chunks
-// of the block size, shifted into B's frame (charges in the w slot when NR
-// is 1).  Each check point sums its sources in order.  No pair coincides:
-// an X(B) leaf does not touch B, so it lies at least one B-width from it,
-// and the check surface reaches only 0.05 h_B beyond B.
-template <int NR>
+// One block per box; thread j holds the check points j + nthr i (i < T).
+// The X leaves are laid end to end as segments of one source list, staged
+// in rounds of up to kXCap sources into shared memory, shifted into B's
+// frame (charges in the w slot when NR is 1), one barrier pair per round
+// however many leaves; each check point sums its sources in list order.  No
+// pair coincides: an X(B) leaf does not touch B, so it lies at least one
+// B-width from it, and the check surface reaches only 0.05 h_B beyond B.
+constexpr int kXCap = 512;      // staged sources per round
+constexpr int kXSegCap = 64;    // X leaves per table window (at most one per thread)
+constexpr int kXMaxWarps = 16;
+
+template <int NR> struct P2LSmem {
+    float4 spos[kXCap];                    // position in B's units, charge in w (NR = 1)
+    float sq[NR > 1 ? kXCap * NR : 1];     // charges (NR > 1)
+    float4 seg_shift[kXSegCap];            // (leaf centre - B's centre) / h_B
+    int seg_first[kXSegCap], seg_start[kXSegCap + 1];
+    int warp_sum[kXMaxWarps];
+};
+
+template <int NR, int T>
 __global__ void __launch_bounds__(512) k_p2l(DevTree t, DevOps o, DevWork w, const int *nodes,
                                              int r0) {
-    extern __shared__ float4 p2l_smem[];
-    float4 *spos = p2l_smem;                                     // blockDim
-    float *sq = reinterpret_cast<float *>(spos + blockDim.x);    // blockDim x NR (NR > 1)
+    __shared__ __align__(16) P2LSmem<NR> sm;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nthr = blockDim.x, nwarps = nthr >> 5;
     const int b = nodes[blockIdx.x];
     const float4 gb = t.geom[b];
     const float inv_h = 1.f / gb.w;
     const int ns = o.ns, nsp = (o.ns + 3) & ~3;
-    const int slot = t.x_slot[b];
-    const int j = threadIdx.x;
-    const float4 s = o.surf[min(j, ns - 1)];
-    const float cx = o.ai * s.x, cy = o.ai * s.y, cz = o.ai * s.z;
-    float acc[NR];
+    float cx[T], cy[T], cz[T], acc[T][NR];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) acc[r] = 0.f;
-    for (int e = t.x_ptr[b]; e < t.x_ptr[b + 1]; ++e) {
-        const int a = t.x_idx[e];
-        const float4 ga = t.geom[a];
-        const float sx = (ga.x - gb.x) * inv_h, sy = (ga.y - gb.y) * inv_h,
-                    sz = (ga.z - gb.z) * inv_h;
-        const int2 rg = t.range[a];
-        for (int i0 = rg.x; i0 < rg.y; i0 += blockDim.x) {
-            __syncthreads();
-            const int i = i0 + threadIdx.x;
-            if (i < rg.y) {
-                const float4 p = t.pts[i];
-                float4 v = make_float4(p.x * inv_h + sx, p.y * inv_h + sy, p.z * inv_h + sz, 0.f);
+    for (int i = 0; i < T; ++i) {
+        const float4 s = o.surf[min(tid + nthr * i, ns - 1)];
+        cx[i] = o.ai * s.x;
+        cy[i] = o.ai * s.y;
+        cz[i] = o.ai * s.z;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[i][r] = 0.f;
+    }
+    const int l0 = t.x_ptr[b], nlist = t.x_ptr[b + 1] - l0;
+    const int segcap = min(kXSegCap, nthr);
+    for (int sw = 0; sw < nlist; sw += segcap) {
+        const int nsegw = min(segcap, nlist - sw);
+        // ---- segment table: the window's X leaves, shifts and offsets
+        int c = 0;
+        if (tid < nsegw) {
+            const int a = t.x_idx[l0 + sw + tid];
+            const int2 ra = t.range[a];
+            const float4 ga = t.geom[a];
+            c = ra.y - ra.x;
+            sm.seg_first[tid] = ra.x;
+            sm.seg_shift[tid] = make_float4((ga.x - gb.x) * inv_h, (ga.y - gb.y) * inv_h,
+                                            (ga.z - gb.z) * inv_h, 0.f);
+        }
+        int incl = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += v;
+        }
+        if (lane == 31) sm.warp_sum[wid] = incl;
+        __syncthreads();
+        int base_w = 0, total = 0;
+        for (int k = 0; k < nwarps; ++k) {
+            const int v = sm.warp_sum[k];
+            if (k < wid) base_w += v;
+            total += v;
+        }
+        if (tid < nsegw) sm.seg_start[tid] = base_w + incl - c;
+        if (tid == 0) sm.seg_start[nsegw] = total;
+        __syncthreads();
+
+        // ---- rounds of at most kXCap staged sources
+        int seg = 0;  // segment of this thread's next source (sources ascend)
+        for (int base = 0; base < total; base += kXCap) {
+            const int m = min(kXCap, total - base);
+            for (int k = tid; k < m; k += nthr) {
+                // f < total = seg_start[nsegw], so the scan stops below nsegw
+                const int f = base + k;
+                while (sm.seg_start[seg + 1] <= f) ++seg;
+                const int i = sm.seg_first[seg] + f - sm.seg_start[seg];
+                const float4 p = __ldg(t.pts + i);
+                const float4 sh = sm.seg_shift[seg];
+                float4 v = make_float4(fmaf(p.x, inv_h, sh.x), fmaf(p.y, inv_h, sh.y),
+                                       fmaf(p.z, inv_h, sh.z), 0.f);
                 const float *qi = w.qs + (size_t)i * w.nrhs + r0;
                 if constexpr (NR == 1) {
-                    v.w = qi[0];
+                    v.w = __ldg(qi);
                 } else {
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) sq[threadIdx.x * NR + r] = qi[r];
+                    for (int r = 0; r < NR; ++r) sm.sq[k * NR + r] = __ldg(qi + r);
                 }
-                spos[threadIdx.x] = v;
+                sm.spos[k] = v;
             }
             __syncthreads();
-            const int cnt = min((int)blockDim.x, rg.y - i0);
-            for (int c = 0; c < cnt; ++c) {
-                const float4 v = spos[c];
-                const float dx = cx - v.x, dy = cy - v.y, dz = cz - v.z;
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                const float inv = KIFMM_RSQRT(r2);
+#pragma unroll 2
+            for (int cc = 0; cc < m; ++cc) {
+                const float4 v = sm.spos[cc];
+                float q[NR];
                 if constexpr (NR == 1) {
-                    acc[0] = fmaf(v.w, inv, acc[0]);
+                    q[0] = v.w;
                 } else {
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) acc[r] = fmaf(sq[c * NR + r], inv, acc[r]);
+                    for (int r = 0; r < NR; ++r) q[r] = sm.sq[cc * NR + r];
+                }
+#pragma unroll
+                for (int i = 0; i < T; ++i) {
+                    const float dx = cx[i] - v.x, dy = cy[i] - v.y, dz = cz[i] - v.z;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    const float inv = KIFMM_RSQRT(r2);
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) acc[i][r] = fmaf(q[r], inv, acc[i][r]);
                 }
             }
+            __syncthreads();
         }
     }
-    if (j < ns) {
+    const size_t slot = (size_t)t.x_slot[b];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) w.xchk[((size_t)slot * w.nrhs + r0 + r) * nsp + j] = acc[r];
+    for (int i = 0; i < T; ++i) {
+        const int j = tid + nthr * i;
+        if (j >= ns) continue;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) w.xchk[(slot * w.nrhs + r0 + r) * nsp + j] = acc[i][r];
     }
 }
 
@@ -193,17 +254,18 @@ cudaError_t launch_p2m_check(const DevTree &t, const DevOps &o, const DevWork &w
 cudaError_t launch_p2l(const DevTree &t, const DevOps &o, const DevWork &w, const int *nodes,
                        int count, cudaStream_t s) {
     if (count == 0) return cudaSuccess;
-    const int threads = (o.ns + 31) & ~31;
-    if (threads > 512) return cudaErrorInvalidValue;
+    // two check points per thread
+    constexpr int T = 2;
+    const int threads = ((o.ns + T - 1) / T + 31) & ~31;
+    if (threads > 32 * kXMaxWarps) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
     for (int r0 = 0; r0 < w.nrhs && e == cudaSuccess;) {
         const int left = w.nrhs - r0;
         const int nr = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
-        const size_t smem = (size_t)threads * 16 + (nr > 1 ? (size_t)threads * nr * 4 : 0);
-        if (nr == 8) k_p2l<8><<<count, threads, smem, s>>>(t, o, w, nodes, r0);
-        else if (nr == 4) k_p2l<4><<<count, threads, smem, s>>>(t, o, w, nodes, r0);
-        else if (nr == 2) k_p2l<2><<<count, threads, smem, s>>>(t, o, w, nodes, r0);
-        else k_p2l<1><<<count, threads, smem, s>>>(t, o, w, nodes, r0);
+        if (nr == 8) k_p2l<8, T><<<count, threads, 0, s>>>(t, o, w, nodes, r0);
+        else if (nr == 4) k_p2l<4, T><<<count, threads, 0, s>>>(t, o, w, nodes, r0);
+        else if (nr == 2) k_p2l<2, T><<<count, threads, 0, s>>>(t, o, w, nodes, r0);
+        else k_p2l<1, T><<<count, threads, 0, s>>>(t, o, w, nodes, r0);
         e = cudaGetLastError();
         r0 += nr;
     }

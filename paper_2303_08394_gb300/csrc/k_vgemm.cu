@@ -11,17 +11,19 @@
 // an index list (a child, the parent, the box itself, ...; -1 reads zeros).
 //
 // Tiling: a block of 128 threads computes BM output rows x BV vectors, each
-// thread a 4 x 4 register tile (rows 4*tr.., vectors tv + TV q).  Three
-// shapes are compiled -- 64 x 32, 32 x 64 and 128 x 16 -- and the plan's
-// autotuner picks one per call site; every shape computes each output with
-// the same K-ordered FMA chain, so the choice never changes a bit of the
-// result.  K advances in chunks of 32, copied global -> shared with
-// cp.async, Stages<BM> chunks in flight, so the per-chunk L2 round trip is
-// paid once per Stages<BM> chunks; the source row of each vector is looked up
-// once per segment, not per chunk.  Missing sources and the ragged end of K are
-// zero-filled by the copies themselves (source size below 16 bytes).  Every
-// source and operator row stride is a multiple of 4 floats, so each 16-byte
-// copy is aligned.
+// thread an RP x 4 register tile (rows RP*tr.., vectors tv + TV q).  Five
+// shapes are compiled -- 64 x 32, 32 x 64 and 128 x 16 with 4 x 4 tiles,
+// 64 x 64 and 128 x 32 with 8 x 4 tiles -- and the plan's autotuner picks
+// one per call site; every shape computes each output with the same
+// K-ordered FMA chain, so the choice never changes a bit of the result.
+// K advances in chunks of 32, copied global -> shared with cp.async,
+// Stages chunks in flight (as many as 48 KB of shared memory holds, up to
+// three), so the per-chunk L2 round trip is paid once per Stages chunks;
+// the source row of each vector is looked up once per segment, not per
+// chunk.  Missing sources and the ragged end of K are zero-filled by the
+// copies themselves (source size below 16 bytes).  Every source and
+// operator row stride is a multiple of 4 floats, so each 16-byte copy is
+// aligned.
 #include "device.cuh"
 
 namespace kifmm {
@@ -30,8 +32,11 @@ namespace {
 
 constexpr int BK = 32;
 constexpr int XLD = BK + 4;  // padded row of the vector tile (floats)
-// chunks in flight (the tiles of the widest shape take more shared memory)
-template <int BM> struct Stages { static constexpr int v = BM >= 128 ? 2 : 3; };
+// chunks in flight: three where they fit the 48 KB of static shared memory
+template <int BM, int BV> struct Stages {
+    static constexpr int bytes = (BK * BM + BV * XLD) * 4;
+    static constexpr int v = 3 * bytes <= 48 * 1024 ? 3 : 2;
+};
 // The split-K decision uses this reference shape whatever shape runs, so it
 // (and the rounding it implies) is the same for every variant.
 constexpr int kRefBM = 64, kRefBV = 32;
@@ -48,12 +53,13 @@ template <int kStages> __device__ __forceinline__ void cp_wait_stages() {
 }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-template <int BM>
+template <int BM, int RP>
 __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
-    constexpr int kStages = Stages<BM>::v;
-    constexpr int TR = BM / 4;          // row groups of 4
+    constexpr int TR = BM / RP;         // row groups of RP
     constexpr int TV = 128 / TR;        // vector lanes
     constexpr int BV = 4 * TV;          // vectors per block
+    constexpr int kStages = Stages<BM, BV>::v;
+    static_assert(RP % 4 == 0 && TR * TV == 128, "whole row groups and vector lanes");
     constexpr int XQ = BK / 4;          // 16-byte pieces of one vector's chunk
     constexpr int XP = BV * XQ;         // 16-byte pieces of one X chunk
     constexpr int AP = BM * BK / 4;     // 16-byte pieces of one A chunk
@@ -141,9 +147,9 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
         cp_commit();
     };
 
-    float acc[4][4];
+    float acc[RP][4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < RP; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
 
@@ -155,23 +161,48 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
         const int st = c % kStages;
 #pragma unroll
         for (int k4 = 0; k4 < BK; k4 += 4) {
-            float a[4][4], x[4][4];  // a[kk][row], x[vec][kk]
+            float x[4][4];  // x[vec][kk]
+            if constexpr (RP == 4) {
+                float a[4][4];  // a[kk][row]
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float4 t = *reinterpret_cast<const float4 *>(&As[st][k4 + e][tr * 4]);
-                a[e][0] = t.x; a[e][1] = t.y; a[e][2] = t.z; a[e][3] = t.w;
+                for (int e = 0; e < 4; ++e) {
+                    const float4 t = *reinterpret_cast<const float4 *>(&As[st][k4 + e][tr * 4]);
+                    a[e][0] = t.x; a[e][1] = t.y; a[e][2] = t.z; a[e][3] = t.w;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 t = *reinterpret_cast<const float4 *>(&Xs[st][tv + TV * q][k4]);
+                    x[q][0] = t.x; x[q][1] = t.y; x[q][2] = t.z; x[q][3] = t.w;
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a[e][p], x[q][e], acc[p][q]);
+            } else {
+                // wide tiles: the vectors first, then one k of A rows at a time
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 t = *reinterpret_cast<const float4 *>(&Xs[st][tv + TV * q][k4]);
+                    x[q][0] = t.x; x[q][1] = t.y; x[q][2] = t.z; x[q][3] = t.w;
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    float a[RP];
+#pragma unroll
+                    for (int g4 = 0; g4 < RP / 4; ++g4) {
+                        const float4 t = *reinterpret_cast<const float4 *>(
+                            &As[st][k4 + e][tr * RP + 4 * g4]);
+                        a[4 * g4] = t.x; a[4 * g4 + 1] = t.y;
+                        a[4 * g4 + 2] = t.z; a[4 * g4 + 3] = t.w;
+                    }
+#pragma unroll
+                    for (int p = 0; p < RP; ++p)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a[p], x[q][e], acc[p][q]);
+                }
             }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 t = *reinterpret_cast<const float4 *>(&Xs[st][tv + TV * q][k4]);
-                x[q][0] = t.x; x[q][1] = t.y; x[q][2] = t.z; x[q][3] = t.w;
-            }
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-#pragma unroll
-                for (int p = 0; p < 4; ++p)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a[e][p], x[q][e], acc[p][q]);
         }
         __syncthreads();
     }
@@ -186,8 +217,8 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
             const int v = v0 + tv + TV * q;
             if (v >= nvec) continue;
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                const int i = i0 + tr * 4 + p;
+            for (int p = 0; p < RP; ++p) {
+                const int i = i0 + tr * RP + p;
                 if (i >= g.m) continue;
                 pz[(size_t)v * mp + i] = g.scale ? acc[p][q] * __ldg(g.scale + i) : acc[p][q];
             }
@@ -209,8 +240,8 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
                 arow = g.add + ((size_t)an * g.nrhs + rhs) * g.add_ld + (g.add_off ? g.add_off[pos] : 0);
         }
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int i = i0 + tr * 4 + p;
+        for (int p = 0; p < RP; ++p) {
+            const int i = i0 + tr * RP + p;
             if (i >= g.m) continue;
             float r = acc[p][q];
             if (g.scale) r *= __ldg(g.scale + i);
@@ -250,12 +281,12 @@ bool wants_split(int m, int count, int nseg) {
     return nseg > 1 && blocks < kSplitBlocks;
 }
 
-template <int BM>
+template <int BM, int RP>
 cudaError_t launch_shape(const VGemm &g, int nvec, bool split, cudaStream_t s) {
-    constexpr int BV = 4 * (128 / (BM / 4));
+    constexpr int BV = 4 * (128 / (BM / RP));
     const dim3 grid((nvec + BV - 1) / BV, (g.m + BM - 1) / BM, split ? g.nseg : 1);
     if (grid.y > 65535u || grid.x > 2147483647u) return cudaErrorInvalidValue;
-    k_vgemm<BM><<<grid, 128, 0, s>>>(g);
+    k_vgemm<BM, RP><<<grid, 128, 0, s>>>(g);
     return cudaGetLastError();
 }
 
@@ -275,9 +306,11 @@ cudaError_t launch_vgemm(const VGemm &g0, cudaStream_t s, int shape) {
     const bool split = g.part && wants_split(g.m, g.count, g.nseg);
     if (!split) g.part = nullptr;
     const int nvec = g.count * g.nrhs;
-    cudaError_t e = shape == 1   ? launch_shape<32>(g, nvec, split, s)
-                    : shape == 2 ? launch_shape<128>(g, nvec, split, s)
-                                 : launch_shape<64>(g, nvec, split, s);
+    cudaError_t e = shape == 1   ? launch_shape<32, 4>(g, nvec, split, s)
+                    : shape == 2 ? launch_shape<128, 4>(g, nvec, split, s)
+                    : shape == 3 ? launch_shape<64, 8>(g, nvec, split, s)
+                    : shape == 4 ? launch_shape<128, 8>(g, nvec, split, s)
+                                 : launch_shape<64, 4>(g, nvec, split, s);
     if (!split || e != cudaSuccess) return e;
     const int64_t total = (int64_t)nvec * g.m;
     int blocks = (int)((total + 255) / 256);

@@ -185,10 +185,15 @@ struct Schedules {
     std::vector<int32_t> down_chunk;      // chunks x 4: start, count, sigma,
                                           // level (chunks never mix sigma)
     std::vector<int32_t> down_chunk_level_ptr; // depth + 2
-    std::vector<int32_t> x_nodes;         // nodes with a non-empty X list
+    std::vector<int32_t> x_nodes;         // nodes whose X list goes through P2L
     std::vector<int32_t> x_slot;          // nodes: slot in x_nodes or -1
+    std::vector<int32_t> w_direct;        // nodes: 1 for a leaf small enough
+                                          // to interact through its points
+                                          // in W and X lists
 };
-void build_schedules(const Tree &tree, int chunk, Schedules &s);
+// direct_max: leaves of at most this many points take their X lists'
+// points in the leaf pass instead of through P2L (-1: none)
+void build_schedules(const Tree &tree, int chunk, int direct_max, Schedules &s);
 
 // Check every index table the kernels read before any of it reaches the
 // device: CSR offsets non-decreasing and ending at their index count, every

@@ -700,7 +700,7 @@ void build_m2l_windows(const Tree &t, int ncta, M2LWindows &w) {
     }
 }
 
-void build_schedules(const Tree &t, int chunk, Schedules &s) {
+void build_schedules(const Tree &t, int chunk, int direct_max, Schedules &s) {
     s = Schedules();
     for (int32_t lf : t.leaves)
         if (t.key[4 * lf] >= 2) s.p2m_nodes.push_back(lf);
@@ -735,9 +735,16 @@ void build_schedules(const Tree &t, int chunk, Schedules &s) {
     s.m2m_level_ptr[t.depth + 1] = (int32_t)s.m2m_nodes.size();
     s.down_level_ptr[t.depth + 1] = (int32_t)s.down_nodes.size();
     s.down_chunk_level_ptr[t.depth + 1] = (int32_t)(s.down_chunk.size() / 4);
+    // The leaf pass takes the points of a W-list box directly when it is a
+    // leaf of at most direct_max points, and those of a leaf's X list when
+    // the leaf itself has at most direct_max points; P2L serves every other
+    // box with an X list.
+    s.w_direct.assign(t.nodes(), 0);
+    for (int32_t lf : t.leaves)
+        if (t.end[lf] - t.begin[lf] <= direct_max) s.w_direct[lf] = 1;
     s.x_slot.assign(t.nodes(), -1);
     for (int64_t b = 0; b < t.nodes(); ++b)
-        if (t.x_ptr[b + 1] > t.x_ptr[b]) {
+        if (t.x_ptr[b + 1] > t.x_ptr[b] && !(t.leaf[b] && s.w_direct[b])) {
             s.x_slot[b] = (int32_t)s.x_nodes.size();
             s.x_nodes.push_back((int32_t)b);
         }
@@ -862,6 +869,8 @@ std::string check_tables(const Tree &t, const Schedules &s, const M2LTable &m, i
     RANGE(s.x_nodes, 0, nn);
     if ((int64_t)s.x_slot.size() != nn) return "x_slot: wrong size";
     RANGE(s.x_slot, -1, (int64_t)s.x_nodes.size());
+    if ((int64_t)s.w_direct.size() != nn) return "w_direct: wrong size";
+    RANGE(s.w_direct, 0, 2);
     CHECK(check_csr("m2m_level_ptr", s.m2m_level_ptr, t.depth + 1, (int64_t)s.m2m_nodes.size()));
     CHECK(check_csr("down_level_ptr", s.down_level_ptr, t.depth + 1,
                     (int64_t)s.down_nodes.size()));

@@ -61,7 +61,7 @@ class FMMPlan:
     distinct target points (the tree is then built on the union).
     p: expansion order; ncrit: largest leaf before a split.
     Options (see include/kifmm.h): alpha_inner, alpha_outer, rcond, eps_svd,
-    max_level, balance, m2l_mode, host_only, device, tree_build.
+    max_level, balance, m2l_mode, host_only, device, tree_build, direct_wx.
     """
 
     def __init__(self, points, p: int, ncrit: int, targets=None, **options):

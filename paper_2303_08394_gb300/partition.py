@@ -18,7 +18,10 @@ threads to ranks):
   needs: the upward density of every box in V(b) (b local) and in W(b)
   (b a local leaf) that it does not already hold, and the points and charges
   of every leaf in U(b) (b a local leaf) and X(b) (b local) that another rank
-  owns.  Both come from the owning rank in one variable-size exchange.
+  owns.  Both come from the owning rank in one variable-size exchange.  A
+  W-list box that is a leaf of at most `direct_max` points acts through its
+  points (the library's direct_wx rule), so its points are sent instead of
+  its density.
 
 This module holds only the host logic (no arithmetic of the method): the
 partition, the per-rank receive and send lists, and the exchange itself over
@@ -109,10 +112,13 @@ class Partition:
         return {r: d[rank] for r, d in enumerate(self.recv_pts) if rank in d}
 
 
-def partition(tree: Tree, world: int, work: np.ndarray | None = None) -> Partition:
+def partition(tree: Tree, world: int, work: np.ndarray | None = None,
+              direct_max: int = -1) -> Partition:
     """Cut the Morton-ordered leaves into `world` ranges of about equal work
     and list what each rank receives.  Deterministic: every rank computes the
-    same partition from the same plan."""
+    same partition from the same plan.  direct_max: W-list leaves of at most
+    this many points are needed as points (the plan's surface size when its
+    direct_wx option is on, else -1)."""
     nn = len(tree.keys)
     leaves = np.flatnonzero(tree.leaf)
     leaves = leaves[np.argsort(tree.rng[leaves, 0], kind="stable")]  # Morton order
@@ -154,7 +160,12 @@ def partition(tree: Tree, world: int, work: np.ndarray | None = None) -> Partiti
             need_up.update(int(a) for a in tree.v[b])
             need_pts.update(int(a) for a in tree.x[b])
             if tree.leaf[b]:
-                need_up.update(int(a) for a in tree.w[b])
+                for a in tree.w[b]:
+                    a = int(a)
+                    if tree.leaf[a] and tree.rng[a, 1] - tree.rng[a, 0] <= direct_max:
+                        need_pts.add(a)
+                    else:
+                        need_up.add(a)
                 need_pts.update(int(a) for a in tree.u[b])
         up_from, pts_from = {}, {}
         for a in sorted(need_up):

@@ -356,22 +356,41 @@ def test_null_and_negative_arguments():
     assert L.fmm_plan_set_option(P._h, N.OPT_GEMM_SHAPE, 5.0) == N.FMM_ERR_INVALID_ARG
 
 
-def test_surface_pair_count():
-    """FMM_INFO_SURF_PAIRS counts the leaf pass's surface pairs: for every
-    leaf, its points times the surface points of its own downward equivalent
-    surface (levels >= 2) and of each W box's upward equivalent surface."""
+def test_surface_and_direct_pair_counts():
+    """FMM_INFO_SURF_PAIRS and FMM_INFO_WX_DIRECT_PAIRS count the leaf pass's
+    pairs beside the near field.  For every leaf B: its points times the
+    surface points of its own downward equivalent surface (levels >= 2) and
+    of each W box's upward surface, except that (direct_wx, the default) a
+    W box that is a leaf with no more points than a surface contributes
+    points x points, and so does every X(B) leaf when B itself has no more
+    points than a surface; without direct_wx every W box is a surface."""
     x, _ = wl.gaussian_mixture(6000, 3)
     for p in (3, 5):
-        P = FMMPlan(x, p, 24, host_only=1)
-        keys = P.array("node_keys").reshape(-1, 4)
-        rng = P.array("node_range").reshape(-1, 2)
-        leaf = P.array("leaf_flag") > 0
-        wptr = P.array("w_ptr")
         ns = 6 * (p - 1) ** 2 + 2
-        assert P.info("nsurf") == ns
-        want = 0
-        for b in np.nonzero(leaf)[0]:
-            surfaces = int(keys[b, 0] >= 2) + int(wptr[b + 1] - wptr[b])
-            want += int(rng[b, 1] - rng[b, 0]) * surfaces * ns
-        assert np.count_nonzero(np.diff(wptr)[leaf]) > 0  # W lists present
-        assert P.info("surf_pairs") == want
+        for direct in (1, 0):
+            P = FMMPlan(x, p, 24, host_only=1, direct_wx=direct)
+            keys = P.array("node_keys").reshape(-1, 4)
+            rng = P.array("node_range").reshape(-1, 2)
+            leaf = P.array("leaf_flag") > 0
+            wptr, widx = P.array("w_ptr"), P.array("w_idx")
+            xptr, xidx = P.array("x_ptr"), P.array("x_idx")
+            npts = rng[:, 1] - rng[:, 0]
+            assert P.info("nsurf") == ns
+
+            def small(a):
+                return direct and leaf[a] and npts[a] <= ns
+            surf = pairs = 0
+            for b in np.nonzero(leaf)[0]:
+                nsurf = int(keys[b, 0] >= 2)
+                for a in widx[wptr[b]:wptr[b + 1]]:
+                    if small(a):
+                        pairs += int(npts[b] * npts[a])
+                    else:
+                        nsurf += 1
+                if small(b):
+                    pairs += int(npts[b] * npts[xidx[xptr[b]:xptr[b + 1]]].sum())
+                surf += int(npts[b]) * nsurf * ns
+            assert np.count_nonzero(np.diff(wptr)[leaf]) > 0  # W lists present
+            assert P.info("surf_pairs") == surf
+            assert P.info("wx_direct_pairs") == pairs
+            assert (pairs > 0) == bool(direct)

@@ -85,6 +85,11 @@ def run_fp64(P, x, q, plant=None):
     def pts(b):
         return slice(rng[b, 0], rng[b, 1])
 
+    def small(b):
+        # a leaf with no more points than a surface takes part in W and X
+        # lists through its points (the plan's default direct_wx rule)
+        return leaf[b] and rng[b, 1] - rng[b, 0] <= ns
+
     up, qhat, chat, down = {}, {}, {}, {}
     k_p2m = lambda b: k1(AO * s, (xs[pts(b)] - cen[b]) / h[b]) @ qs[pts(b)]
     for l in range(keys[:, 0].max(), 1, -1):
@@ -108,7 +113,7 @@ def run_fp64(P, x, q, plant=None):
             y = np.zeros((rQ, nrhs))
             if b in chat:
                 y += QUk @ chat[b]
-            if len(X[b]):
+            if len(X[b]) and not small(b):
                 xchk = sum(k1(AI * s, (xs[pts(a)] - cen[b]) / h[b]) @ qs[pts(a)] for a in X[b])
                 y += Qu.T @ xchk
             if l >= 3:
@@ -122,7 +127,13 @@ def run_fp64(P, x, q, plant=None):
         if keys[b, 0] >= 2:
             acc = acc + k1((xt - cen[b]) / h[b], AO * s) @ down[b] / (4 * np.pi * h[b])
         for a in W[b]:
-            acc = acc + k1((xt - cen[a]) / h[a], AI * s) @ up[a] / (4 * np.pi * h[a])
+            if small(a):
+                acc = acc + k1(xt, xs[pts(a)]) @ qs[pts(a)] / (4 * np.pi)
+            else:
+                acc = acc + k1((xt - cen[a]) / h[a], AI * s) @ up[a] / (4 * np.pi * h[a])
+        if small(b):
+            for a in X[b]:
+                acc = acc + k1(xt, xs[pts(a)]) @ qs[pts(a)] / (4 * np.pi)
         phi[perm[pts(b)]] = acc
     return phi, dict(up=up, chat=chat, down=down, keys=keys, h=h, s=s,
                      Uk=P.array("m2l_u").reshape(ns, k))

@@ -105,22 +105,27 @@ def test_upward_densities_reproduce_source_field():
 def _far_sources_of_leaf(f, b):
     """Indices of the points whose field reaches leaf b through its local
     (downward) expansion: all points except those of U(b) leaves and of the
-    boxes in W(b)."""
+    boxes in W(b), and -- when b takes its X list directly (a leaf with no
+    more points than a surface, under direct_wx) -- of the X(b) leaves."""
     t = f.tree
     excl = set()
     for a in f.U[b]:
         excl.update(t.points[a].tolist())
     for a in f.W.get(b, ()):
         excl.update(t.points[a].tolist())
+    if f.direct_wx and len(t.points[b]) <= len(f.surf):
+        for a in f.X.get(b, ()):
+            excl.update(t.points[a].tolist())
     return np.array(sorted(set(range(len(t.x))) - excl), dtype=np.int64)
 
 
-def test_downward_density_reproduces_far_field():
+@pytest.mark.parametrize("direct_wx", [True, False])
+def test_downward_density_reproduces_far_field(direct_wx):
     """M2L, P2L and L2L together: a leaf's downward density evaluated at its
     own points equals the direct field of its far sources."""
     x, q = wl.sphere_surface(3000, 8)
     q = q[:, 0]
-    f = KIFMM(x, 6, 12)
+    f = KIFMM(x, 6, 12, direct_wx=direct_wx)
     f.evaluate(q)
     t = f.tree
     leaves = [b for b in t.leaves if b[0] >= 2]
@@ -158,3 +163,28 @@ def test_duplicate_points_and_tiny_inputs():
     assert rel(phi, direct_sum(x, q)) < 1e-4
     one = fmm(np.array([[0.2, 0.3, 0.4]]), np.array([1.0]), p=4, ncrit=1)
     assert one.shape == (1,) and one[0] == 0.0
+
+
+def test_direct_wx_rule_is_exact_for_its_terms():
+    """The direct_wx reading: small W boxes and the X lists of small leaves
+    interact through their points.  On clustered points (W and X lists in
+    use, many small leaves) both forms stay within the method's error of the
+    direct sum, the direct form is no less accurate, and the leaf step's W
+    part changes only where the rule applies."""
+    x, q = wl.gaussian_mixture(3000, 21)
+    q = q[:, 0]
+    ref = direct_sum(x, q)
+    f1 = KIFMM(x, 5, 16, direct_wx=True)
+    f0 = KIFMM(x, 5, 16, direct_wx=False)
+    phi1, phi0 = f1.evaluate(q), f0.evaluate(q)
+    t = f1.tree
+    ne = len(f1.surf)
+    small_w = sum(1 for b in t.leaves for a in f1.W.get(b, ())
+                  if t.is_leaf(a) and len(t.points[a]) <= ne)
+    small_x = sum(len(f1.X.get(b, ())) for b in t.leaves if len(t.points[b]) <= ne)
+    assert small_w > 0 and small_x > 0
+    e1, e0 = rel(phi1, ref), rel(phi0, ref)
+    assert e0 < 1e-4 and e1 <= e0 * 1.02, (e1, e0)
+    # identical near field; the far parts differ by at most the method's error
+    np.testing.assert_array_equal(f1.near, f0.near)
+    assert rel(f1.far[:, 0], f0.far[:, 0]) < 1e-3

@@ -57,7 +57,7 @@ def test_partition_covers_and_balances():
     tree = pt.Tree.from_plan(P)
     work = pt.leaf_work(tree, P.info("nsurf"))
     for world in (1, 2, 3, 5):
-        part = pt.partition(tree, world, work)
+        part = pt.partition(tree, world, work, direct_max=P.info("nsurf"))
         leaves = np.flatnonzero(tree.leaf)
         assert np.all(part.owner[leaves] >= 0) and np.all(part.owner[~tree.leaf] == -1)
         # contiguous Morton ranges, ranks in order
@@ -101,8 +101,8 @@ def _rank_main(rank, world, port, out):
         x, q = _problem()
         P = FMMPlan(x, P_ORDER, NCRIT, host_only=1)
         tree = pt.Tree.from_plan(P)
-        part = pt.partition(tree, world, pt.leaf_work(tree, P.info("nsurf")))
         ns, rP, rQ, k = (P.info(a) for a in ("nsurf", "rank_up", "rank_down", "rank_m2l"))
+        part = pt.partition(tree, world, pt.leaf_work(tree, ns), direct_max=ns)
         s = P.array("surface").reshape(ns, 3)
         Pu, Ps, Pv = (P.array("op_pu").reshape(ns, rP), P.array("op_ps"),
                       P.array("op_pv").reshape(ns, rP))
@@ -131,6 +131,9 @@ def _rank_main(rank, world, port, out):
 
         def pts(b):
             return slice(rng[b, 0], rng[b, 1])
+
+        def small(b):
+            return leaf[b] and rng[b, 1] - rng[b, 0] <= ns
 
         def children(b):
             l = keys[b, 0]
@@ -196,7 +199,7 @@ def _rank_main(rank, world, port, out):
                 if len(V[b]):
                     y += QUk @ sum(S[OFFSETS[tuple(keys[a, 1:] - keys[b, 1:])]] @ (Vk.T @ up[a])
                                    for a in V[b])
-                if len(X[b]):
+                if len(X[b]) and not small(b):
                     xchk = sum(_k1(AI * s, (xs[pts(a)] - cen[b]) / h[b]) @ qs[pts(a)]
                                for a in X[b])
                     y += Qu.T @ xchk
@@ -211,7 +214,13 @@ def _rank_main(rank, world, port, out):
             if keys[b, 0] >= 2:
                 acc = acc + _k1((xt - cen[b]) / h[b], AO * s) @ down[b] / (4 * np.pi * h[b])
             for a in W[b]:
-                acc = acc + _k1((xt - cen[a]) / h[a], AI * s) @ up[a] / (4 * np.pi * h[a])
+                if small(a):
+                    acc = acc + _k1(xt, xs[pts(a)]) @ qs[pts(a)] / (4 * np.pi)
+                else:
+                    acc = acc + _k1((xt - cen[a]) / h[a], AI * s) @ up[a] / (4 * np.pi * h[a])
+            if small(b):
+                for a in X[b]:
+                    acc = acc + _k1(xt, xs[pts(a)]) @ qs[pts(a)] / (4 * np.pi)
             for i, row in zip(perm[pts(b)], acc):
                 phi[int(i)] = row
         out[rank] = (phi, {s_: ids.tolist() for s_, ids in part.recv_up[rank].items()},
