@@ -911,7 +911,7 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
             g.count = cnt;
             g.nseg = 1;
             g.seg[0] = seg(o.QUkT, kp, b.chat, kp, P->d_chat_src + b0, 0);
-            if (!sc.x_nodes.empty()) {
+            if (sc.x_level_count[l] > 0) {  // boxes of this level with a P2L slot
                 g.seg[1] = seg(o.Qu, ns, b.xchk, nsp, P->dt.x_slot + b0, 0);
                 g.nseg = 2;
             }

@@ -187,6 +187,7 @@ struct Schedules {
     std::vector<int32_t> down_chunk_level_ptr; // depth + 2
     std::vector<int32_t> x_nodes;         // nodes whose X list goes through P2L
     std::vector<int32_t> x_slot;          // nodes: slot in x_nodes or -1
+    std::vector<int32_t> x_level_count;   // depth + 1: x_nodes per level
     std::vector<int32_t> w_direct;        // nodes: 1 for a leaf small enough
                                           // to interact through its points
                                           // in W and X lists

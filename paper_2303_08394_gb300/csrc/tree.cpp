@@ -743,10 +743,12 @@ void build_schedules(const Tree &t, int chunk, int direct_max, Schedules &s) {
     for (int32_t lf : t.leaves)
         if (t.end[lf] - t.begin[lf] <= direct_max) s.w_direct[lf] = 1;
     s.x_slot.assign(t.nodes(), -1);
+    s.x_level_count.assign(t.depth + 1, 0);
     for (int64_t b = 0; b < t.nodes(); ++b)
         if (t.x_ptr[b + 1] > t.x_ptr[b] && !(t.leaf[b] && s.w_direct[b])) {
             s.x_slot[b] = (int32_t)s.x_nodes.size();
             s.x_nodes.push_back((int32_t)b);
+            ++s.x_level_count[t.key[4 * b]];
         }
 }
 
