@@ -64,13 +64,14 @@ template <int NR, bool kGrad> struct Sums {
     static constexpr int n = kGrad ? 4 : NR;
 };
 
-// minb: resident blocks per SM the register allocation must allow; the
-// narrow widths (T <= 2, the bulk of the leaves at ncrit ~ 150) fit more.
+// minb: resident blocks per SM the register allocation must allow (the
+// largest counts that compile without spills, and measured faster than the
+// register-rich ones: the leaf pass is latency-bound, so more warps help).
 template <int NR, int T> struct Cfg {
-    // staged sources per round (a multiple of 256, see run()); the narrow
-    // widths take fewer so that more blocks fit the shared memory
-    static constexpr int cap = NR == 1 ? (T <= 3 ? 512 : 1024) : (NR == 2 ? 768 : 512);
-    static constexpr int minb = NR == 1 ? (T <= 2 ? 7 : (T == 3 ? 6 : (T == 4 ? 5 : (T <= 7 ? 4 : 3))))
+    // sources per block-staged round (several columns; a multiple of 256,
+    // see run()); one column stages per warp and does not use it
+    static constexpr int cap = NR == 1 ? 256 : (NR == 2 ? 768 : 512);
+    static constexpr int minb = NR == 1 ? (T <= 3 ? 7 : (T <= 5 ? 6 : (T <= 7 ? 5 : 4)))
                                         : (NR == 2 ? (T <= 2 ? 5 : 4) : 1);
 };
 
@@ -676,7 +677,7 @@ __device__ __forceinline__ void leaf(const DevTree &t, const DevOps &o, const De
 
 template <int NR, int T, bool kGrad>
 struct Occupancy {
-    static constexpr int minb = kGrad ? (T <= 2 ? 5 : (T == 3 ? 4 : 3)) : Cfg<NR, T>::minb;
+    static constexpr int minb = kGrad ? (T <= 2 ? 6 : (T == 3 ? 5 : 4)) : Cfg<NR, T>::minb;
 };
 
 template <int NR, int T, bool kGrad>
