@@ -418,7 +418,12 @@ enum {
     FMM_ARRAY_M2L_PAIR_SRC = 40,       /* [V pairs]: source box */
     FMM_ARRAY_M2L_PAIR_SLOT = 41,      /* [V pairs]: target's place in its window */
     FMM_ARRAY_M2L_CTA_PTR = 42,        /* [blocks+1] */
-    FMM_ARRAY_M2L_CTA_WIN = 43         /* [windows]: window ids per block */
+    FMM_ARRAY_M2L_CTA_WIN = 43,        /* [windows]: window ids per block */
+    /* the target-tile M2L's block schedule (int32; empty when the plan has
+     * fewer tiles than the device has SMs): tiles dealt longest first
+     * (cost = entries) to the least loaded persistent block */
+    FMM_ARRAY_M2L_TILE_CTA_PTR = 44,   /* [blocks+1] */
+    FMM_ARRAY_M2L_TILE_CTA_TILES = 45  /* [tiles]: tile ids per block */
 };
 /* Copy array `which` into dst (capacity `bytes`).  *needed receives the
  * size in bytes (may be NULL).  dst == NULL only queries the size. */

@@ -44,7 +44,8 @@ ARRAYS = {"node_keys": (0, "i4"), "node_range": (1, "i8"), "leaf_flag": (2, "i4"
           "m2l_win_target_ptr": (35, "i4"), "m2l_win_targets": (36, "i4"),
           "m2l_win_item_ptr": (37, "i4"), "m2l_item_offset": (38, "i4"),
           "m2l_item_pair_ptr": (39, "i4"), "m2l_pair_src": (40, "i4"),
-          "m2l_pair_slot": (41, "i4"), "m2l_cta_ptr": (42, "i4"), "m2l_cta_win": (43, "i4")}
+          "m2l_pair_slot": (41, "i4"), "m2l_cta_ptr": (42, "i4"), "m2l_cta_win": (43, "i4"),
+          "m2l_tile_cta_ptr": (44, "i4"), "m2l_tile_cta_tiles": (45, "i4")}
 
 # every symbol include/kifmm.h declares
 EXPORTS = ("fmm_options_init", "fmm_plan_create", "fmm_plan_create_ex",

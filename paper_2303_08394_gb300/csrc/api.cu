@@ -438,6 +438,14 @@ fmm_status upload_plan(fmm_plan_s *P) {
     m.entry_offset = mt;
     if ((s = P->upload(P->m2l.entry_src, &mt))) return s;
     m.entry_src = mt;
+    m.ncta = P->m2l.ncta;
+    m.cta_ptr = m.cta_tiles = nullptr;
+    if (m.ncta > 0) {
+        if ((s = P->upload(P->m2l.cta_ptr, &mt))) return s;
+        m.cta_ptr = mt;
+        if ((s = P->upload(P->m2l.cta_tiles, &mt))) return s;
+        m.cta_tiles = mt;
+    }
     {
         const M2LWindows &wt = P->m2lw;
         DevM2LPc &pc = P->dpc;
@@ -1173,6 +1181,7 @@ fmm_status create_plan(const double *const *sources, const double *const *target
                 nsm = 152;
             }
             build_m2l_windows(P->tree, nsm, P->m2lw);
+            build_m2l_schedule(nsm, P->m2l);
         }
         // points on a check or equivalent surface: 6 (p - 1)^2 + 2
         const int nsurf = 6 * (p - 1) * (p - 1) + 2;
@@ -1524,6 +1533,14 @@ fmm_status fmm_plan_get_array(fmm_plan_t P, int which, void *dst, int64_t bytes,
     WARR(FMM_ARRAY_M2L_CTA_PTR, cta_ptr)
     WARR(FMM_ARRAY_M2L_CTA_WIN, cta_win)
 #undef WARR
+    case FMM_ARRAY_M2L_TILE_CTA_PTR:
+        src = P->m2l.cta_ptr.data();
+        size = P->m2l.cta_ptr.size() * 4;
+        break;
+    case FMM_ARRAY_M2L_TILE_CTA_TILES:
+        src = P->m2l.cta_tiles.data();
+        size = P->m2l.cta_tiles.size() * 4;
+        break;
     default: return fail(FMM_ERR_INVALID_ARG, "unknown array");
     }
     if (needed) *needed = (int64_t)size;

@@ -82,6 +82,9 @@ struct DevM2L {
     const int *tile_entry_ptr;  // ntiles + 1
     const int *entry_offset;    // entries
     const int *entry_src;       // entries x 128
+    int ncta;                   // blocks of the schedule (0: none, round robin)
+    const int *cta_ptr;         // ncta + 1
+    const int *cta_tiles;       // ntiles: the tiles of each block
 };
 
 // Pair-column M2L tables (plan.h, M2LWindows).

@@ -75,6 +75,23 @@ template <bool kTF32> struct Fmt {
     static constexpr uint32_t ab = kTF32 ? 2u : 1u;
 };
 
+// The (tile, row chunk) items of this block, in the order every role walks
+// them: with a schedule, the block's tiles (dealt longest first on the
+// host) times all row chunks; without one, every gridDim-th item.
+__device__ __forceinline__ int block_items(const TcArgs &a) {
+    if (a.m.cta_ptr)
+        return (a.m.cta_ptr[blockIdx.x + 1] - a.m.cta_ptr[blockIdx.x]) * a.row_chunks;
+    return (int)blockIdx.x < a.nitems ? (a.nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1
+                                       : 0;
+}
+__device__ __forceinline__ int block_item(const TcArgs &a, int k) {
+    if (a.m.cta_ptr) {
+        const int tile = a.m.cta_tiles[a.m.cta_ptr[blockIdx.x] + k / a.row_chunks];
+        return tile * a.row_chunks + k % a.row_chunks;
+    }
+    return (int)blockIdx.x + k * (int)gridDim.x;
+}
+
 template <bool kTF32>
 __global__ void __launch_bounds__(kThreads, 1)
     k_m2l_tc(const __grid_constant__ CUtensorMap s_hi, const __grid_constant__ CUtensorMap s_lo,
@@ -148,7 +165,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int piece = lane & 7, sub = lane >> 3;
         uint32_t j = 0;
         bool ok = true;
-        for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x) {
+        for (int k = 0, nk = block_items(a); k < nk && ok; ++k) {
+            const int item = block_item(a, k);
             const int tile = item / a.row_chunks, rc = item - tile * a.row_chunks;
             const int e0 = a.m.tile_entry_ptr[tile], e1 = a.m.tile_entry_ptr[tile + 1];
             for (int e = e0; e < e1 && ok; ++e) {
@@ -204,7 +222,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
         uint32_t gi = 0;
         bool ok = true;
-        for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x) {
+        for (int k = 0, nk = block_items(a); k < nk && ok; ++k) {
+            const int item = block_item(a, k);
             const int tile = item / a.row_chunks, rc = item - tile * a.row_chunks;
             const int g = rc * 128 + row;
             const int slot = g / a.nrhs, rhs = g - slot * a.nrhs;
@@ -257,7 +276,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             uint32_t j = 0;
             bool ok = true;
-            for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x) {
+            for (int k = 0, nk = block_items(a); k < nk && ok; ++k) {
+                const int item = block_item(a, k);
                 const int tile = item / a.row_chunks;
                 const int e0 = a.m.tile_entry_ptr[tile], e1 = a.m.tile_entry_ptr[tile + 1];
                 for (int e = e0; e < e1 && ok; ++e) {
@@ -305,7 +325,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ok = tc::mbar_wait(done, 0, abort_flag, kTestStallLimit);
                 if (!ok && !*abort_flag) fail(5);
             }
-            for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x) {
+            for (int k = 0, nk = block_items(a); k < nk && ok; ++k) {
+                const int item = block_item(a, k);
                 const int tile = item / a.row_chunks;
                 const int e0 = a.m.tile_entry_ptr[tile], e1 = a.m.tile_entry_ptr[tile + 1];
                 for (int eg = e0; eg < e1 && ok; eg += a.group, ++gi) {
@@ -460,7 +481,9 @@ cudaError_t launch_m2l_tc(const DevM2L &m, const DevOps &o, const DevWork &w, in
     a.err = err;
     a.test_stall = test_stall ? 1 : 0;
     const size_t sm = m2l_tc_smem(kp, &a.stages);
-    const int grid = std::min(a.nitems, num_sms);
+    // the plan's block schedule, when it was made for this many blocks
+    if (a.m.ncta != num_sms) a.m.cta_ptr = a.m.cta_tiles = nullptr;
+    const int grid = a.m.cta_ptr ? a.m.ncta : std::min(a.nitems, num_sms);
     if (tf32)
         k_m2l_tc<true><<<grid, kThreads, sm, st>>>(s_hi, s_lo, a);
     else

@@ -19,7 +19,9 @@ namespace {
 // (the block is ns rounded up to a warp).  The leaf's points are staged in
 // shared memory, scaled to leaf units (an exact power-of-two scaling), with
 // the charge in the w slot when NR is 1; each check point sums them in
-// order.
+// order.  No pair coincides: the points lie in the leaf's cube (half-width
+// 1 in leaf units) and the check surface on the cube of half-width
+// alpha_outer > 1, at least alpha_outer - 1 away.
 template <int NR>
 __global__ void __launch_bounds__(512) k_p2m_check(DevTree t, DevOps o, DevWork w,
                                                    const int *nodes, int count, float *chk,
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(512) k_p2m_check(DevTree t, DevOps o, DevWork 
                 const float4 v = spos[c];
                 const float dx = cx - v.x, dy = cy - v.y, dz = cz - v.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
-                const float inv = r2 > 0.f ? KIFMM_RSQRT(r2) : 0.f;
+                const float inv = KIFMM_RSQRT(r2);
                 if constexpr (NR == 1) {
                     acc[0] = fmaf(v.w, inv, acc[0]);
                 } else {

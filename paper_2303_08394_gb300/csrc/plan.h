@@ -149,8 +149,16 @@ struct M2LTable {
     std::vector<int32_t> tile_entry_ptr;  // tiles + 1
     std::vector<int32_t> entry_offset;    // entries
     std::vector<int32_t> entry_src;       // entries x kTileRows (-1 none)
+    // tiles of each persistent block (empty when there are fewer tiles
+    // than blocks): cta_ptr[ncta + 1], cta_tiles[tiles]
+    int ncta = 0;
+    std::vector<int32_t> cta_ptr, cta_tiles;
 };
 void build_m2l_table(const Tree &tree, M2LTable &table);
+// Deals the tiles to `ncta` persistent blocks, longest first (cost: the
+// tile's entries), each to the least loaded block; no schedule when there
+// are fewer tiles than blocks.
+void build_m2l_schedule(int ncta, M2LTable &table);
 
 // M2L work decomposition of the pair-column tensor-core kernel: the boxes
 // with a V list, in plan order, are cut into windows of at most

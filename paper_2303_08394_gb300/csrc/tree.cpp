@@ -20,6 +20,7 @@
 //    adjacent same-level boxes that are not adjacent to B but whose parent
 //    is; X(B) = {A : B in W(A)}.
 #include <algorithm>
+#include <queue>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -579,6 +580,38 @@ void build_m2l_table(const Tree &t, M2LTable &m) {
     }
 }
 
+void build_m2l_schedule(int ncta, M2LTable &m) {
+    m.ncta = 0;
+    m.cta_ptr.clear();
+    m.cta_tiles.clear();
+    const int nt = (int)m.tile_level.size();
+    if (ncta <= 0 || nt < ncta) return;
+    std::vector<int32_t> order(nt);
+    for (int i = 0; i < nt; ++i) order[i] = i;
+    auto cost = [&](int i) { return m.tile_entry_ptr[i + 1] - m.tile_entry_ptr[i]; };
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return cost(a) > cost(b); });
+    // (load, block) min-heap: ties go to the lower block, so it is deterministic
+    std::priority_queue<std::pair<int64_t, int>, std::vector<std::pair<int64_t, int>>,
+                        std::greater<std::pair<int64_t, int>>>
+        heap;
+    for (int c = 0; c < ncta; ++c) heap.push({0, c});
+    std::vector<std::vector<int32_t>> per(ncta);
+    for (int i : order) {
+        auto top = heap.top();
+        heap.pop();
+        per[top.second].push_back(i);
+        // an entry is two K chunks of MMAs; a tile also pays its epilogue
+        heap.push({top.first + cost(i) + 1, top.second});
+    }
+    m.ncta = ncta;
+    m.cta_ptr.push_back(0);
+    for (int c = 0; c < ncta; ++c) {
+        m.cta_tiles.insert(m.cta_tiles.end(), per[c].begin(), per[c].end());
+        m.cta_ptr.push_back((int32_t)m.cta_tiles.size());
+    }
+}
+
 void build_m2l_windows(const Tree &t, int ncta, M2LWindows &w) {
     w = M2LWindows();
     w.ncta = std::max(1, ncta);
@@ -895,6 +928,15 @@ std::string check_tables(const Tree &t, const Schedules &s, const M2LTable &m, i
     RANGE(m.tile_target, -1, nn);
     RANGE(m.entry_offset, 0, kNumOffsets);
     RANGE(m.entry_src, -1, nn);
+    if (m.ncta > 0) {
+        // the block schedule: every tile exactly once
+        CHECK(check_csr("m2l cta_ptr", m.cta_ptr, m.ncta, (int64_t)m.cta_tiles.size()));
+        if ((int64_t)m.cta_tiles.size() != nt) return "m2l cta_tiles: wrong size";
+        RANGE(m.cta_tiles, 0, nt);
+        std::vector<char> seen(nt, 0);
+        for (int32_t i : m.cta_tiles)
+            if (seen[i]++) return "m2l cta_tiles: tile " + std::to_string(i) + " twice";
+    }
 #undef RANGE
 #undef CHECK
     return "";

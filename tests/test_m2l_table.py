@@ -201,3 +201,30 @@ def test_pair_column_windows_balance_the_blocks():
     # a whole number of windows per block, so no block idles
     assert per.min() == per.max() >= 1
     check_windows(P, ncta=152)
+
+
+def test_tile_schedule_deals_every_tile_once_and_balances():
+    """The target-tile M2L's block schedule: with at least as many tiles as
+    blocks, every tile goes to exactly one of the 152 blocks (host-only plans
+    assume 152 SMs), longest first to the least loaded block, so the largest
+    load exceeds the mean by less than the largest tile (cost: entries + 1);
+    with fewer tiles there is no schedule (the kernel takes every gridDim-th
+    tile)."""
+    x, _ = wl.sphere_surface(200_000, 12)
+    P = FMMPlan(x, 4, 32, host_only=1)
+    eptr = P.array("m2l_tile_entry_ptr").astype(np.int64)
+    cost = np.diff(eptr) + 1
+    nt = len(cost)
+    assert nt >= 152
+    cptr = P.array("m2l_tile_cta_ptr").astype(np.int64)
+    tiles = P.array("m2l_tile_cta_tiles").astype(np.int64)
+    assert len(cptr) == 153 and cptr[0] == 0 and cptr[-1] == nt and np.all(np.diff(cptr) >= 1)
+    assert np.array_equal(np.sort(tiles), np.arange(nt))
+    load = np.array([cost[tiles[cptr[c]:cptr[c + 1]]].sum() for c in range(152)])
+    assert load.max() - load.sum() / 152 < cost.max()
+    # the round-robin order it replaces is worse on this adaptive tree
+    rr = np.array([cost[c::152].sum() for c in range(152)])
+    assert load.max() <= rr.max()
+    small = FMMPlan(wl.uniform_cube(5000, 3)[0], 4, 64, host_only=1)
+    assert small.info("m2l_tiles") < 152
+    assert len(small.array("m2l_tile_cta_ptr")) == 0
