@@ -64,10 +64,13 @@ def reference_sample_n(reps, rate=4e3):
 
 
 # DRAM bytes (read + write) of one launch, from the ncu captures summarised
-# in profiles/.  Keyed by kernel, workload, M2L mode and M2L operand width
+# in profiles/ (the leaf pass: the sum over its width-group launches, each
+# captured cold).  Keyed by kernel, workload, M2L mode and M2L operand width
 # (kpad; the leaf kernel does not depend on it: None); any other combination
 # reports null.
-TRAFFIC = {}
+TRAFFIC = {
+    ("k_eval", "sphere_n4e6_p7_ncrit128", "bf16x3", None): 1415.7e6 + 62.4e6,
+}
 
 
 def parse():
