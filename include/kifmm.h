@@ -202,7 +202,7 @@ enum {
                              with host buffers, else the next evaluation)
                              returns FMM_ERR_TIMEOUT, roles mask 32.  The
                              plan stays usable.  No effect in FP32 mode. */
-    FMM_OPT_M2L_KERNEL = 6 /* which tensor-core M2L kernel the BF16x3 and
+    FMM_OPT_M2L_KERNEL = 6,/* which tensor-core M2L kernel the BF16x3 and
                              TF32x3 modes run: 0 the pair-column kernel
                              (each V pair one column of a product by S_t,
                              in windows of up to 256 target boxes; needs an
@@ -212,6 +212,15 @@ enum {
                              parity class per product).  Both sum each
                              target's offsets in the same order: the
                              results agree to rounding. */
+    FMM_OPT_FORCE_KNOBS = 7 /* value -1 (default): the autotuner (first
+                             evaluation of each nrhs) also times two
+                             choices that change no result and keeps the
+                             faster: the target-tile M2L's block schedule
+                             and the leaf pass's launch order (see
+                             FMM_ARRAY_TUNED_KNOBS); 0..3 sets them instead:
+                             bit 0 = longest-first M2L tile schedule (else
+                             round robin), bit 1 = leaf width groups
+                             narrowest first (else widest first). */
 };
 fmm_status fmm_plan_set_option(fmm_plan_t plan, int key, double value);
 
@@ -423,7 +432,13 @@ enum {
      * fewer tiles than the device has SMs): tiles dealt longest first
      * (cost = entries) to the least loaded persistent block */
     FMM_ARRAY_M2L_TILE_CTA_PTR = 44,   /* [blocks+1] */
-    FMM_ARRAY_M2L_TILE_CTA_TILES = 45  /* [tiles]: tile ids per block */
+    FMM_ARRAY_M2L_TILE_CTA_TILES = 45, /* [tiles]: tile ids per block */
+    FMM_ARRAY_TUNED_KNOBS = 46         /* int32 [2]: the choices of the last
+                                          evaluation: the M2L block schedule
+                                          (1 longest-first tiles, 0 round
+                                          robin) and the leaf pass's launch
+                                          order (0 widest first, 1 narrowest
+                                          first) */
 };
 /* Copy array `which` into dst (capacity `bytes`).  *needed receives the
  * size in bytes (may be NULL).  dst == NULL only queries the size. */

@@ -21,6 +21,7 @@ OPT_AUTOTUNE = 3
 OPT_GEMM_SHAPE = 4
 OPT_TEST_M2L_STALL = 5
 OPT_M2L_KERNEL = 6
+OPT_FORCE_KNOBS = 7
 TREE_AUTO, TREE_HOST, TREE_DEVICE, TREE_LEVELS_HOST = 0, 1, 2, 3
 
 INFO = {"n": 0, "nodes": 1, "leaves": 2, "depth": 3, "nsurf": 4, "rank_m2l": 5,
@@ -45,7 +46,8 @@ ARRAYS = {"node_keys": (0, "i4"), "node_range": (1, "i8"), "leaf_flag": (2, "i4"
           "m2l_win_item_ptr": (37, "i4"), "m2l_item_offset": (38, "i4"),
           "m2l_item_pair_ptr": (39, "i4"), "m2l_pair_src": (40, "i4"),
           "m2l_pair_slot": (41, "i4"), "m2l_cta_ptr": (42, "i4"), "m2l_cta_win": (43, "i4"),
-          "m2l_tile_cta_ptr": (44, "i4"), "m2l_tile_cta_tiles": (45, "i4")}
+          "m2l_tile_cta_ptr": (44, "i4"), "m2l_tile_cta_tiles": (45, "i4"),
+          "tuned_knobs": (46, "i4")}
 
 # every symbol include/kifmm.h declares
 EXPORTS = ("fmm_options_init", "fmm_plan_create", "fmm_plan_create_ex",

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <array>
 #include <map>
 #include <new>
 #include <stdexcept>
@@ -119,6 +120,14 @@ struct fmm_plan_s {
     std::map<int, std::vector<int>> tuned_shapes;   // nrhs -> shapes per site
     std::vector<int> gemm_shape;
     std::vector<float> gemm_ms;   // best time per site (ms) of the last tuning
+    // Two more tuned choices that keep every summation order (so the results
+    // are the same bits either way), kept per nrhs like the shapes:
+    // knob[0] the target-tile M2L's block schedule (1 longest-first tiles,
+    // 0 round robin), knob[1] the leaf pass's launch order (0 widest group
+    // first, 1 narrowest first).  forced_knobs >= 0 sets both (bit 0, bit 1).
+    int knob[2] = {1, 0};
+    int forced_knobs = -1;
+    std::map<int, std::array<int, 2>> tuned_knobs;
     // CUDA graphs of recent evaluations, each replayed while its key holds:
     // the caller's buffers, nrhs, the M2L mode and kernel, and the workspace
     // generation; the least recently used of kGraphCache is dropped first
@@ -638,15 +647,27 @@ fmm_status run_evaluation(fmm_plan_s *P, const float *charges, int nrhs, double 
             // this evaluation tunes the level products (direct launches,
             // timed one by one) and is itself the result
             P->tuning = true;
+            P->knob[0] = 1;
+            P->knob[1] = 0;
             fmm_status s = enqueue(P, charges, nrhs, pot, grad, st);
             P->tuning = false;
             if (s != FMM_OK) return s;
             P->tuned_shapes[nrhs] = P->gemm_shape;
+            P->tuned_knobs[nrhs] = {P->knob[0], P->knob[1]};
             return FMM_OK;
         }
         P->gemm_shape = it->second;
+        const auto kn = P->tuned_knobs.find(nrhs);
+        P->knob[0] = kn != P->tuned_knobs.end() ? kn->second[0] : 1;
+        P->knob[1] = kn != P->tuned_knobs.end() ? kn->second[1] : 0;
     } else if (!P->autotune) {
         P->gemm_shape.clear();  // the default shape everywhere
+        P->knob[0] = 1;
+        P->knob[1] = 0;
+    }
+    if (P->forced_knobs >= 0) {
+        P->knob[0] = P->forced_knobs & 1;
+        P->knob[1] = (P->forced_knobs >> 1) & 1;
     }
     const bool legacy = st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread;
     if (!P->use_graph || legacy) return enqueue(P, charges, nrhs, pot, grad, st);
@@ -719,6 +740,27 @@ cudaError_t record_phase(cudaEvent_t ev, cudaStream_t st) {
 
 // Enqueue every kernel of one evaluation on `st`, using the given
 // per-evaluation buffers (sized for nrhs, see plan_workspace_bytes).
+// Autotuning of a two-way choice that changes no result: runs each
+// alternative twice on `st` and times the second run; *best receives the
+// faster one (ties keep *best).
+template <class F>
+static cudaError_t time_choice(fmm_plan_s *P, cudaStream_t st, F &&run, int *best) {
+    float ms[2] = {0.f, 0.f};
+    for (int c = 0; c < 2; ++c)
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaError_t e;
+            if ((e = cudaEventRecord(P->tune_ev[0], st)) != cudaSuccess) return e;
+            if ((e = run(c)) != cudaSuccess) return e;
+            if ((e = cudaEventRecord(P->tune_ev[1], st)) != cudaSuccess) return e;
+            if ((e = cudaEventSynchronize(P->tune_ev[1])) != cudaSuccess) return e;
+            if ((e = cudaEventElapsedTime(&ms[c], P->tune_ev[0], P->tune_ev[1])) != cudaSuccess)
+                return e;
+        }
+    if (ms[0] < ms[1]) *best = 0;
+    else if (ms[1] < ms[0]) *best = 1;
+    return cudaSuccess;
+}
+
 fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, double *pot,
                                double *grad, const WorkBuffers &b, cudaStream_t st) {
     const Tree &t = P->tree;
@@ -883,10 +925,22 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
                 CK(launch_m2l_pc(P->dpc, P->dops, w, (int)t.nodes(), idx == 1, P->tmap[idx][0],
                                  P->tmap[idx][1], b.qh_hi, b.qh_lo, P->err_dev,
                                  P->test_m2l_stall != 0, st));
-            else
-                CK(launch_m2l_tc(P->dm, P->dops, w, (int)t.nodes(), idx == 1, P->tmap[idx][0],
-                                 P->tmap[idx][1], b.qh_hi, b.qh_lo, P->err_dev,
-                                 P->test_m2l_stall != 0, P->num_sms, st));
+            else {
+                auto m2l = [&](int sched) {
+                    DevM2L dm = P->dm;
+                    if (!sched) dm.ncta = 0;  // round robin over the tiles
+                    return launch_m2l_tc(dm, P->dops, w, (int)t.nodes(), idx == 1,
+                                         P->tmap[idx][0], P->tmap[idx][1], b.qh_hi, b.qh_lo,
+                                         P->err_dev, P->test_m2l_stall != 0, P->num_sms, st);
+                };
+                if (P->tuning && P->forced_knobs < 0 && !P->test_m2l_stall && P->dm.ncta > 0) {
+                    // both schedules give the same bits: keep the faster
+                    int best = 1;
+                    CK(time_choice(P, st, m2l, &best));
+                    P->knob[0] = best;
+                }
+                CK(m2l(P->knob[0]));
+            }
             launches += 2;
         }
     }
@@ -948,7 +1002,17 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
     if (P->timing) CK(record_phase(P->ev[3], st));
     {
         int leaf_launches = 0;
-        CK(launch_eval(P->dt, P->dops, w, st, &leaf_launches));
+        auto leafpass = [&](int narrow_first) {
+            leaf_launches = 0;
+            return launch_eval(P->dt, P->dops, w, st, &leaf_launches, narrow_first != 0);
+        };
+        if (P->tuning && P->forced_knobs < 0) {
+            // both orders give the same bits: keep the faster
+            int best = 0;
+            CK(time_choice(P, st, leafpass, &best));
+            P->knob[1] = best;
+        }
+        CK(leafpass(P->knob[1]));
         launches += leaf_launches;
     }
     if (P->timing) CK(record_phase(P->ev[4], st));
@@ -1328,6 +1392,7 @@ fmm_status fmm_plan_set_option(fmm_plan_t plan, int key, double value) {
     if (key == FMM_OPT_AUTOTUNE) {
         plan->autotune = value != 0.0;
         plan->tuned_shapes.clear();
+        plan->tuned_knobs.clear();
         plan->drop_graph();
         return FMM_OK;
     }
@@ -1335,6 +1400,14 @@ fmm_status fmm_plan_set_option(fmm_plan_t plan, int key, double value) {
         const int sh = (int)value;
         if (sh < -1 || sh >= kGemmShapes) return fail(FMM_ERR_INVALID_ARG, "shape in [-1, 4]");
         plan->forced_shape = sh;
+        plan->drop_graph();
+        return FMM_OK;
+    }
+    if (key == FMM_OPT_FORCE_KNOBS) {
+        const int v = (int)value;
+        if ((double)v != value || v < -1 || v > 3)
+            return fail(FMM_ERR_INVALID_ARG, "value -1 or 0..3");
+        plan->forced_knobs = v;
         plan->drop_graph();
         return FMM_OK;
     }
@@ -1540,6 +1613,10 @@ fmm_status fmm_plan_get_array(fmm_plan_t P, int which, void *dst, int64_t bytes,
     case FMM_ARRAY_M2L_TILE_CTA_TILES:
         src = P->m2l.cta_tiles.data();
         size = P->m2l.cta_tiles.size() * 4;
+        break;
+    case FMM_ARRAY_TUNED_KNOBS:
+        src = P->knob;
+        size = sizeof(P->knob);
         break;
     default: return fail(FMM_ERR_INVALID_ARG, "unknown array");
     }

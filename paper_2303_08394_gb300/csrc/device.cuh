@@ -168,9 +168,10 @@ cudaError_t launch_p2l(const DevTree &t, const DevOps &o, const DevWork &w,
 cudaError_t launch_m2l_simt(const DevM2L &m, const DevOps &o, const DevWork &w,
                             cudaStream_t s);
 // Leaf pass (k_eval.cu): near field, L2P and M2P into the caller's rows;
-// *launches receives the kernels it enqueued.
+// *launches receives the kernels it enqueued.  narrow_first: launch the
+// width groups narrowest first instead of widest first (same results).
 cudaError_t launch_eval(const DevTree &t, const DevOps &o, const DevWork &w,
-                        cudaStream_t s, int *launches);
+                        cudaStream_t s, int *launches, bool narrow_first = false);
 
 // Tensor-core M2L (k_m2l_tc.cu).  qh_hi/qh_lo hold (nnodes*nrhs + 1) rows of
 // kpad operand elements (BF16, or TF32 in 32-bit words), the last row zero;

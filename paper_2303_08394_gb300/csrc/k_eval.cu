@@ -691,8 +691,10 @@ __global__ void __launch_bounds__(kThreads, (Occupancy<NR, T, kGrad>::minb))
     leaf<NR, T, kGrad>(t, o, w, r0, sm, b, rb, nt);
 }
 
-// one launch per non-empty width group, widest first (longest blocks
-// start first); group Tg runs with min(Tg, TMax) targets per lane
+// one launch per non-empty width group, widest first (longest blocks start
+// first) or narrowest first (the autotuner's choice; the groups write
+// disjoint rows, so the order changes no result); group Tg runs with
+// min(Tg, TMax) targets per lane
 template <int NR, bool kGrad, int T>
 void launch_width(const DevTree &t, const DevOps &o, const DevWork &w, int r0, int first,
                   int n, cudaStream_t s) {
@@ -701,8 +703,9 @@ void launch_width(const DevTree &t, const DevOps &o, const DevWork &w, int r0, i
 
 template <int NR, bool kGrad = false>
 cudaError_t launch_eval_nr(const DevTree &t, const DevOps &o, const DevWork &w, int r0,
-                           cudaStream_t s, int *launches) {
-    for (int Tg = kLeafWidths; Tg >= 1; --Tg) {
+                           cudaStream_t s, int *launches, bool narrow_first) {
+    for (int step = 0; step < kLeafWidths; ++step) {
+        const int Tg = narrow_first ? 1 + step : kLeafWidths - step;
         const int n = t.t_first[Tg - 1] - t.t_first[Tg], first = t.t_first[Tg];
         if (n <= 0) continue;
         const int T = Tg < TMax<NR, kGrad>::v ? Tg : TMax<NR, kGrad>::v;
@@ -730,23 +733,23 @@ cudaError_t launch_eval_nr(const DevTree &t, const DevOps &o, const DevWork &w, 
 } // namespace
 
 cudaError_t launch_eval(const DevTree &t, const DevOps &o, const DevWork &w, cudaStream_t s,
-                        int *launches) {
+                        int *launches, bool narrow_first) {
     *launches = 0;
     if (w.grad_user) {
         // potentials (if w.pot_user) and gradients, one column per launch
         cudaError_t e = cudaSuccess;
         for (int r0 = 0; r0 < w.nrhs && e == cudaSuccess; ++r0)
-            e = launch_eval_nr<1, true>(t, o, w, r0, s, launches);
+            e = launch_eval_nr<1, true>(t, o, w, r0, s, launches, narrow_first);
         return e;
     }
     int r0 = 0;
     cudaError_t e = cudaSuccess;
     while (r0 < w.nrhs && e == cudaSuccess) {
         int left = w.nrhs - r0;
-        if (left >= 8) { e = launch_eval_nr<8>(t, o, w, r0, s, launches); r0 += 8; }
-        else if (left >= 4) { e = launch_eval_nr<4>(t, o, w, r0, s, launches); r0 += 4; }
-        else if (left >= 2) { e = launch_eval_nr<2>(t, o, w, r0, s, launches); r0 += 2; }
-        else { e = launch_eval_nr<1>(t, o, w, r0, s, launches); r0 += 1; }
+        if (left >= 8) { e = launch_eval_nr<8>(t, o, w, r0, s, launches, narrow_first); r0 += 8; }
+        else if (left >= 4) { e = launch_eval_nr<4>(t, o, w, r0, s, launches, narrow_first); r0 += 4; }
+        else if (left >= 2) { e = launch_eval_nr<2>(t, o, w, r0, s, launches, narrow_first); r0 += 2; }
+        else { e = launch_eval_nr<1>(t, o, w, r0, s, launches, narrow_first); r0 += 1; }
     }
     return e;
 }

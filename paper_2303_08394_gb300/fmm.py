@@ -157,6 +157,11 @@ class FMMPlan:
         """Force one level-product tile shape (0, 1, 2) or -1 for automatic."""
         N.check(N.lib().fmm_plan_set_option(self._h, N.OPT_GEMM_SHAPE, float(shape)))
 
+    def set_knobs(self, knobs: int):
+        """-1: the autotuner's choice of the M2L block schedule and the leaf
+        launch order; 0..3 forces them (FMM_OPT_FORCE_KNOBS)."""
+        N.check(N.lib().fmm_plan_set_option(self._h, N.OPT_FORCE_KNOBS, float(knobs)))
+
     def set_m2l_kernel(self, kernel: int):
         """Tensor-core M2L kernel: 0 pair columns (operand width <= 128),
         1 target tiles (the default) (FMM_OPT_M2L_KERNEL)."""

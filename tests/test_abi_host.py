@@ -354,6 +354,10 @@ def test_null_and_negative_arguments():
     assert L.fmm_plan_set_option(P._h, 99, 1.0) == N.FMM_ERR_INVALID_ARG
     assert L.fmm_plan_set_option(P._h, N.OPT_M2L_MODE, 7.0) == N.FMM_ERR_INVALID_ARG
     assert L.fmm_plan_set_option(P._h, N.OPT_GEMM_SHAPE, 5.0) == N.FMM_ERR_INVALID_ARG
+    assert L.fmm_plan_set_option(P._h, N.OPT_FORCE_KNOBS, 4.0) == N.FMM_ERR_INVALID_ARG
+    assert L.fmm_plan_set_option(P._h, N.OPT_FORCE_KNOBS, 0.5) == N.FMM_ERR_INVALID_ARG
+    for v in (-1.0, 0.0, 3.0):
+        assert L.fmm_plan_set_option(P._h, N.OPT_FORCE_KNOBS, v) == 0
 
 
 def test_surface_and_direct_pair_counts():

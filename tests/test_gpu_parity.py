@@ -198,6 +198,31 @@ def test_autotuned_tile_shapes_are_bit_identical(mode):
     np.testing.assert_array_equal(gpu_eval(plan, q), tuned)
 
 
+@pytest.mark.parametrize("mode", [N.M2L_BF16X3, N.M2L_FP32], ids=["bf16x3", "fp32"])
+def test_tuned_m2l_schedule_and_leaf_order_are_bit_identical(mode):
+    """The autotuner's other two choices (the target-tile M2L's block
+    schedule, the leaf pass's launch order) change no summation order: the
+    tuned result equals every forced combination, and the choices are
+    exported."""
+    x, q = wl.sphere_surface(300_000, 57, nrhs=2)
+    plan = FMMPlan(x, 4, 16, m2l_mode=mode)
+    assert plan.info("m2l_tiles") >= 152  # the block schedule exists
+    tuned = gpu_eval(plan, q)
+    knobs = plan.array("tuned_knobs")
+    assert len(knobs) == 2 and set(knobs.tolist()) <= {0, 1}
+    for k in range(4):
+        plan.set_knobs(k)
+        np.testing.assert_array_equal(gpu_eval(plan, q), tuned)
+        assert plan.array("tuned_knobs").tolist() == [k & 1, k >> 1]
+    plan.set_knobs(-1)
+    np.testing.assert_array_equal(gpu_eval(plan, q), tuned)
+    # the gradient pass takes the same leaf launch order
+    q0 = np.ascontiguousarray(q[:, 0], dtype=np.float32)
+    g_tuned = plan.evaluate_gradient(q0)[1]
+    plan.set_knobs(2)
+    np.testing.assert_array_equal(plan.evaluate_gradient(q0)[1], g_tuned)
+
+
 @pytest.mark.slow
 def test_million_point_workload_sampled_against_direct_sum():
     """The 10^6-point uniform workload at p=6, ncrit=150 (the benchmark's
