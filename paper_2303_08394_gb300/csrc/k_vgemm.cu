@@ -153,6 +153,11 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
 
+    // Launched as a programmatic dependent of the previous kernel in the
+    // stream: everything above reads only kernel parameters and the plan's
+    // constant index tables, so it overlaps that kernel's tail; the vectors
+    // and add rows it produced are read only after this wait.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int c = 0; c < kStages - 1; ++c) issue(c);
     for (int c = 0; c < total_chunks; ++c) {
         issue(c + kStages - 1);
@@ -286,8 +291,19 @@ cudaError_t launch_shape(const VGemm &g, int nvec, bool split, cudaStream_t s) {
     constexpr int BV = 4 * (128 / (BM / RP));
     const dim3 grid((nvec + BV - 1) / BV, (g.m + BM - 1) / BM, split ? g.nseg : 1);
     if (grid.y > 65535u || grid.x > 2147483647u) return cudaErrorInvalidValue;
-    k_vgemm<BM, RP><<<grid, 128, 0, s>>>(g);
-    return cudaGetLastError();
+    // programmatic dependent launch: the blocks may start (and run their
+    // prologue) while the previous kernel of the stream finishes
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_vgemm<BM, RP>, g);
 }
 
 } // namespace
