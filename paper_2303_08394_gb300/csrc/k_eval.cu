@@ -683,12 +683,20 @@ struct Occupancy {
 template <int NR, int T, bool kGrad>
 __global__ void __launch_bounds__(kThreads, (Occupancy<NR, T, kGrad>::minb))
     k_eval(DevTree t, DevOps o, DevWork w, int r0, int first) {
+    // The width groups of one pass read only what the passes before them
+    // wrote and write disjoint rows, so the next group may start as soon as
+    // every block of this one has started (it fills this group's last
+    // wave).  Each block ends by waiting for its programmatic predecessor
+    // (the previous group; nothing for the first), so a group completes
+    // only after all groups before it, and the work after the pass sees
+    // every row.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __shared__ __align__(16) Smem<NR, Cfg<NR, T>::cap> sm;
     const int b = t.leaves[first + blockIdx.x];
     const int2 rb = t.range[b];
     const int nt = rb.y - rb.x;
-    if (nt <= 0) return;
-    leaf<NR, T, kGrad>(t, o, w, r0, sm, b, rb, nt);
+    if (nt > 0) leaf<NR, T, kGrad>(t, o, w, r0, sm, b, rb, nt);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // one launch per non-empty width group, widest first (longest blocks start
@@ -697,34 +705,51 @@ __global__ void __launch_bounds__(kThreads, (Occupancy<NR, T, kGrad>::minb))
 // min(Tg, TMax) targets per lane
 template <int NR, bool kGrad, int T>
 void launch_width(const DevTree &t, const DevOps &o, const DevWork &w, int r0, int first,
-                  int n, cudaStream_t s) {
-    k_eval<NR, T, kGrad><<<n, kThreads, 0, s>>>(t, o, w, r0, first);
+                  int n, cudaStream_t s, bool pdl) {
+    if (!pdl) {
+        k_eval<NR, T, kGrad><<<n, kThreads, 0, s>>>(t, o, w, r0, first);
+        return;
+    }
+    // a programmatic dependent of the previous width group (see k_eval)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n);
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_eval<NR, T, kGrad>, t, o, w, r0, first);
 }
 
 template <int NR, bool kGrad = false>
 cudaError_t launch_eval_nr(const DevTree &t, const DevOps &o, const DevWork &w, int r0,
                            cudaStream_t s, int *launches, bool narrow_first) {
+    int launched = 0;  // groups of this pass launched so far
     for (int step = 0; step < kLeafWidths; ++step) {
         const int Tg = narrow_first ? 1 + step : kLeafWidths - step;
         const int n = t.t_first[Tg - 1] - t.t_first[Tg], first = t.t_first[Tg];
         if (n <= 0) continue;
         const int T = Tg < TMax<NR, kGrad>::v ? Tg : TMax<NR, kGrad>::v;
+        const bool pdl = launched > 0;
         switch (T) {
-        case 1: launch_width<NR, kGrad, 1>(t, o, w, r0, first, n, s); break;
-        case 2: launch_width<NR, kGrad, 2>(t, o, w, r0, first, n, s); break;
-        case 3: launch_width<NR, kGrad, 3>(t, o, w, r0, first, n, s); break;
-        case 4: launch_width<NR, kGrad, 4>(t, o, w, r0, first, n, s); break;
+        case 1: launch_width<NR, kGrad, 1>(t, o, w, r0, first, n, s, pdl); break;
+        case 2: launch_width<NR, kGrad, 2>(t, o, w, r0, first, n, s, pdl); break;
+        case 3: launch_width<NR, kGrad, 3>(t, o, w, r0, first, n, s, pdl); break;
+        case 4: launch_width<NR, kGrad, 4>(t, o, w, r0, first, n, s, pdl); break;
         default:
             if constexpr (TMax<NR, kGrad>::v > 4) {
                 switch (T) {
-                case 5: launch_width<NR, kGrad, 5>(t, o, w, r0, first, n, s); break;
-                case 6: launch_width<NR, kGrad, 6>(t, o, w, r0, first, n, s); break;
-                case 7: launch_width<NR, kGrad, 7>(t, o, w, r0, first, n, s); break;
-                default: launch_width<NR, kGrad, 8>(t, o, w, r0, first, n, s); break;
+                case 5: launch_width<NR, kGrad, 5>(t, o, w, r0, first, n, s, pdl); break;
+                case 6: launch_width<NR, kGrad, 6>(t, o, w, r0, first, n, s, pdl); break;
+                case 7: launch_width<NR, kGrad, 7>(t, o, w, r0, first, n, s, pdl); break;
+                default: launch_width<NR, kGrad, 8>(t, o, w, r0, first, n, s, pdl); break;
                 }
             }
             break;
         }
+        ++launched;
         ++*launches;
     }
     return cudaGetLastError();
