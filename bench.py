@@ -41,7 +41,8 @@ DEFAULT_WORKLOAD = "sphere_n4e6_p7_ncrit128"
 # against the direct sum where p puts it and gives an operand width of 128
 # (k = 127 at p = 6, 122 at p = 7, 124 at p = 8)
 EPS_SVD = {"cube_n1e6_p6_ncrit150": 5e-7, "cube_n1e6_p6_ncrit150_nrhs64": 5e-7,
-           "sphere_n4e6_p7_ncrit128": 1e-6, "gauss8_n1.6e7_p8_ncrit128_nrhs8": 1e-6}
+           "sphere_n4e6_p7_ncrit128": 1e-6, "gauss8_n1.6e7_p8_ncrit128_nrhs8": 1e-6,
+           "batch256_cube_p6_ncrit150": 5e-7}
 # CPU oracle samples: points per worker process (one process per host core)
 CPU_SAMPLE_N = 20_000
 # --impl reference: the whole run (warm-up + timed steps) is held to about
@@ -70,6 +71,7 @@ def reference_sample_n(reps, rate=4e3):
 # reports null.
 TRAFFIC = {
     ("k_m2l_tc", "sphere_n4e6_p7_ncrit128", "bf16x3", 128): 139.3e6 + 34.0e6,
+    ("k_eval", "sphere_n4e6_p7_ncrit128", "bf16x3", None): 1415.6e6 + 62.3e6,
 }
 
 
@@ -143,7 +145,8 @@ sys.path.insert(0, {root!r})
 from oracle.kifmm import KIFMM
 from paper_2303_08394_gb300 import workloads as wl
 w = wl.WORKLOADS[{workload!r}]
-gen = {{"cube": wl.uniform_cube, "sphere": wl.sphere_surface, "gauss": wl.gaussian_mixture}}[w.kind]
+gen = {{"cube": wl.uniform_cube, "sphere": wl.sphere_surface, "gauss": wl.gaussian_mixture,
+        "batch": wl.uniform_cube}}[w.kind]
 x, q = gen({n}, {seed}, w.nrhs)
 f = KIFMM(x, w.p, w.ncrit)
 out = {{"n": {n}, "nrhs": w.nrhs, "depth": f.tree.depth, "warm": [], "timed": []}}
@@ -205,14 +208,29 @@ sys.path.insert(0, {root!r})
 from oracle import direct
 from paper_2303_08394_gb300 import workloads as wl
 w = wl.WORKLOADS[{workload!r}]
-x, q = w.generate(0)
-idx = wl.sample_targets(w.n, {m}, 0)
 direct.build()
-t0 = time.perf_counter()
-phi = direct.direct_sum(x, q, targets=x[idx])
-t = time.perf_counter() - t0
+if w.kind == "batch":
+    # each sampled target sums over its own problem (the bench's samples)
+    sets = w.problem_sets(0)
+    parts, t, pairs = [], 0.0, 0
+    for i, (xi, qi) in enumerate(sets):
+        loc = wl.sample_targets(len(xi), min({m}, len(xi)), i)
+        t0 = time.perf_counter()
+        parts.append(direct.direct_sum(xi, qi, targets=xi[loc]))
+        t += time.perf_counter() - t0
+        pairs += len(loc) * len(xi)
+    phi = np.concatenate(parts)
+    idx = np.arange(len(phi))
+else:
+    x, q = w.generate(0)
+    idx = wl.sample_targets(w.n, {m}, 0)
+    t0 = time.perf_counter()
+    phi = direct.direct_sum(x, q, targets=x[idx])
+    t = time.perf_counter() - t0
+    pairs = len(idx) * w.n
 np.save({out!r}, phi)
-print(json.dumps({{"seconds": t, "threads": direct.num_threads(), "targets": len(idx)}}))
+print(json.dumps({{"seconds": t, "threads": direct.num_threads(), "targets": len(idx),
+                  "pairs": pairs}}))
 """
 
 
@@ -242,8 +260,9 @@ def cpu_baseline(workload, w, ref_sampled=None):
         if r.returncode == 0:
             d = json.loads(r.stdout.strip().splitlines()[-1])
             phi = np.load(out)
+            # a batch's targets each see their own problem's sources only
             d["sources"] = w.n
-            d["pairs_per_s"] = w.n * d["targets"] / d["seconds"]
+            d["pairs_per_s"] = d["pairs"] / d["seconds"]
             d["targets_per_s"] = d["targets"] / d["seconds"]
             d["what"] = ("oracle/direct.c, FP64 O(N) sum per sampled target over all N sources, "
                          "OpenMP over targets")
@@ -329,6 +348,33 @@ def _direct_sampled(x, q, idx, dev, gradient=False, chunk=1 << 15):
             out += inv @ qs[s:s + chunk]
         del d, r, inv
     return (out / (4 * np.pi)).cpu().numpy()
+
+
+def _batch_samples(sets, per):
+    """`per` sampled targets of every problem of a batch, as indices into the
+    concatenated points."""
+    import numpy as np
+    from paper_2303_08394_gb300 import workloads as wl
+    out, base = [], 0
+    for i, (xi, _) in enumerate(sets):
+        out.append(base + wl.sample_targets(len(xi), min(per, len(xi)), i))
+        base += len(xi)
+    return np.concatenate(out)
+
+
+def _reference(x, q, idx, dev, sets=None, gradient=False):
+    """FP64 direct sum at the points idx; for a batch, each point's sum runs
+    over its own problem's sources only."""
+    import numpy as np
+    if sets is None:
+        return _direct_sampled(x, q, idx, dev, gradient=gradient)
+    parts, base = [], 0
+    for xi, qi in sets:
+        sel = idx[(idx >= base) & (idx < base + len(xi))] - base
+        if len(sel):
+            parts.append(_direct_sampled(xi, qi, sel, dev, gradient=gradient))
+        base += len(xi)
+    return np.concatenate(parts)
 
 
 def rel_l2(a, b):
@@ -473,13 +519,19 @@ def main():
     if not os.path.exists(N.LIB_PATH):
         build.build()
     modes = {"fp32": N.M2L_FP32, "bf16x3": N.M2L_BF16X3, "tf32x3": N.M2L_TF32X3}
+    sets = w.problem_sets(rank) if w.kind == "batch" else None
     x, q = w.generate(rank)
+    n = len(x)  # a batch's total depends on the seed
     t0 = time.perf_counter()
-    plan = FMMPlan(x, w.p, w.ncrit, m2l_mode=modes[a.m2l], eps_svd=a.eps_svd)
+    if sets is not None:
+        plan = FMMPlan.batch([xi for xi, _ in sets], w.p, w.ncrit, m2l_mode=modes[a.m2l],
+                             eps_svd=a.eps_svd)
+    else:
+        plan = FMMPlan(x, w.p, w.ncrit, m2l_mode=modes[a.m2l], eps_svd=a.eps_svd)
     plan.set_m2l_kernel(0 if a.m2l_kernel == "pairs" else 1)
     plan_s = time.perf_counter() - t0
     qd = torch.as_tensor(q.astype(np.float32), device=dev)
-    out = torch.empty((w.n, w.nrhs), dtype=torch.float64, device=dev)
+    out = torch.empty((n, w.nrhs), dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
 
@@ -492,14 +544,16 @@ def main():
     clk = clocks.stop()
     total_ms = max_over_ranks(sum(step_ms), world, dev)
     ms_per_step = total_ms / a.steps
-    value = job_value(w.n * w.nrhs, a.steps, world, total_ms / 1e3)
+    value = job_value(n * w.nrhs, a.steps, world, total_ms / 1e3)
 
-    # accuracy gate on sampled targets (FP64 direct sum)
+    # accuracy gate on sampled targets (FP64 direct sum; for a batch, over
+    # each target's own problem)
     err = idx = ref = None
     if not a.no_error_check and rank == 0:
-        idx = wl.sample_targets(w.n, w.error_samples or 1000, 0)
+        idx = (_batch_samples(sets, w.error_samples) if sets is not None
+               else wl.sample_targets(n, w.error_samples or 1000, 0))
         got = out.cpu().numpy()[idx]
-        ref = _direct_sampled(x, q, idx, dev)
+        ref = _reference(x, q, idx, dev, sets)
         err = rel_l2(got, ref)
 
     # the other M2L modes on the same plan, same protocol: the plain FP32
@@ -512,7 +566,7 @@ def main():
             plan.set_m2l_mode(modes[name])
             l_ms, l_ph, _ = time_mode(plan, qd, out, flush, stream, a.steps, a.warmup, world)
             l_tot = max_over_ranks(sum(l_ms), world, dev)
-            leg = {"value": job_value(w.n * w.nrhs, a.steps, world, l_tot / 1e3),
+            leg = {"value": job_value(n * w.nrhs, a.steps, world, l_tot / 1e3),
                    "ms_per_step": l_tot / a.steps, "phase_ms": mean_phases(l_ph)}
             if ref is not None:
                 leg["rel_l2_err"] = rel_l2(out.cpu().numpy()[idx], ref)
@@ -524,19 +578,19 @@ def main():
     # gradients only
     gradient = None
     if not a.quick and w.nrhs == 1:
-        gout = torch.empty((w.n, 1, 3), dtype=torch.float64, device=dev)
+        gout = torch.empty((n, 1, 3), dtype=torch.float64, device=dev)
         g_steps = min(a.steps, 50)
         g_ms, g_ph, g_launch = time_mode(
             plan, qd, out, flush, stream, g_steps, a.warmup, world,
             call=lambda: plan.evaluate_gradient(qd, grad_out=gout, potentials=False,
                                                 stream=stream))
         g_tot = max_over_ranks(sum(g_ms), world, dev)
-        gradient = {"value": job_value(w.n, g_steps, world, g_tot / 1e3), "unit": UNIT,
+        gradient = {"value": job_value(n, g_steps, world, g_tot / 1e3), "unit": UNIT,
                     "ms_per_step": g_tot / g_steps, "steps": g_steps,
                     "phase_ms": mean_phases(g_ph), "gpu_launches": g_launch * g_steps}
         if idx is not None:
             got = gout.cpu().numpy()[idx, 0, :]
-            gref = _direct_sampled(x, q, idx, dev, gradient=True)
+            gref = _reference(x, q, idx, dev, sets, gradient=True)
             gradient["rel_l2_err"] = rel_l2(got, gref)
 
     # rooflines from the library's per-phase CUDA events (each phase is
@@ -620,8 +674,9 @@ def run_e2e(plan, q, w, a, world, dev):
     import numpy as np
     import torch
     import torch.distributed as dist
+    n = len(q)
     qh = torch.tensor(q.astype(np.float32)).pin_memory()
-    oh = torch.empty((w.n, w.nrhs), dtype=torch.float64).pin_memory()
+    oh = torch.empty((n, w.nrhs), dtype=torch.float64).pin_memory()
     stream = torch.cuda.Stream(device=dev)
     # host buffers: the library copies charges in, replays its graph and
     # copies potentials out on `stream`, and returns when they have landed
@@ -633,8 +688,8 @@ def run_e2e(plan, q, w, a, world, dev):
     for _ in range(steps):
         plan.evaluate(qh, out=oh, stream=stream)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
-    return {"value": job_value(w.n * w.nrhs, steps, world, e2e_s), "unit": UNIT,
-            "h2d_bytes_per_step": w.n * w.nrhs * 4, "d2h_bytes_per_step": w.n * w.nrhs * 8,
+    return {"value": job_value(n * w.nrhs, steps, world, e2e_s), "unit": UNIT,
+            "h2d_bytes_per_step": n * w.nrhs * 4, "d2h_bytes_per_step": n * w.nrhs * 8,
             "steps": steps}
 
 

@@ -72,16 +72,28 @@ def sample_targets(n: int, m: int, seed: int):
 
 @dataclasses.dataclass(frozen=True)
 class Workload:
-    """One named workload: point distribution, size and FMM parameters."""
+    """One named workload: point distribution, size and FMM parameters.
+    kind "batch": `problems` independent uniform cubes of log-uniform sizes
+    (batch_problems), evaluated as one plan; n is their total at seed 0 and
+    error_samples the sampled targets per problem."""
     name: str
-    kind: str            # "cube" | "sphere" | "gauss"
+    kind: str            # "cube" | "sphere" | "gauss" | "batch"
     n: int
     p: int
     ncrit: int
     nrhs: int = 1
     error_samples: int = 0   # 0: all targets
+    problems: int = 0
+
+    def problem_sets(self, seed: int = 0):
+        """kind "batch": the list of (x_i, q_i)."""
+        return batch_problems(self.problems, seed, self.nrhs)
 
     def generate(self, seed: int = 0):
+        if self.kind == "batch":
+            sets = self.problem_sets(seed)
+            return (np.concatenate([x for x, _ in sets]),
+                    np.concatenate([q for _, q in sets]))
         gen = {"cube": uniform_cube, "sphere": sphere_surface,
                "gauss": gaussian_mixture}[self.kind]
         return gen(self.n, seed, self.nrhs)
@@ -98,6 +110,10 @@ CUBE_1M_P6_NRHS64 = Workload("cube_n1e6_p6_ncrit150_nrhs64", "cube", 1_000_000,
 GAUSS_16M_P8 = Workload("gauss8_n1.6e7_p8_ncrit128_nrhs8", "gauss", 16_000_000,
                         8, 128, nrhs=8, error_samples=2000)
 
+BATCH_256_P6 = Workload("batch256_cube_p6_ncrit150", "batch",
+                        int(log_uniform_sizes(256, 0).sum()), 6, 150,
+                        error_samples=8, problems=256)
+
 WORKLOADS = {w.name: w for w in
              (CUBE_10K_P4, CUBE_1M_P6, SPHERE_4M_P7, CUBE_1M_P6_NRHS64,
-              GAUSS_16M_P8)}
+              GAUSS_16M_P8, BATCH_256_P6)}

@@ -89,7 +89,18 @@ def test_sample_targets():
     ("sphere_n4e6_p7_ncrit128", "sphere", 4_000_000, 7, 128, 1),
     ("cube_n1e6_p6_ncrit150_nrhs64", "cube", 1_000_000, 6, 150, 64),
     ("gauss8_n1.6e7_p8_ncrit128_nrhs8", "gauss", 16_000_000, 8, 128, 8),
+    ("batch256_cube_p6_ncrit150", "batch", 6_523_380, 6, 150, 1),
 ])
 def test_named_workloads(name, kind, n, p, ncrit, nrhs):
     w = wl.WORKLOADS[name]
     assert (w.name, w.kind, w.n, w.p, w.ncrit, w.nrhs) == (name, kind, n, p, ncrit, nrhs)
+
+
+def test_batch_workload_is_the_concatenated_problems():
+    w = wl.WORKLOADS["batch256_cube_p6_ncrit150"]
+    sets = w.problem_sets(0)
+    assert len(sets) == 256 and w.problems == 256
+    x, q = w.generate(0)
+    assert len(x) == w.n == sum(len(a) for a, _ in sets)
+    np.testing.assert_array_equal(x[:len(sets[0][0])], sets[0][0])
+    np.testing.assert_array_equal(q[-len(sets[-1][1]):], sets[-1][1])
