@@ -264,8 +264,8 @@ def cpu_baseline(workload, w, ref_sampled=None):
             d["sources"] = w.n
             d["pairs_per_s"] = d["pairs"] / d["seconds"]
             d["targets_per_s"] = d["targets"] / d["seconds"]
-            d["what"] = ("oracle/direct.c, FP64 O(N) sum per sampled target over all N sources, "
-                         "OpenMP over targets")
+            d["what"] = ("oracle/direct.c, FP64 O(N) sum per sampled target over all N sources "
+                         "(a batch: over its own problem's), OpenMP over targets")
             if ref_sampled is not None:
                 d["max_rel_diff_vs_bench_reference"] = float(
                     np.max(np.abs(phi - ref_sampled)) / np.max(np.abs(ref_sampled)))
