@@ -81,6 +81,27 @@ def test_fmm_matches_oracle(name, gen, n, p, ncrit):
     assert plan.info("u_pairs") == sum(len(v) for v in ora.U.values())
 
 
+@pytest.mark.parametrize("mode", [N.M2L_FP32, N.M2L_BF16X3], ids=["fp32", "bf16x3"])
+def test_w_and_x_through_surfaces_match_oracle(mode):
+    """direct_wx = 0: every W box through M2P and every X list through P2L
+    (the paper's form), against the oracle run the same way, on clustered
+    points where both lists are used; and the two forms against each other
+    within the method's error."""
+    x, q = wl.gaussian_mixture(8000, 46, nrhs=2)
+    plan0 = FMMPlan(x, 5, 16, direct_wx=0, m2l_mode=mode)
+    plan1 = FMMPlan(x, 5, 16, m2l_mode=mode)
+    assert plan0.info("wx_direct_pairs") == 0 and plan1.info("wx_direct_pairs") > 0
+    assert plan0.info("surf_pairs") > plan1.info("surf_pairs")
+    phi0, phi1 = gpu_eval(plan0, q), gpu_eval(plan1, q)
+    ora = KIFMM(x, 5, 16, direct_wx=False).evaluate(q)
+    bar = 1e-6 if mode == N.M2L_FP32 else 1e-5
+    for r in range(2):
+        check(phi0[:, r], ora[:, r], bar, what=f"surface W/X column {r} vs oracle")
+    ref = direct_sum(x, q[:, 0])
+    e0, e1 = rel(phi0[:, 0], ref), rel(phi1[:, 0], ref)
+    assert e1 <= 1.2 * e0 + FP32_FLOOR, (e1, e0)
+
+
 @pytest.mark.parametrize("nrhs", [3, 8, 21])
 def test_nrhs_columns_equal_single_vector(nrhs):
     x, q = wl.gaussian_mixture(5000, 42, nrhs=nrhs)
