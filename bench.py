@@ -37,6 +37,8 @@ UNIT = "points/s"
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
 DEFAULT_WORKLOAD = "sphere_n4e6_p7_ncrit128"
+# the batched-problems workload reported beside every full run
+BATCH_WORKLOAD = "batch256_cube_p6_ncrit150"
 # M2L compression tolerance per workload: the largest that keeps the error
 # against the direct sum where p puts it and gives an operand width of 128
 # (k = 127 at p = 6, 122 at p = 7, 124 at p = 8)
@@ -417,6 +419,42 @@ def time_mode(plan, qd, out, flush, stream, steps, warmup, world, call=None):
     return [a.elapsed_time(b) for a, b in zip(starts, ends)], phases, launches
 
 
+def run_batch_leg(a, world, rank, dev, flush, stream):
+    """The 256-problem batch (one forest plan: every problem's boxes in the
+    same level products, M2L tiles and leaf launches, one graph per
+    evaluation) timed with the main line's protocol, its error over each
+    sampled target's own problem."""
+    import numpy as np
+    import torch
+    from paper_2303_08394_gb300 import FMMPlan, _native as N
+    from paper_2303_08394_gb300 import workloads as wl
+    w = wl.WORKLOADS[BATCH_WORKLOAD]
+    modes = {"fp32": N.M2L_FP32, "bf16x3": N.M2L_BF16X3, "tf32x3": N.M2L_TF32X3}
+    sets = w.problem_sets(rank)
+    x, q = w.generate(rank)
+    n = len(x)
+    t0 = time.perf_counter()
+    plan = FMMPlan.batch([xi for xi, _ in sets], w.p, w.ncrit, m2l_mode=modes[a.m2l],
+                         eps_svd=EPS_SVD[BATCH_WORKLOAD])
+    plan_s = time.perf_counter() - t0
+    qd = torch.as_tensor(q.astype(np.float32), device=dev)
+    out = torch.empty((n, w.nrhs), dtype=torch.float64, device=dev)
+    steps = min(a.steps, 30)
+    ms, ph, launches = time_mode(plan, qd, out, flush, stream, steps, a.warmup, world)
+    tot = max_over_ranks(sum(ms), world, dev)
+    leg = {"workload": w.name, "problems": len(sets), "n": n, "p": w.p, "ncrit": w.ncrit,
+           "m2l": a.m2l, "value": job_value(n * w.nrhs, steps, world, tot / 1e3),
+           "unit": UNIT, "ms_per_step": tot / steps, "steps": steps,
+           "phase_ms": mean_phases(ph), "gpu_launches_per_step": launches,
+           "plan_s": plan_s}
+    if not a.no_error_check and rank == 0:
+        idx = _batch_samples(sets, w.error_samples)
+        leg["rel_l2_err"] = rel_l2(out.cpu().numpy()[idx], _reference(x, q, idx, dev, sets))
+        leg["error_samples"] = len(idx)
+    del plan
+    return leg
+
+
 def mean_phases(phases):
     return {k: statistics.mean(ph[k] for ph in phases) for k in phases[0]}
 
@@ -640,6 +678,11 @@ def main():
                                 "note": "19 flops per evaluated pair (near field, direct "
                                         "W/X leaves, L2P, M2P)"}
 
+    # the batch of 256 independent problems, same protocol
+    batch = None
+    if not a.quick and w.kind != "batch":
+        batch = run_batch_leg(a, world, rank, dev, flush, stream)
+
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not a.quick:
@@ -654,6 +697,7 @@ def main():
                 "data": "synthetic", "config": config,
                 "rel_l2_err": err, "error_gate_1e-5": (err is not None and err <= 1e-5),
                 "legs": legs, "fp32": legs.get("fp32"), "gradient": gradient,
+                "batch": batch,
                 "roofline": dominant, "rooflines": {"m2l": m2l_roof, "leaf": leaf_roof},
                 "phase_ms": ph, "e2e": e2e,
                 "gpu_launches": launches_per_step * a.steps, "clocks": clk,

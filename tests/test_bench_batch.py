@@ -35,3 +35,12 @@ def test_batch_samples_and_reference_stay_within_each_problem():
     # and not against the whole concatenation
     whole = direct_sum(x, q, targets=x[idx]).reshape(ref.shape)
     assert np.max(np.abs(whole - want)) > 1e-3 * np.max(np.abs(want))
+
+
+def test_batch_leg_names_a_batch_workload_with_its_tolerance():
+    import bench
+    from paper_2303_08394_gb300 import workloads as wl
+    w = wl.WORKLOADS[bench.BATCH_WORKLOAD]
+    assert w.kind == "batch" and w.problems == 256
+    assert bench.BATCH_WORKLOAD in bench.EPS_SVD
+    assert callable(bench.run_batch_leg)
