@@ -92,6 +92,14 @@ __device__ __forceinline__ int block_item(const TcArgs &a, int k) {
     return (int)blockIdx.x + k * (int)gridDim.x;
 }
 
+// A read-only 32-bit load issued where it stands in the program (volatile
+// asm keeps the compiler from sinking it towards its first use).
+__device__ __forceinline__ int ld_nc_s32(const int *p) {
+    int v;
+    asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
 template <bool kTF32>
 __global__ void __launch_bounds__(kThreads, 1)
     k_m2l_tc(const __grid_constant__ CUtensorMap s_hi, const __grid_constant__ CUtensorMap s_lo,
@@ -165,22 +173,37 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int piece = lane & 7, sub = lane >> 3;
         uint32_t j = 0;
         bool ok = true;
+        const int row16 = kp * F::esize / 16;
         for (int k = 0, nk = block_items(a); k < nk && ok; ++k) {
             const int item = block_item(a, k);
             const int tile = item / a.row_chunks, rc = item - tile * a.row_chunks;
             const int e0 = a.m.tile_entry_ptr[tile], e1 = a.m.tile_entry_ptr[tile + 1];
+            // tile slot of each of this thread's eight rows (row g of the
+            // item is slot g / nrhs, right-hand side g mod nrhs)
+            int slot[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) slot[i] = (rc * 128 + (wi * 8 + i) * 4 + sub) / a.nrhs;
+            // source boxes of the rows for the current entry; the next
+            // entry's are loaded one entry ahead (in program order, so their
+            // latency overlaps this entry's copies)
+            int src[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                src[i] = e0 < e1 ? ld_nc_s32(a.m.entry_src + (size_t)e0 * kTileRows + slot[i]) : -1;
             for (int e = e0; e < e1 && ok; ++e) {
+                int nsrc[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    nsrc[i] = e + 1 < e1
+                                  ? ld_nc_s32(a.m.entry_src + (size_t)(e + 1) * kTileRows + slot[i])
+                                  : -1;
                 // source row of each of this thread's eight tile rows, as an
                 // offset in 16-byte pieces
-                const int row16 = kp * F::esize / 16;
                 uint32_t qoff[8];   // < 2^32: checked by the launcher
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    const int r = (wi * 8 + i) * 4 + sub;
-                    const int g = rc * 128 + r;
-                    const int slot = g / a.nrhs, rhs = g - slot * a.nrhs;
-                    const int src = a.m.entry_src[(size_t)e * kTileRows + slot];
-                    const int qrow = src >= 0 ? src * a.nrhs + rhs : a.zero_row;
+                    const int rhs = rc * 128 + (wi * 8 + i) * 4 + sub - slot[i] * a.nrhs;
+                    const int qrow = src[i] >= 0 ? src[i] * a.nrhs + rhs : a.zero_row;
                     qoff[i] = (uint32_t)qrow * (uint32_t)row16 + (uint32_t)piece;
                 }
                 for (int c = 0; c < a.nch && ok; ++c, ++j) {
@@ -213,6 +236,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc::fence_proxy_async_smem();
                     tc::mbar_arrive(&full[s]);
                 }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) src[i] = nsrc[i];
             }
         }
     } else if (warp >= 4 && warp < 8) {
