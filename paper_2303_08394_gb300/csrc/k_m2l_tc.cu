@@ -5,6 +5,12 @@
 // source at offset t from target r (zero row if none).  Operands are split
 // x = x_hi + x_lo in BF16 (kind::f16) or TF32 (kind::tf32) and every K step
 // issues x_hi*S_hi + x_hi*S_lo + x_lo*S_hi with FP32 accumulation in TMEM.
+// For kpad <= 128 ("wide" products) the first two are one MMA of N = 2 kpad,
+// x_hi * [S_hi; S_lo], whose second half accumulates the tile's x_hi*S_lo
+// correction over all of its offsets in TMEM columns of its own: two MMAs per
+// K step instead of three, the same products.  The correction is 2^-8 (BF16)
+// or 2^-11 (TF32) of the total, so its long accumulation adds nothing
+// measurable to the error.
 //
 // Warp roles (448 threads):
 //   0-3, 10-13  two sets that gather the 128 rows of X_t for one
@@ -14,10 +20,14 @@
 //        chunk's loads before waiting for its stage, so loads overlap the
 //        MMAs;
 //   4-7  epilogue: every group of offsets, add the TMEM accumulator into a
-//        TMEM running total; after the tile's last offset write the total
-//        (FP32) to chat.  The two-level sum keeps the FP32 rounding of the
-//        ~189 k products per target at the level the FP32 path reaches;
-//   8    TMA loads of the S_t chunks (hi and lo) for the same K chunk;
+//        TMEM running total; after the tile's last offset add the wide
+//        products' correction columns, zero them for the next tile (and
+//        say so on an mbarrier the MMA thread waits on before the next
+//        tile) and write the total (FP32) to chat.  The two-level sum keeps
+//        the FP32 rounding of the ~189 k products per target at the level
+//        the FP32 path reaches;
+//   8    TMA loads of the S_t chunks (hi and lo) for the same K chunk, in
+//        the order the wide product of the chunk's accumulator reads them;
 //   9    allocates TMEM, issues the MMAs (one thread), frees TMEM.
 // Roles in the error word: 0 gatherers, 1 epilogue, 2 TMA, 3 and 4 MMA
 // thread (accumulator, stage), 5 the test hook's stall.
@@ -48,9 +58,12 @@ constexpr int kThreads = 32 * (10 + 4 * (kSets - 1));
 // (all ~189 offsets of a tile in one accumulator: 2.4e-5 relative error
 // with BF16x3), so sums are kept short.  BF16x3 uses 4 (its error, 5.5e-6
 // against the direct sum, is set by the BF16 split itself); TF32x3 uses 1,
-// which its 1e-6 bar needs (4 gave 1.5e-6 against the oracle).
+// which its 1e-6 bar needs (4 gave 1.5e-6 against the oracle).  This holds
+// for the main terms; the small x_hi*S_lo correction of wide products is
+// drained once per tile.
 inline int group_for(bool tf32) { return tf32 ? 1 : 4; }
 constexpr uint64_t kWaitLimit = 2000000000ull;  // 2 s per wait
+constexpr uint32_t kNoRow = 0xFFFFFFFFu;  // gather offset of a row with no source
 // Test hook: with TcArgs::test_stall set, block 0's MMA thread first waits
 // on `done`, which nothing completes before the thread's own final commit,
 // with this shorter limit, so that its expiry (role 5) comes first and the
@@ -60,6 +73,7 @@ constexpr uint64_t kTestStallLimit = 100000000ull;  // 0.1 s
 struct TcArgs {
     DevM2L m;
     int nrhs, kpad, nch, stages, row_chunks, nitems, nbuf, group;
+    int wide;  // hi x [S_hi; S_lo] as one N = 2 kpad product (see the MMA issuer)
     uint32_t tmem_cols;
     const uint4 *qh_hi, *qh_lo;   // rows of kpad elements (16-byte pieces)
     int zero_row;                 // index of an all-zero qhat row
@@ -118,7 +132,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     // S_t chunk's bytes, so the MMA thread waits once per stage
     uint64_t *full = bars, *empty = bars + 2 * S;
     uint64_t *acc_full = bars + 3 * S, *acc_empty = acc_full + 2, *done = acc_full + 4;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    // corr_empty: the epilogue has added a tile's correction columns into
+    // its total and zeroed them (wide products only)
+    uint64_t *corr_empty = done + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(corr_empty + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     volatile int *never = abort_flag + 1;  // stays 0: drains ignore the abort flag
 
@@ -133,6 +150,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc::mbar_init(&acc_empty[b], 128);
         }
         tc::mbar_init(done, 1);
+        tc::mbar_init(corr_empty, 128);
         *abort_flag = 0;
         *never = 0;
         tc::fence_mbar_init();
@@ -148,9 +166,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = *tmem_slot;
     // TMEM columns: nbuf accumulators of kp columns, then the running total.
     // With two accumulators the epilogue drains one while the MMAs fill the
-    // other.
+    // other.  Wide products: main accumulator 0 at 0, the correction
+    // columns at kp, main accumulator 1 at 2 kp, the total at 3 kp, so that
+    // either main accumulator and the correction are kp-column neighbours
+    // (0 and 1: [main0 | corr], [corr | main1]).
     const int nbuf = a.nbuf;
-    const uint32_t tot_col = (uint32_t)(nbuf * kp);
+    const uint32_t tot_col = a.wide ? (uint32_t)(3 * kp) : (uint32_t)(nbuf * kp);
+    auto main_col = [&](int buf) {
+        return a.wide ? (uint32_t)(buf ? 2 * kp : 0) : (uint32_t)(buf * kp);
+    };
+    const uint32_t corr_col = (uint32_t)kp;
 
     auto a_tile = [&](int s, int split) { return smem + (size_t)s * stage_bytes + split * a_bytes; };
     auto b_tile = [&](int s, int split) {
@@ -198,13 +223,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                                   ? ld_nc_s32(a.m.entry_src + (size_t)(e + 1) * kTileRows + slot[i])
                                   : -1;
                 // source row of each of this thread's eight tile rows, as an
-                // offset in 16-byte pieces
-                uint32_t qoff[8];   // < 2^32: checked by the launcher
+                // offset in 16-byte pieces; kNoRow where the target has no
+                // source at this offset (the row is zero and is not loaded:
+                // on adaptive trees most tile rows of an entry are such rows)
+                uint32_t qoff[8];   // < 2^32 - 1: checked by the launcher
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int rhs = rc * 128 + (wi * 8 + i) * 4 + sub - slot[i] * a.nrhs;
-                    const int qrow = src[i] >= 0 ? src[i] * a.nrhs + rhs : a.zero_row;
-                    qoff[i] = (uint32_t)qrow * (uint32_t)row16 + (uint32_t)piece;
+                    qoff[i] = src[i] >= 0 ? (uint32_t)(src[i] * a.nrhs + rhs) * (uint32_t)row16 +
+                                                (uint32_t)piece
+                                          : kNoRow;
                 }
                 for (int c = 0; c < a.nch && ok; ++c, ++j) {
                     if ((int)(j % kSets) != set) continue;
@@ -213,11 +241,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const bool mine = piece * 16 < valid * F::esize; // this lane's piece exists
                     uint4 vh[8], vl[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        if (mine) {
+                    for (int i = 0; i < 8; ++i) {
+                        vh[i] = vl[i] = make_uint4(0u, 0u, 0u, 0u);
+                        if (mine && qoff[i] != kNoRow) {
                             vh[i] = __ldg(a.qh_hi + qoff[i] + c * 8);
                             vl[i] = __ldg(a.qh_lo + qoff[i] + c * 8);
                         }
+                    }
                     ok = tc::mbar_wait(&empty[s], ((j / S) & 1) ^ 1, abort_flag, kWaitLimit);
                     if (!ok) {
                         if (!*abort_flag) fail(0);
@@ -247,6 +277,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
         uint32_t gi = 0;
         bool ok = true;
+        const float zero16[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f,
+                                  0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (a.wide) {
+            // the correction columns start at zero
+            for (int cc = 0; cc < kp; cc += 16) tc::tmem_st16(lane_addr + corr_col + cc, zero16);
+            tc::tmem_wait_st();
+            tc::tc_fence_before();
+            tc::mbar_arrive(corr_empty);
+        }
         for (int k = 0, nk = block_items(a); k < nk && ok; ++k) {
             const int item = block_item(a, k);
             const int tile = item / a.row_chunks, rc = item - tile * a.row_chunks;
@@ -257,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int ngroups = (ne + a.group - 1) / a.group;
             for (int grp = 0; grp < ngroups; ++grp, ++gi) {
                 const int buf = gi % nbuf;
-                const uint32_t acc_col = (uint32_t)(buf * kp);
+                const uint32_t acc_col = main_col(buf);
                 ok = tc::mbar_wait(&acc_full[buf], (gi / nbuf) & 1, abort_flag, kWaitLimit);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) {
@@ -267,9 +306,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc::tc_fence_after();
                 const bool first = grp == 0, last = grp == ngroups - 1;
                 for (int cc = 0; cc < kp; cc += 16) {
-                    float v[16], t[16];
+                    float v[16], t[16], u[16];
                     tc::tmem_ld16(lane_addr + acc_col + cc, v);
                     if (!first) tc::tmem_ld16(lane_addr + tot_col + cc, t);
+                    if (last && a.wide) tc::tmem_ld16(lane_addr + corr_col + cc, u);
                     tc::tmem_wait_ld();
                     if (first) {
 #pragma unroll
@@ -277,6 +317,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     } else {
 #pragma unroll
                         for (int i = 0; i < 16; ++i) t[i] += v[i];
+                    }
+                    if (last && a.wide) {
+                        // the tile's hi x lo correction, then zero it for the next tile
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) t[i] += u[i];
+                        tc::tmem_st16(lane_addr + corr_col + cc, zero16);
                     }
                     if (last) {
                         if (slot < kTileRows && tgt >= 0) {
@@ -294,19 +340,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc::tmem_wait_st();
                 tc::tc_fence_before();
                 tc::mbar_arrive(&acc_empty[buf]);
+                if (last && a.wide) tc::mbar_arrive(corr_empty);
             }
         }
     } else if (warp == 8) {
         // ------------------------------------------------ TMA for S_t chunks
         if (lane == 0) {
-            uint32_t j = 0;
+            uint32_t j = 0, gbase = 0;
             bool ok = true;
             for (int k = 0, nk = block_items(a); k < nk && ok; ++k) {
                 const int item = block_item(a, k);
                 const int tile = item / a.row_chunks;
                 const int e0 = a.m.tile_entry_ptr[tile], e1 = a.m.tile_entry_ptr[tile + 1];
+                const uint32_t gfirst = gbase;
+                gbase += (uint32_t)((e1 - e0 + a.group - 1) / a.group);
                 for (int e = e0; e < e1 && ok; ++e) {
                     const int row0 = a.m.entry_offset[e] * kp;
+                    // wide products: S_hi first for accumulator 0, S_lo first
+                    // for accumulator 1 (see the MMA issuer)
+                    const int p = a.wide ? (int)((gfirst + (uint32_t)((e - e0) / a.group)) & 1u) : 0;
                     for (int c = 0; c < a.nch; ++c, ++j) {
                         const int s = j % S;
                         ok = tc::mbar_wait(&empty[s], ((j / S) & 1) ^ 1, abort_flag, kWaitLimit);
@@ -315,8 +367,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                             break;
                         }
                         tc::mbar_arrive_expect_tx(&full[s], 2 * b_bytes);
-                        tc::tma_load_2d(b_tile(s, 0), &s_hi, &full[s], c * F::kc, row0);
-                        tc::tma_load_2d(b_tile(s, 1), &s_lo, &full[s], c * F::kc, row0);
+                        tc::tma_load_2d(b_tile(s, p), &s_hi, &full[s], c * F::kc, row0);
+                        tc::tma_load_2d(b_tile(s, 1 - p), &s_lo, &full[s], c * F::kc, row0);
                     }
                 }
             }
@@ -332,12 +384,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t id = tc::idesc(F::ab, 128, (uint32_t)kp);
+            const uint32_t id2 = tc::idesc(F::ab, 128, 2u * (uint32_t)kp);
             // The MMA thread is the critical path: tcgen05.mma issue proceeds
             // at the tensor pipe's pace, so everything else it does per stage
             // adds to the kernel's time.  Stage and phase advance by counting;
             // the next stage's barrier is polled before this stage's MMAs are
             // issued, so that poll's latency overlaps the issue.
-            uint32_t s = 0, ph = 0, gi = 0;
+            uint32_t s = 0, ph = 0, gi = 0, citem = 0;
             bool ready = false;
             bool ok = true;
             const int ks_last = (kp - (a.nch - 1) * F::kc) / F::kstep;
@@ -354,9 +407,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int item = block_item(a, k);
                 const int tile = item / a.row_chunks;
                 const int e0 = a.m.tile_entry_ptr[tile], e1 = a.m.tile_entry_ptr[tile + 1];
+                if (a.wide && e1 > e0) {
+                    // the previous tile's correction columns are drained and zero
+                    ok = tc::mbar_wait(corr_empty, citem & 1u, abort_flag, kWaitLimit);
+                    if (!ok) {
+                        if (!*abort_flag) fail(3);
+                        break;
+                    }
+                    ++citem;
+                }
                 for (int eg = e0; eg < e1 && ok; eg += a.group, ++gi) {
                     const int buf = gi % nbuf;
-                    const uint32_t acc_col = (uint32_t)(buf * kp);
+                    const uint32_t acc_col = main_col(buf);
                     ok = tc::mbar_wait(&acc_empty[buf], ((gi / nbuf) & 1) ^ 1, abort_flag,
                                        kWaitLimit);
                     if (!ok) {
@@ -386,6 +448,36 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const uint64_t dbh = tc::sdesc_advance(db_hi0, so);
                             const uint64_t dbl = tc::sdesc_advance(db_lo0, so);
                             const uint32_t d = tmem + acc_col;
+                            if (a.wide) {
+                                // per K step: lo x S_hi into the main accumulator
+                                // (the group's first overwrites it), then
+                                // hi x [S_hi; S_lo] (or [S_lo; S_hi] for accumulator 1)
+                                // as one N = 2 kp product into the main accumulator
+                                // and the tile's correction columns
+                                const uint32_t dw = tmem + (buf ? (uint32_t)kp : 0u);
+                                const uint64_t db2 = dbh;
+                                const uint64_t dbx = buf ? dbl : dbh;   // where S_hi is
+#pragma unroll
+                                for (int kk = 0; kk < 4; ++kk) {
+                                    if (kk >= ksteps) break;
+                                    const uint32_t kb = 32u * kk;
+                                    if (first) {
+                                        tc::mma_c<kTF32, false>(d, tc::sdesc_advance(dal, kb),
+                                                                tc::sdesc_advance(dbx, kb), id);
+                                        first = false;
+                                    } else {
+                                        tc::mma_c<kTF32, true>(d, tc::sdesc_advance(dal, kb),
+                                                               tc::sdesc_advance(dbx, kb), id);
+                                    }
+                                    tc::mma_c<kTF32, true>(dw, tc::sdesc_advance(dah, kb),
+                                                           tc::sdesc_advance(db2, kb), id2);
+                                }
+                                tc::mma_commit(&empty[s]);
+                                s = s1;
+                                ph = ph1;
+                                ready = ready1;
+                                continue;
+                            }
                             if (first) {
                                 tc::mma_c<kTF32, false>(d, dah, dbh, id);
                                 first = false;
@@ -495,9 +587,10 @@ cudaError_t launch_m2l_tc(const DevM2L &m, const DevOps &o, const DevWork &w, in
     a.row_chunks = w.nrhs;
     a.nitems = m.ntiles * a.row_chunks;
     a.nbuf = 3 * kp <= 512 ? 2 : 1;
+    a.wide = 4 * kp <= 512 ? 1 : 0;
     a.group = group_for(tf32);
     uint32_t cols = 32;
-    while (cols < (uint32_t)((a.nbuf + 1) * kp)) cols <<= 1;
+    while (cols < (uint32_t)((a.wide ? 4 : a.nbuf + 1) * kp)) cols <<= 1;
     a.tmem_cols = cols;
     a.qh_hi = static_cast<const uint4 *>(qh_hi);
     a.qh_lo = static_cast<const uint4 *>(qh_lo);
