@@ -72,6 +72,7 @@ def reference_sample_n(reps, rate=4e3):
 # (kpad; the leaf kernel does not depend on it: None); any other combination
 # reports null.
 TRAFFIC = {
+    ("k_m2l_tc", "sphere_n4e6_p7_ncrit128", "bf16x3", 128): 138.7e6 + 32.4e6,
     ("k_eval", "sphere_n4e6_p7_ncrit128", "bf16x3", None): 1415.6e6 + 62.3e6,
 }
 
