@@ -455,6 +455,40 @@ def run_batch_leg(a, world, rank, dev, flush, stream):
     return leg
 
 
+def run_trials(a, w, dev, flush, stream, value0, err0, seeds=(1, 2, 3, 4)):
+    """The same workload on further seeds (new points and charges, a new
+    plan each), with the main line's protocol but fewer steps: the spread of
+    points/s and error over seeds 0..4 (seed 0 is the main run)."""
+    import numpy as np
+    import torch
+    from paper_2303_08394_gb300 import FMMPlan, _native as N
+    from paper_2303_08394_gb300 import workloads as wl
+    modes = {"fp32": N.M2L_FP32, "bf16x3": N.M2L_BF16X3, "tf32x3": N.M2L_TF32X3}
+    steps = min(a.steps, 20)
+    values, errs = [value0], [err0]
+    for seed in seeds:
+        x, q = w.generate(seed)
+        n = len(x)
+        plan = FMMPlan(x, w.p, w.ncrit, m2l_mode=modes[a.m2l], eps_svd=a.eps_svd)
+        qd = torch.as_tensor(q.astype(np.float32), device=dev)
+        out = torch.empty((n, w.nrhs), dtype=torch.float64, device=dev)
+        ms, _, _ = time_mode(plan, qd, out, flush, stream, steps, a.warmup, 1)
+        values.append(job_value(n * w.nrhs, steps, 1, sum(ms) / 1e3))
+        err = None
+        if err0 is not None:
+            idx = wl.sample_targets(n, w.error_samples or 1000, seed)
+            err = rel_l2(out.cpu().numpy()[idx], _reference(x, q, idx, dev))
+        errs.append(err)
+        del plan, qd, out
+    res = {"seeds": [0, *seeds], "value": values, "unit": UNIT,
+           "value_mean": statistics.mean(values), "value_std": statistics.stdev(values),
+           "steps_per_seed": steps, "rel_l2_err": errs}
+    if all(e is not None for e in errs):
+        res["rel_l2_err_mean"] = statistics.mean(errs)
+        res["rel_l2_err_std"] = statistics.stdev(errs)
+    return res
+
+
 def mean_phases(phases):
     return {k: statistics.mean(ph[k] for ph in phases) for k in phases[0]}
 
@@ -678,6 +712,11 @@ def main():
                                 "note": "19 flops per evaluated pair (near field, direct "
                                         "W/X leaves, L2P, M2P)"}
 
+    # the same workload on seeds 1..4 (one rank only): mean and spread
+    trials = None
+    if not a.quick and world == 1 and w.kind != "batch":
+        trials = run_trials(a, w, dev, flush, stream, value, err)
+
     # the batch of 256 independent problems, same protocol
     batch = None
     if not a.quick and w.kind != "batch":
@@ -697,7 +736,7 @@ def main():
                 "data": "synthetic", "config": config,
                 "rel_l2_err": err, "error_gate_1e-5": (err is not None and err <= 1e-5),
                 "legs": legs, "fp32": legs.get("fp32"), "gradient": gradient,
-                "batch": batch,
+                "batch": batch, "trials": trials,
                 "roofline": dominant, "rooflines": {"m2l": m2l_roof, "leaf": leaf_roof},
                 "phase_ms": ph, "e2e": e2e,
                 "gpu_launches": launches_per_step * a.steps, "clocks": clk,

@@ -44,3 +44,10 @@ def test_batch_leg_names_a_batch_workload_with_its_tolerance():
     assert w.kind == "batch" and w.problems == 256
     assert bench.BATCH_WORKLOAD in bench.EPS_SVD
     assert callable(bench.run_batch_leg)
+
+
+def test_trials_use_four_more_seeds_of_the_same_workload():
+    import inspect
+    import bench
+    sig = inspect.signature(bench.run_trials)
+    assert sig.parameters["seeds"].default == (1, 2, 3, 4)
