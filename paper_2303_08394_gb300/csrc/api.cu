@@ -976,6 +976,7 @@ fmm_status kifmm::plan_enqueue(fmm_plan_s *P, const float *charges, int nrhs, do
             if (sc.x_level_count[l] > 0) {  // boxes of this level with a P2L slot
                 g.seg[1] = seg(o.Qu, ns, b.xchk, nsp, P->dt.x_slot + b0, 0);
                 g.nseg = 2;
+                g.sparse = 1u << 1;  // a few boxes of the level have a slot
             }
             g.scale = o.Qs_inv;
             if (l >= 3) {

@@ -132,6 +132,10 @@ struct VSeg {
 struct VGemm {
     int m, count, nrhs, nseg;
     VSeg seg[kMaxSeg];
+    // Segments (bit s) whose index list names a row for few vectors: a
+    // block skips such a segment when none of its vectors has a row (the
+    // sums are unchanged: the skipped terms are exact zeros).
+    uint32_t sparse;
     const float *scale;
     float *dst;
     int dst_ld;

@@ -91,12 +91,43 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
     const bool split = g.part != nullptr;
     const int s_first = split ? (int)blockIdx.z : 0;
     const int s_end = split ? s_first + 1 : g.nseg;
+    // A segment with no source row for any vector of this block adds only
+    // exact zeros (each of its FMAs adds a * 0 to the sum), so the block
+    // skips its chunks and the sums are bit for bit those of the full walk.
+    // Only the segments the caller marks sparse are checked (the downward
+    // step's X-list segment has rows for a few boxes of a level).  The index
+    // tables are constant, so this runs before the programmatic-dependence
+    // wait.
+    __shared__ uint32_t live_s;
+    uint32_t mine = 0, listed = 0;  // checked segments with a row here / checked
+    for (int s = s_first; s < s_end; ++s) {
+        const VSeg &sg = g.seg[s];
+        if (!sg.src_idx || !((g.sparse >> s) & 1u)) continue;
+        listed |= 1u << s;
+#pragma unroll
+        for (int h = 0; h < XH; ++h)
+            if (tid + h * 128 < XP && pos_l[h] >= 0 && sg.src_idx[pos_l[h]] >= 0)
+                mine |= 1u << s;
+    }
+    uint32_t live = ((1u << s_end) - 1u) & ~((1u << s_first) - 1u);
+    if (listed) {
+        if (tid == 0) live_s = 0;
+        __syncthreads();
+        mine = __reduce_or_sync(0xffffffffu, mine);
+        if ((tid & 31) == 0 && mine) atomicOr(&live_s, mine);
+        __syncthreads();
+        live = (live & ~listed) | live_s;
+    }
     int total_chunks = 0;
-    for (int s = s_first; s < s_end; ++s) total_chunks += (g.seg[s].n + BK - 1) / BK;
+    for (int s = s_first; s < s_end; ++s)
+        if ((live >> s) & 1u) total_chunks += (g.seg[s].n + BK - 1) / BK;
 
-    // the issue side walks the chunks in order: segment is_, chunk icc of
-    // it, and each X piece's source row for that segment
-    int is_ = s_first, icc = 0, inch = s_first < s_end ? (g.seg[s_first].n + BK - 1) / BK : 0;
+    // the issue side walks the chunks of the live segments in order:
+    // segment is_, chunk icc of it, and each X piece's source row for that
+    // segment
+    int is_ = s_first;
+    while (is_ < s_end && !((live >> is_) & 1u)) ++is_;
+    int icc = 0, inch = is_ < s_end ? (g.seg[is_].n + BK - 1) / BK : 0;
     const float *xrow[XH];
     auto set_rows = [&](int s) {
         const VSeg &sg = g.seg[s];
@@ -109,12 +140,14 @@ __global__ void __launch_bounds__(128) k_vgemm(VGemm g) {
             }
         }
     };
-    if (s_first < s_end) set_rows(s_first);
+    if (is_ < s_end) set_rows(is_);
     // copy the next chunk (the c-th, flattened over the segments) into stage c % kStages
     auto issue = [&](int c) {
         if (c < total_chunks) {
             while (icc == inch) {
-                ++is_;
+                do {
+                    ++is_;
+                } while (!((live >> is_) & 1u));
                 icc = 0;
                 inch = (g.seg[is_].n + BK - 1) / BK;
                 set_rows(is_);
